@@ -1,0 +1,328 @@
+"""FP64 CPU oracle of the transport-velocity WCSPH kick-drift-kick step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow reference the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the library itself never
+does, and the two share no code.
+
+The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, compiled with
+``-ffp-contract=off``); this module only builds it with gcc, loads it with
+ctypes and marshals numpy arrays.  Vectors are (N, 3) float64 arrays, with a
+zero third column in 2-D.
+
+Functions and the passages they follow (paper sections / equations):
+
+* ``kernel_W``, ``kernel_dW`` -- Wendland C2 kernel, support 2h (Sec. 4).
+* ``lattice_sum`` -- the reference sum of Eq. 8 on a perfect lattice.
+* ``neighbours`` -- all j with |x_i - x_j| < 2 h_ij (brute force or cells).
+* ``density`` -- Eq. 8 with Eq. 2.
+* ``forces`` -- Eq. 3 (row 2), 5, 6, 7 and Eq. 14-16.
+* ``time_step`` -- Eq. 9-11.
+* ``step`` -- one kick-drift-kick step (Sec. 1, Sec. 3).
+
+Pins (tests/test_oracle_*.py): kernel normalisation by quadrature and its
+derivative by finite differences; lattice partition of unity and zero
+residual; linear pressure and quadratic velocity fields (gradient and
+Laplacian consistency, which fix the factors and signs of Eq. 3 and Eq. 7);
+pairwise momentum and central-force angular momentum conservation; Galilean
+and translation invariance; Riemann limiter scaling; limiter values from
+Eq. 15; the Taylor-Green kinetic-energy decay exp(-16 pi^2 nu t).  The wall
+branch and the variable-resolution pair smoothing length are PARITY UNPINNED
+(the paper states neither).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIBPATH = os.path.join(_BUILD, "libsph_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TV_NONE, TV_LIMITED, TV_UNLIMITED = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available).  Returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIBPATH) and os.path.getmtime(_LIBPATH) >= os.path.getmtime(_SRC):
+        return _LIBPATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    tmp = _LIBPATH + ".tmp%d" % os.getpid()
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``orc_params`` in sph_oracle.c."""
+
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("periodic", ctypes.c_int32 * 3),
+        ("lo", ctypes.c_double * 3),
+        ("L", ctypes.c_double * 3),
+        ("rho0", ctypes.c_double),
+        ("c", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("h_min", ctypes.c_double),
+        ("riemann_eta", ctypes.c_double),
+        ("tv_mode", ctypes.c_int32),
+        ("tv_h_per_particle", ctypes.c_int32),
+        ("tv_xi", ctypes.c_double),
+        ("tv_C", ctypes.c_double),
+        ("tv_thresh", ctypes.c_double),
+        ("h_pair_max", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("cfl_ad", ctypes.c_double),
+        ("cfl_ac", ctypes.c_double),
+        ("u_ref", ctypes.c_double),
+    ]
+
+
+def make_params(dim, lo, L, periodic, rho0, c, eta, h_min, g=(0.0, 0.0, 0.0), u_ref=0.0,
+                tv_mode=TV_LIMITED, tv_h_per_particle=False, h_pair_max=False,
+                riemann_eta=3.0, tv_xi=-0.2, tv_C=1.0e3, tv_thresh=5.0e-4,
+                cfl_ad=0.25, cfl_ac=0.6) -> Params:
+    """Oracle parameters; defaults are the paper's constants (Eq. 6, 9-11, 15, 16)."""
+    P = Params()
+    P.dim = int(dim)
+    for d in range(3):
+        P.periodic[d] = int(bool(periodic[d])) if d < len(periodic) else 0
+        P.lo[d] = float(lo[d]) if d < len(lo) else 0.0
+        P.L[d] = float(L[d]) if d < len(L) else 1.0
+        P.g[d] = float(g[d]) if d < len(g) else 0.0
+    P.rho0, P.c, P.eta, P.h_min = float(rho0), float(c), float(eta), float(h_min)
+    P.riemann_eta = float(riemann_eta)
+    P.tv_mode, P.tv_h_per_particle = int(tv_mode), int(bool(tv_h_per_particle))
+    P.tv_xi, P.tv_C, P.tv_thresh = float(tv_xi), float(tv_C), float(tv_thresh)
+    P.h_pair_max = int(bool(h_pair_max))
+    P.cfl_ad, P.cfl_ac, P.u_ref = float(cfl_ad), float(cfl_ac), float(u_ref)
+    return P
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int64)
+_bp = ctypes.POINTER(ctypes.c_int8)
+_pp = ctypes.POINTER(Params)
+_i64 = ctypes.c_int64
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            sig = {
+                "orc_set_threads": (None, [ctypes.c_int]),
+                "orc_get_threads": (ctypes.c_int, []),
+                "orc_kernel_W": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+                "orc_kernel_dW": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+                "orc_lattice_sum": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
+                "orc_pair_h": (ctypes.c_double, [_pp, ctypes.c_double, ctypes.c_double]),
+                "orc_eos": (ctypes.c_double, [_pp, ctypes.c_double]),
+                "orc_riemann_beta": (ctypes.c_double, [_pp, ctypes.c_double, ctypes.c_double]),
+                "orc_riemann_pstar": (ctypes.c_double, [_pp] + [ctypes.c_double] * 5),
+                "orc_tv_limiter": (ctypes.c_double, [_pp, ctypes.c_double]),
+                "orc_neighbours": (_i64, [_pp, _i64, _dp, _dp, ctypes.c_int, _ip, _ip]),
+                "orc_density": (None, [_pp, _i64, _dp, _dp, _bp, _dp, _ip, _ip, _dp, _dp]),
+                "orc_forces": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip,
+                                      _dp, _dp, _dp, _dp]),
+                "orc_kick": (None, [_pp, _i64, ctypes.c_double, _dp, _dp, _bp]),
+                "orc_drift": (None, [_pp, _i64, ctypes.c_double, _dp, _dp, _dp, _bp]),
+                "orc_time_step": (ctypes.c_double, [_pp, _i64, _dp, _bp]),
+                "orc_diagnostics": (None, [_pp, _i64, _dp, _dp, _bp, _dp, _dp, ctypes.c_double, _dp]),
+                "orc_force_pass": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
+                                                  ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
+                "orc_step": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
+                                            ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _vec(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape == (n, 2):
+        a = np.concatenate([a, np.zeros((n, 1))], axis=1)
+    assert a.shape == (n, 3), a.shape
+    return np.ascontiguousarray(a)
+
+
+def _sca(a, n, dtype=np.float64):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=dtype), (n,)), dtype=dtype)
+    return a
+
+
+def kernel_W(r, h, dim):
+    return lib().orc_kernel_W(float(r), float(h), int(dim))
+
+
+def kernel_dW(r, h, dim):
+    return lib().orc_kernel_dW(float(r), float(h), int(dim))
+
+
+def lattice_sum(dim, h_over_dp=1.3):
+    """sum_k W(|k|, h_over_dp) over the unit integer lattice (sigma0 * dp^D)."""
+    return lib().orc_lattice_sum(int(dim), float(h_over_dp))
+
+
+def pair_h(P, hi, hj):
+    return lib().orc_pair_h(ctypes.byref(P), float(hi), float(hj))
+
+
+def eos(P, rho):
+    return lib().orc_eos(ctypes.byref(P), float(rho))
+
+
+def riemann_beta(P, ul, ur):
+    return lib().orc_riemann_beta(ctypes.byref(P), float(ul), float(ur))
+
+
+def riemann_pstar(P, pl, pr, rhobar, ul, ur):
+    return lib().orc_riemann_pstar(ctypes.byref(P), float(pl), float(pr), float(rhobar), float(ul), float(ur))
+
+
+def tv_limiter(P, s):
+    return lib().orc_tv_limiter(ctypes.byref(P), float(s))
+
+
+def neighbours(P, x, h, mode="cells"):
+    """CSR neighbour lists (self included, ascending j): returns (start, idx)."""
+    n = len(x)
+    x = _vec(x, n)
+    h = _sca(h, n)
+    m = {"brute": 0, "cells": 1}[mode]
+    start = np.zeros(n + 1, dtype=np.int64)
+    tot = lib().orc_neighbours(ctypes.byref(P), n, _d(x), _d(h), m, start.ctypes.data_as(_ip), None)
+    idx = np.zeros(max(int(tot), 1), dtype=np.int64)
+    lib().orc_neighbours(ctypes.byref(P), n, _d(x), _d(h), m, start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip))
+    return start, idx[: int(tot)]
+
+
+def density(P, x, h, kind, sigma0, nbrs):
+    """Eq. 8: returns (rho, sigma)."""
+    n = len(x)
+    x, h, s0 = _vec(x, n), _sca(h, n), _sca(sigma0, n)
+    kind = _sca(kind, n, np.int8)
+    start, idx = nbrs
+    idx = np.ascontiguousarray(idx, dtype=np.int64) if len(idx) else np.zeros(1, np.int64)
+    rho, sigma = np.zeros(n), np.zeros(n)
+    lib().orc_density(ctypes.byref(P), n, _d(x), _d(h), kind.ctypes.data_as(_bp), _d(s0),
+                      start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), _d(rho), _d(sigma))
+    return rho, sigma
+
+
+def forces(P, x, v, h, m, kind, vw, rho, nbrs):
+    """Eq. 3, 5-7, 14-16: returns dict a, R, chi, dr."""
+    n = len(x)
+    x, v, vw = _vec(x, n), _vec(v, n), _vec(vw, n)
+    h, m, rho = _sca(h, n), _sca(m, n), _sca(rho, n)
+    kind = _sca(kind, n, np.int8)
+    start, idx = nbrs
+    idx = np.ascontiguousarray(idx, dtype=np.int64) if len(idx) else np.zeros(1, np.int64)
+    a, R, dr = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    chi = np.zeros(n)
+    lib().orc_forces(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp), _d(vw), _d(rho),
+                     start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), _d(a), _d(R), _d(chi), _d(dr))
+    return {"a": a, "R": R, "chi": chi, "dr": dr}
+
+
+def time_step(P, v, kind):
+    """Eq. 9-11 with h = h_min."""
+    n = len(v)
+    v = _vec(v, n)
+    kind = _sca(kind, n, np.int8)
+    return lib().orc_time_step(ctypes.byref(P), n, _d(v), kind.ctypes.data_as(_bp))
+
+
+def diagnostics(P, v, m, kind, dr, chi, dt):
+    """mass, momentum[3], KE, max|v|, max overcorrection ratio, count chi>0."""
+    n = len(v)
+    v, dr = _vec(v, n), _vec(dr, n)
+    m, chi = _sca(m, n), _sca(chi, n)
+    kind = _sca(kind, n, np.int8)
+    out = np.zeros(8)
+    lib().orc_diagnostics(ctypes.byref(P), n, _d(v), _d(m), kind.ctypes.data_as(_bp), _d(dr), _d(chi),
+                          float(dt), _d(out))
+    return {"mass": out[0], "momentum": out[1:4].copy(), "ke": out[4], "vmax": out[5],
+            "overcorrection": out[6], "n_chi": int(out[7])}
+
+
+def _case_arrays(case, n):
+    h = _sca(case["h"], n)
+    m = _sca(case["m"], n)
+    kind = _sca(case.get("kind", 0), n, np.int8)
+    vw = _vec(case.get("vw", np.zeros((n, 3))), n)
+    return h, m, kind, vw
+
+
+def force_pass(P, case, x, v, sigma0, mode="cells"):
+    """Neighbours + density + forces on (x, v): returns dict rho, a, R, chi, dr."""
+    n = len(x)
+    x, v = _vec(x, n), _vec(v, n)
+    h, m, kind, vw = _case_arrays(case, n)
+    s0 = _sca(sigma0, n)
+    rho, chi = np.zeros(n), np.zeros(n)
+    a, R, dr = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    rc = lib().orc_force_pass(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp), _d(vw),
+                              _d(s0), {"brute": 0, "cells": 1}[mode], _d(rho), _d(a), _d(R), _d(chi), _d(dr))
+    if rc:
+        raise MemoryError("oracle force pass failed")
+    return {"rho": rho, "a": a, "R": R, "chi": chi, "dr": dr}
+
+
+def step(P, case, state, sigma0, dt, mode="cells"):
+    """One kick-drift-kick step.  ``state`` holds x, v, a, dr ((N,3) float64);
+    returns a new dict with x, v, a, dr, rho, R, chi (inputs untouched)."""
+    n = len(state["x"])
+    x, v = _vec(state["x"], n).copy(), _vec(state["v"], n).copy()
+    a, dr = _vec(state["a"], n).copy(), _vec(state["dr"], n).copy()
+    h, m, kind, vw = _case_arrays(case, n)
+    s0 = _sca(sigma0, n)
+    rho, chi, R = np.zeros(n), np.zeros(n), np.zeros((n, 3))
+    rc = lib().orc_step(ctypes.byref(P), n, _d(x), _d(v), _d(a), _d(dr), _d(h), _d(m), kind.ctypes.data_as(_bp),
+                        _d(vw), _d(s0), float(dt), {"brute": 0, "cells": 1}[mode], _d(rho), _d(R), _d(chi))
+    if rc:
+        raise MemoryError("oracle step failed")
+    return {"x": x, "v": v, "a": a, "dr": dr, "rho": rho, "R": R, "chi": chi}
+
+
+def sigma0_for(case, dim):
+    """Per-particle reference sum of Eq. 8: the perfect-lattice sum at the
+    particle's own spacing dp = (m / rho0)^(1/D) and smoothing length h."""
+    h = np.asarray(case["h"], dtype=np.float64)
+    m = np.asarray(case["m"], dtype=np.float64)
+    dp = (m / case["rho0"]) ** (1.0 / dim)
+    out = np.empty(len(h))
+    pairs, inv = np.unique(np.stack([h, dp], axis=1), axis=0, return_inverse=True)
+    vals = np.array([lattice_sum(dim, hh / dd) / dd ** dim for hh, dd in pairs])
+    out[:] = vals[np.ravel(inv)]
+    return out
