@@ -1,0 +1,220 @@
+/*
+ * sphtv.h -- C ABI of libsphtv, a single-GPU (sm_103a) library for one
+ * kick-drift-kick step of weakly-compressible SPH with the limited,
+ * h^2-scaled transport-velocity correction of Wang, Haidn & Hu, "The
+ * efficient implementation of transport velocity formulation"
+ * (arXiv 2411.13992).
+ *
+ * What one step computes (paper sections / equations):
+ *   1. half kick  v += dt/2 a;  drift  x += dt v + dr  (kick-drift-kick,
+ *      Sec. 1 and Sec. 3; dr is the transport-velocity displacement of the
+ *      previous step, applied once per step, Sec. 3);
+ *   2. cell-linked list: particles counting-sorted by cell index, ties broken
+ *      by particle id, so the order is deterministic;
+ *   3. density summation rho_i = rho0 sum_j W_ij / sigma0_i (Eq. 8) with the
+ *      equation of state p = c^2 (rho - rho0) (Eq. 2), Wendland C2 kernel
+ *      with support 2h (Sec. 4);
+ *   4. one fused pair pass: Riemann pressure force with the dissipation
+ *      limiter (Eq. 3 second row, Eq. 5-6), viscous force (Eq. 7), the
+ *      residual R_i = sum_j V_j grad_i W_ij and the limited displacement
+ *      dr_i = xi chi_i h^2 R_i (Eq. 14-16);
+ *   5. closing half kick, FP64 diagnostics and the next step size
+ *      min(dt_ad, dt_ac) (Eq. 9-11, h = h_min).
+ *
+ * Conventions.
+ *   - Vectors crossing the ABI are row-major [n][3] doubles (x, y, z per
+ *     particle; z is ignored in 2-D).  Scalars are [n] arrays.
+ *   - Every pointer argument may be host or device memory (the library
+ *     copies with cudaMemcpyKind Default); host memory should be pinned for
+ *     asynchronous transfers.  Arrays passed in are read during the call's
+ *     stream work only; the library keeps its own copy in the workspace.
+ *   - Results are always returned in the particle order given to
+ *     sph_set_state, whatever the internal (cell-sorted) order is.
+ *   - The caller owns the device workspace and the stream.  The library
+ *     allocates no device memory: it carves every buffer out of the
+ *     workspace given to sph_create, whose size sph_query_workspace reports.
+ *     The context itself is a small host object.
+ *   - All calls enqueue work on the context's stream and return without
+ *     waiting, except sph_sync, sph_get_diag, and sph_get_state /
+ *     sph_step_adjoint when they write to host memory.
+ *   - Every call returns a status.  Host-detectable errors (bad arguments,
+ *     call order, workspace too small, CUDA launch errors) return at once.
+ *     Device-detected errors (cell overflow, non-finite values, particle
+ *     outside a non-periodic box) set a sticky error word that sph_sync
+ *     returns.  Nothing is thrown across the ABI; no call traps the GPU.
+ */
+#ifndef SPHTV_H
+#define SPHTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPH_API __attribute__((visibility("default")))
+#else
+#define SPH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sph_status {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,        /* invalid argument (host check) */
+    SPH_ERR_CUDA = 2,       /* a CUDA call failed */
+    SPH_ERR_WORKSPACE = 3,  /* workspace NULL, misaligned or too small */
+    SPH_ERR_OVERFLOW = 4,   /* device: a cell held more particles than supported */
+    SPH_ERR_NAN = 5,        /* device: non-finite position or velocity */
+    SPH_ERR_DOMAIN = 6,     /* device: particle left a non-periodic box */
+    SPH_ERR_STATE = 7       /* call order: e.g. sph_step before sph_build_cells */
+} sph_status;
+
+enum { SPH_TV_OFF = 0, SPH_TV_LIMITED = 1, SPH_TV_UNLIMITED = 2 };
+enum { SPH_TVH_MIN = 0, SPH_TVH_PARTICLE = 1 };
+enum { SPH_HPAIR_MEAN = 0, SPH_HPAIR_MAX = 1 };
+
+/* Plain-data parameter block.  sph_default_params fills the paper's
+ * constants; the caller sets the domain and the fluid. */
+typedef struct sph_params {
+    int32_t dim;            /* 2 or 3 */
+    int32_t precision;      /* 64: FP64 throughout; 32: FP32 pair sums with
+                               Kahan compensation, FP32 cell-relative positions,
+                               FP64 positions for the drift and FP64 reductions */
+    int32_t periodic[3];    /* 1: periodic along that axis */
+    int32_t tv_mode;        /* SPH_TV_*: none / limited (Eq. 16) / unlimited (Eq. 14) */
+    double lo[3];           /* domain lower corner */
+    double L[3];            /* domain lengths; every particle must stay in
+                               [lo, lo+L] along non-periodic axes */
+    double rho0;            /* reference density (Eq. 2, 8) */
+    double c0;              /* artificial sound speed c (Eq. 2) */
+    double eta;             /* dynamic viscosity (Eq. 7) */
+    double g[3];            /* body force per unit mass */
+    double h_min;           /* minimum smoothing length (Eq. 9-11, 15-16) */
+    double h_max;           /* maximum smoothing length: sets the cell edge >= 2 h_max */
+    double riemann_eta;     /* dissipation limiter slope, 3 (Eq. 6) */
+    double tv_xi;           /* -0.2 (Eq. 14, 16) */
+    double tv_C;            /* 1e3 (Eq. 15) */
+    double tv_thresh;       /* 5e-4 (Eq. 15) */
+    double cfl_ad;          /* 0.25 (Eq. 9) */
+    double cfl_ac;          /* 0.6 (Eq. 11) */
+    double u_ref;           /* reference velocity U_ref (Eq. 10) */
+    double fixed_dt;        /* > 0: every step uses this dt; 0: Eq. 9-11 */
+    int32_t tv_h;           /* SPH_TVH_*: h in Eq. 14-16 is h_min (paper) or h_i */
+    int32_t h_pair;         /* SPH_HPAIR_*: h_ij = (h_i+h_j)/2 (default) or max */
+    int32_t kahan;          /* FP32 form: 1 = compensated pair sums (default) */
+    int32_t reserved;
+} sph_params;
+
+/* FP64 diagnostics of the fluid particles after a step (or after
+ * sph_build_cells). */
+typedef struct sph_diag {
+    double mass;            /* sum m */
+    double momentum[3];     /* sum m v */
+    double kinetic;         /* 1/2 sum m |v|^2 */
+    double vmax;            /* max |v| */
+    double vt_max;          /* max |v + dr/dt|: transport velocity (Sec. 3) */
+    double dr_max;          /* max |dr| */
+    double n_chi;           /* number of particles with chi > 0 (Eq. 15) */
+    double dt;              /* step size used by the last step */
+    double dt_next;         /* step size the next step will use */
+    double steps;           /* steps taken since sph_build_cells */
+} sph_diag;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Fill *p with the paper's constants: riemann_eta 3, tv_xi -0.2, tv_C 1e3,
+ * tv_thresh 5e-4, cfl_ad 0.25, cfl_ac 0.6, tv_mode limited, tv_h h_min,
+ * h_pair mean, kahan on, precision 64, dim 2, rho0 1.  Returns SPH_ERR_ARG
+ * on NULL. */
+SPH_API sph_status sph_default_params(sph_params* p);
+
+/* Bytes of device workspace a context for n particles needs.  n >= 1.
+ * The cell grid follows from dim, lo, L, periodic and h_max: along each
+ * axis floor(L / (2 h_max)) cells (at least 3 along periodic axes, else
+ * SPH_ERR_ARG).  Returns SPH_ERR_ARG on invalid parameters. */
+SPH_API sph_status sph_query_workspace(const sph_params* p, int64_t n, size_t* bytes);
+
+/* Create a context on the current CUDA device.  workspace: device memory
+ * of at least the queried size, 256-byte aligned, owned by the caller and
+ * kept alive until sph_destroy.  stream: a cudaStream_t (NULL = legacy
+ * default stream) on which every call of this context enqueues its work. */
+SPH_API sph_status sph_create(const sph_params* p, int64_t n, void* workspace, size_t bytes, void* stream,
+                      sph_ctx** out);
+
+/* Load the particle state (Sec. 2; Eq. 8 reference sums).
+ *   x  [n][3] positions (required)            v  [n][3] velocities (required)
+ *   a  [n][3] accelerations or NULL           dr [n][3] displacements or NULL
+ *   h  [n] smoothing lengths (required)       m  [n] masses (required)
+ *   kind [n] int8: 0 fluid, 1 wall, or NULL (all fluid)
+ *   vw [n][3] prescribed wall velocities or NULL (zero)
+ *   sigma0 [n] reference sums of Eq. 8 or NULL: then sigma0_i is the
+ *     perfect-lattice sum at spacing dp_i = (m_i/rho0)^(1/D) and h_i.
+ * With a and dr NULL, sph_build_cells computes them from x and v (initial
+ * force pass).  Velocities of walls are their prescribed velocities. */
+SPH_API sph_status sph_set_state(sph_ctx* ctx, const double* x, const double* v, const double* a, const double* dr,
+                         const double* h, const double* m, const int8_t* kind, const double* vw,
+                         const double* sigma0);
+
+/* Sort the loaded state into cells and run the density pass; when a/dr
+ * were not given, also the force pass (a, dr from x and v).  Then compute
+ * the diagnostics and the first dt (Eq. 9-11, or fixed_dt). */
+SPH_API sph_status sph_build_cells(sph_ctx* ctx);
+
+/* Advance nsteps >= 0 kick-drift-kick steps on the context's stream. */
+SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
+
+/* Override the step size of the next step (> 0). */
+SPH_API sph_status sph_set_dt(sph_ctx* ctx, double dt);
+
+/* Copy the state out in the caller's original particle order.  Any pointer
+ * may be NULL.  x, v, a, dr: [n][3]; rho: [n] (walls report rho0).  Waits
+ * for the copy when a destination is host memory. */
+SPH_API sph_status sph_get_state(sph_ctx* ctx, double* x, double* v, double* a, double* dr, double* rho);
+
+/* Wait for the stream and copy the diagnostics of the last step. */
+SPH_API sph_status sph_get_diag(sph_ctx* ctx, sph_diag* out);
+
+/* Wait for the context's stream; return the sticky device error word as a
+ * status (SPH_OK if none), then clear it. */
+SPH_API sph_status sph_sync(sph_ctx* ctx);
+
+/* Destroy the host context (the workspace stays the caller's). */
+SPH_API void sph_destroy(sph_ctx* ctx);
+
+/* Static description of a status code. */
+SPH_API const char* sph_status_str(sph_status s);
+
+/* Number of kernel launches this context has enqueued since creation. */
+SPH_API int64_t sph_launch_count(const sph_ctx* ctx);
+
+/* Kernel classes of one step, for per-kernel timing. */
+enum {
+    SPH_K_KICKDRIFT = 0,   /* kick + drift + cell key + histogram */
+    SPH_K_SCAN = 1,        /* exclusive scan of the cell counts */
+    SPH_K_ORDER = 2,       /* scatter into cells + per-cell order by id */
+    SPH_K_PERMUTE = 3,     /* permute the particle arrays */
+    SPH_K_DENSITY = 4,     /* density summation (Eq. 8) */
+    SPH_K_FORCES = 5,      /* fused pair pass (Eq. 3, 5-7, 14-16) + closing kick */
+    SPH_K_FINALIZE = 6,    /* FP64 reductions and dt (Eq. 9-11) */
+    SPH_K_NCLASS = 7
+};
+
+/* Per-kernel timing (tracing).  After sph_profile_begin, each of the next
+ * max_steps steps records a CUDA event before and after every kernel class
+ * on the context's stream (events are host-created driver objects; no device
+ * memory is allocated).  sph_profile_end waits for the stream and writes,
+ * per class, the summed elapsed milliseconds (ms[SPH_K_NCLASS]) and the
+ * number of timed launches (count[SPH_K_NCLASS]); either may be NULL.
+ * Returns SPH_ERR_STATE if no profile is open, SPH_ERR_ARG if max_steps < 1. */
+SPH_API sph_status sph_profile_begin(sph_ctx* ctx, int32_t max_steps);
+SPH_API sph_status sph_profile_end(sph_ctx* ctx, double* ms, int64_t* count);
+
+/* Static name of a kernel class ("forces", ...), or "?" when out of range. */
+SPH_API const char* sph_kernel_class_name(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHTV_H */

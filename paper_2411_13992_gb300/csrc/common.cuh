@@ -1,0 +1,188 @@
+// common.cuh -- device helpers shared by the libsphtv kernels: the Wendland
+// C2 kernel (Sec. 4, h = 1.3 dp, support 2h), the cell grid of the
+// cell-linked list, compensated FP32 summation, and the context's buffer
+// layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sphtv.h"
+
+namespace sphtv {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Device error word bits (sticky; read back by sph_sync).
+enum : uint32_t { ERRB_OVERFLOW = 1u, ERRB_NAN = 2u, ERRB_DOMAIN = 4u };
+
+// Number of FP64 per-block partial values the fused force kernel writes.
+constexpr int kNPart = 10;
+// Indices into the device diagnostics block (doubles).
+enum {
+    DG_MASS = 0, DG_MOM = 1, DG_KE = 4, DG_VMAX = 5, DG_VTMAX = 6, DG_DRMAX = 7, DG_NCHI = 8,
+    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_COUNT = 16
+};
+
+// Cell grid of the cell-linked list: edge >= 2 h_max along every axis, so
+// every neighbour of a particle lies in the 3^D block around its cell.
+struct Grid {
+    int nc[3];
+    int periodic[3];
+    double lo[3];
+    double hi[3];       // lo + L, computed once on the host
+    double L[3];
+    double half_L[3];
+    double edge[3];
+    double inv_edge[3];
+    float edgef[3];
+    int ncell;
+};
+
+// Constants of the method for one precision.
+template <typename Real>
+struct Consts {
+    Real rho0, c, c2, eta, two_eta, beta_slope, inv_c;
+    Real g[3];
+    Real h_min, tv_xi, tv_C, tv_thresh;
+    int tv_mode, tv_h_particle, h_pair_max, kahan;
+};
+
+// Velocity + density deviation packed per particle for the pair pass:
+// w = rho - rho0 (fluid), +inf marks a wall particle.
+template <typename Real> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4_32a; };
+
+// ------------------------------------------------------------ kernel W
+
+template <int DIM, typename Real>
+__device__ __forceinline__ Real kernel_norm()
+{
+    // a_D h^D: 7/(4 pi) in 2-D, 21/(16 pi) in 3-D
+    return DIM == 2 ? Real(7.0 / (4.0 * kPi)) : Real(21.0 / (16.0 * kPi));
+}
+
+template <int DIM, typename Real>
+__device__ __forceinline__ Real pow_dim(Real x)
+{
+    return DIM == 2 ? x * x : x * x * x;
+}
+
+// W(r, h) for r < 2h (callers test the support first).
+template <int DIM, typename Real>
+__device__ __forceinline__ Real wendland_W(Real r, Real inv_h)
+{
+    Real q = r * inv_h;
+    Real t = Real(1) - Real(0.5) * q;
+    Real t2 = t * t;
+    return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * (t2 * t2) * (Real(2) * q + Real(1));
+}
+
+// dW/dr (r, h) for r < 2h.
+template <int DIM, typename Real>
+__device__ __forceinline__ Real wendland_dW(Real r, Real inv_h)
+{
+    Real q = r * inv_h;
+    Real t = Real(1) - Real(0.5) * q;
+    return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * inv_h * (Real(-5) * q) * (t * t * t);
+}
+
+// ------------------------------------------------------- compensated sum
+
+struct KSum {
+    float s, c;
+    __device__ __forceinline__ KSum() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float x)
+    {
+        // Kahan: explicit round-to-nearest intrinsics so that neither
+        // contraction nor reassociation removes the compensation.
+        float y = __fsub_rn(x, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s; }
+};
+
+struct PlainF {
+    float s;
+    __device__ __forceinline__ PlainF() : s(0.f) {}
+    __device__ __forceinline__ void add(float x) { s += x; }
+    __device__ __forceinline__ float value() const { return s; }
+};
+
+struct PlainD {
+    double s;
+    __device__ __forceinline__ PlainD() : s(0.0) {}
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// ------------------------------------------------------------ cell grid
+
+__device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
+{
+    int c = (int)floor((x - G.lo[d]) * G.inv_edge[d]);
+    c = c < 0 ? 0 : c;
+    c = c >= G.nc[d] ? G.nc[d] - 1 : c;
+    return c;
+}
+
+template <int DIM>
+__device__ __forceinline__ int cell_index(const Grid& G, const double* xs)
+{
+    int c0 = cell_coord(G, xs[0], 0);
+    int c1 = cell_coord(G, xs[1], 1);
+    int c2 = DIM == 3 ? cell_coord(G, xs[2], 2) : 0;
+    return c0 + G.nc[0] * (c1 + G.nc[1] * c2);
+}
+
+__device__ __forceinline__ void cell_decode(const Grid& G, int key, int* c)
+{
+    c[0] = key % G.nc[0];
+    int r = key / G.nc[0];
+    c[1] = r % G.nc[1];
+    c[2] = r / G.nc[1];
+}
+
+// Neighbour cell coordinate along axis d, or -1 when it falls outside a
+// non-periodic axis.
+__device__ __forceinline__ int cell_step(const Grid& G, int c, int dc, int d)
+{
+    int n = c + dc;
+    if (n < 0 || n >= G.nc[d]) {
+        if (!G.periodic[d]) return -1;
+        n = n < 0 ? n + G.nc[d] : n - G.nc[d];
+    }
+    return n;
+}
+
+// x_i - x_j along axis d with the minimum image on periodic axes (FP64).
+__device__ __forceinline__ double min_image(const Grid& G, double xi, double xj, int d)
+{
+    double dx = __dsub_rn(xi, xj);
+    if (G.periodic[d]) {
+        if (dx > G.half_L[d]) dx = __dsub_rn(dx, G.L[d]);
+        else if (dx < -G.half_L[d]) dx = __dadd_rn(dx, G.L[d]);
+    }
+    return dx;
+}
+
+// ------------------------------------------------------------ buffers
+
+// Particle arrays of one cell-sorted copy of the state.
+template <typename Real>
+struct StateSet {
+    double* x;      // [DIM][n] positions (FP64 master in both precisions)
+    Real* v;        // [DIM][n] velocities (walls: prescribed velocity)
+    Real* a;        // [DIM][n] accelerations (only carried by the first sort)
+    Real* dr;       // [DIM][n] transport displacements (only carried by the first sort)
+    double* h;      // [n] smoothing lengths
+    double* m;      // [n] masses
+    double* s0;     // [n] reference sums sigma0 (Eq. 8)
+    int32_t* id;    // [n] caller's particle index
+    int8_t* kind;   // [n] 0 fluid, 1 wall
+};
+
+}  // namespace sphtv

@@ -1,0 +1,283 @@
+// k_cells.cu -- the kick-drift stage and the cell-linked list of libsphtv.
+//
+// Per step:  kick + drift + cell key + histogram  ->  exclusive scan of the
+// cell counts  ->  atomic scatter into cell ranges  ->  per-cell ordering by
+// particle id (so the sorted order never depends on atomic timing)  ->
+// permute the particle arrays into the new order (and, in the FP32 form,
+// emit FP32 positions relative to each particle's cell origin).
+//
+// The kick-drift follows the kick-drift-kick scheme the paper names (Sec. 1,
+// Sec. 3): v += dt/2 a; x += dt v + dr, where dr is the transport-velocity
+// displacement of the previous step (Eq. 16), applied once per step.
+#include "common.cuh"
+#include "launch.h"
+
+namespace sphtv {
+
+template <typename Real>
+__device__ __forceinline__ Real kick(Real v, double hdt, Real a);
+
+template <>
+__device__ __forceinline__ double kick<double>(double v, double hdt, double a)
+{
+    return __dadd_rn(v, __dmul_rn(hdt, a));
+}
+
+template <>
+__device__ __forceinline__ float kick<float>(float v, double hdt, float a)
+{
+    return __fadd_rn(v, __fmul_rn((float)hdt, a));
+}
+
+template <typename Real, int DIM>
+__global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restrict__ dt_ptr, int drift, Grid G,
+                                 int32_t* __restrict__ key, int32_t* __restrict__ count, uint32_t* err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) xs[d] = S.x[(size_t)d * n + i];
+    uint32_t e = 0;
+    if (drift && S.kind[i] == 0) {
+        const double dt = *dt_ptr;
+        const double hdt = 0.5 * dt;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            size_t o = (size_t)d * n + i;
+            Real vh = kick<Real>(S.v[o], hdt, S.a[o]);
+            S.v[o] = vh;
+            double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, (double)vh)), (double)S.dr[o]);
+            if (G.periodic[d]) {
+                if (xn < G.lo[d]) xn = __dadd_rn(xn, G.L[d]);
+                else if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
+            }
+            if (!isfinite(xn) || !isfinite((double)vh)) e |= ERRB_NAN;
+            xs[d] = xn;
+            S.x[o] = xn;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        if (!isfinite(xs[d])) { e |= ERRB_NAN; xs[d] = G.lo[d]; }
+        else if (xs[d] < G.lo[d] || xs[d] > G.hi[d]) e |= ERRB_DOMAIN;
+    }
+    if (e) atomicOr(err, e);
+    int k = cell_index<DIM>(G, xs);
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+}
+
+// ------------------------------------------------------- exclusive scan
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of in[0, n) into out (in place allowed); each block scans
+// one tile and writes its total to bsum[blockIdx.x].
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const int32_t* in, int32_t* out, int32_t* bsum, int n)
+{
+    __shared__ int32_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int32_t vals[kScanItems];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int idx = base + k;
+        vals[k] = idx < n ? in[idx] : 0;
+        s += vals[k];
+    }
+    int32_t incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        constexpr int nw = kScanThreads / 32;
+        int32_t t = lane < nw ? warp_tot[lane] : 0;
+        int32_t ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int32_t u = __shfl_up_sync(0xffffffffu, ti, off);
+            if (lane >= off) ti += u;
+        }
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == nw - 1) bsum[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    int32_t pre = warp_tot[w] + incl - s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int idx = base + k;
+        if (idx < n) out[idx] = pre;
+        pre += vals[k];
+    }
+}
+
+__global__ void k_scan_add(int32_t* out, const int32_t* boff, int n)
+{
+    int idx = blockIdx.x * kScanTile + threadIdx.x;
+    int32_t add = boff[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k, idx += kScanThreads)
+        if (idx < n) out[idx] += add;
+}
+
+size_t scan_temp_elems(int n)
+{
+    size_t tot = 0;
+    while (n > 1) {
+        n = (n + kScanTile - 1) / kScanTile;
+        tot += (size_t)n + 1;
+    }
+    return tot + 1;
+}
+
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* tmp, cudaStream_t st,
+                                  int64_t* launches)
+{
+    int nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_tile<<<nb, kScanThreads, 0, st>>>(in, out, tmp, n);
+    ++*launches;
+    if (nb > 1) {
+        cudaError_t e = launch_exclusive_scan(tmp, tmp, nb, tmp + nb + 1, st, launches);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<nb, kScanThreads, 0, st>>>(out, tmp, n);
+        ++*launches;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ scatter and cell order
+
+__global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
+                          int32_t* __restrict__ cursor, int32_t* __restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = key[i];
+    int pos = start[k] + atomicAdd(&cursor[k], 1);
+    perm[pos] = i;
+}
+
+// One warp per cell: place the cell's particles in increasing caller id
+// (ids are unique, so the rank of each is its slot).
+__global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, const int32_t* __restrict__ perm_in,
+                              const int32_t* __restrict__ id, int32_t* __restrict__ perm_out)
+{
+    int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (warp >= ncell) return;
+    int s = start[warp], e = start[warp + 1];
+    for (int k = s + lane; k < e; k += 32) {
+        int p = perm_in[k];
+        int myid = id[p];
+        int rank = 0;
+        for (int t = s; t < e; ++t) rank += id[perm_in[t]] < myid;
+        perm_out[s + rank] = p;
+    }
+}
+
+// --------------------------------------------------------------- permute
+
+template <typename Real, int DIM, bool CARRY_AD, bool F32POS>
+__global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real> src, StateSet<Real> dst,
+                          const int32_t* __restrict__ key, Grid G, float4* __restrict__ pos4,
+                          int32_t* __restrict__ cell_out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = perm[k];
+    double xs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        size_t so = (size_t)d * n + i, dof = (size_t)d * n + k;
+        xs[d] = src.x[so];
+        dst.x[dof] = xs[d];
+        dst.v[dof] = src.v[so];
+        if (CARRY_AD) {
+            dst.a[dof] = src.a[so];
+            dst.dr[dof] = src.dr[so];
+        }
+    }
+    double h = src.h[i];
+    dst.h[k] = h;
+    dst.m[k] = src.m[i];
+    dst.s0[k] = src.s0[i];
+    dst.id[k] = src.id[i];
+    dst.kind[k] = src.kind[i];
+    if (F32POS) {
+        int kk = key[i];
+        int c[3];
+        cell_decode(G, kk, c);
+        float o[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) o[d] = (float)(xs[d] - (G.lo[d] + (double)c[d] * G.edge[d]));
+        pos4[k] = make_float4(o[0], o[1], o[2], (float)h);
+        cell_out[k] = kk;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const double* dt, int drift, const Grid& G,
+                                  int32_t* key, int32_t* count, uint32_t* err, cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        auto s = *(StateSet<double>*)S;
+        if (dim == 2) k_kick_drift_key<double, 2><<<nblk(n, T), T, 0, st>>>(n, s, dt, drift, G, key, count, err);
+        else k_kick_drift_key<double, 3><<<nblk(n, T), T, 0, st>>>(n, s, dt, drift, G, key, count, err);
+    } else {
+        auto s = *(StateSet<float>*)S;
+        if (dim == 2) k_kick_drift_key<float, 2><<<nblk(n, T), T, 0, st>>>(n, s, dt, drift, G, key, count, err);
+        else k_kick_drift_key<float, 3><<<nblk(n, T), T, 0, st>>>(n, s, dt, drift, G, key, count, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int32_t* start, int32_t* cursor,
+                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, cudaStream_t st,
+                                 int64_t* launches)
+{
+    const int T = 256;
+    k_scatter<<<nblk(n, T), T, 0, st>>>(n, key, start, cursor, perm_tmp);
+    int warps_per_block = T / 32;
+    k_order_cells<<<nblk(ncell, warps_per_block), T, 0, st>>>(ncell, start, perm_tmp, id, perm);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename Real>
+static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
+                      const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st)
+{
+    const int T = 256;
+    auto s = *(StateSet<Real>*)src;
+    auto d = *(StateSet<Real>*)dst;
+    constexpr bool F32 = sizeof(Real) == 4;
+    if (dim == 2) {
+        if (carry_ad) k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+        else k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+    } else {
+        if (carry_ad) k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+        else k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+    }
+}
+
+cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
+                           const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st)
+{
+    if (prec == 64) permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, carry_ad, st);
+    else permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, carry_ad, st);
+    return cudaGetLastError();
+}
+
+}  // namespace sphtv

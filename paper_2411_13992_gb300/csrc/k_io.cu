@@ -1,0 +1,158 @@
+// k_io.cu -- state transfer kernels of libsphtv: caller [n][3] rows <->
+// per-component arrays, un-permuting from the cell order back to the
+// caller's order, wall velocities, and the per-particle reference sums
+// sigma0 of Eq. 8 (the perfect-lattice sum at the particle's own spacing
+// dp = (m/rho0)^(1/D) and smoothing length h).
+#include "common.cuh"
+#include "launch.h"
+
+namespace sphtv {
+
+template <typename Real, int DIM>
+__global__ void k_vec_in(int n, const double* __restrict__ src3, Real* __restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) dst[(size_t)d * n + i] = (Real)src3[3 * (size_t)i + d];
+}
+
+template <typename Real, int DIM>
+__global__ void k_vec_out(int n, const Real* __restrict__ src, const int32_t* __restrict__ id,
+                          double* __restrict__ dst3)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    size_t o = 3 * (size_t)id[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dst3[o + d] = d < DIM ? (double)src[(size_t)d * n + k] : 0.0;
+}
+
+template <typename Real, int DIM>
+__global__ void k_walls_velocity(int n, const int8_t* __restrict__ kind, const double* __restrict__ vw3,
+                                 Real* __restrict__ v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !kind[i]) return;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) v[(size_t)d * n + i] = vw3 ? (Real)vw3[3 * (size_t)i + d] : Real(0);
+}
+
+__global__ void k_init_ids(int n, int32_t* id)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) id[i] = i;
+}
+
+template <int DIM>
+__global__ void k_sigma0(int n, const double* __restrict__ h, const double* __restrict__ m, double rho0,
+                         double* __restrict__ s0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double vol = m[i] / rho0;
+    const double dp = DIM == 2 ? sqrt(vol) : cbrt(vol);
+    const double ratio = h[i] / dp;            // smoothing length in units of dp
+    const int K = (int)ceil(2.0 * ratio) + 1;
+    const double inv = 1.0 / ratio;
+    double s = 0.0;
+    const int kz0 = DIM == 3 ? -K : 0, kz1 = DIM == 3 ? K : 0;
+    for (int kz = kz0; kz <= kz1; ++kz)
+        for (int ky = -K; ky <= K; ++ky)
+            for (int kx = -K; kx <= K; ++kx) {
+                double r = sqrt((double)(kx * kx + ky * ky + kz * kz));
+                if (r < 2.0 * ratio) s += wendland_W<DIM, double>(r, inv);
+            }
+    s0[i] = s / (DIM == 2 ? dp * dp : dp * dp * dp);
+}
+
+template <typename V4>
+__global__ void k_rho_out(int n, const V4* __restrict__ vr, const int8_t* __restrict__ kind,
+                          const int32_t* __restrict__ id, double rho0, double* __restrict__ dst)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    dst[id[k]] = kind[k] ? rho0 : rho0 + (double)vr[k].w;
+}
+
+template <typename Real>
+__global__ void k_scalar_out(int n, const Real* __restrict__ src, const int32_t* __restrict__ id,
+                             double* __restrict__ dst)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[id[k]] = (double)src[k];
+}
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+cudaError_t launch_vec_in(int prec, int dim, int n, const double* src3, void* dst, cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        if (dim == 2) k_vec_in<double, 2><<<nblk(n, T), T, 0, st>>>(n, src3, (double*)dst);
+        else k_vec_in<double, 3><<<nblk(n, T), T, 0, st>>>(n, src3, (double*)dst);
+    } else {
+        if (dim == 2) k_vec_in<float, 2><<<nblk(n, T), T, 0, st>>>(n, src3, (float*)dst);
+        else k_vec_in<float, 3><<<nblk(n, T), T, 0, st>>>(n, src3, (float*)dst);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_out(int prec, int dim, int n, const void* src, const int32_t* id, double* dst3,
+                           cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        if (dim == 2) k_vec_out<double, 2><<<nblk(n, T), T, 0, st>>>(n, (const double*)src, id, dst3);
+        else k_vec_out<double, 3><<<nblk(n, T), T, 0, st>>>(n, (const double*)src, id, dst3);
+    } else {
+        if (dim == 2) k_vec_out<float, 2><<<nblk(n, T), T, 0, st>>>(n, (const float*)src, id, dst3);
+        else k_vec_out<float, 3><<<nblk(n, T), T, 0, st>>>(n, (const float*)src, id, dst3);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walls_velocity(int prec, int dim, int n, const int8_t* kind, const double* vw3, void* v,
+                                  cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        if (dim == 2) k_walls_velocity<double, 2><<<nblk(n, T), T, 0, st>>>(n, kind, vw3, (double*)v);
+        else k_walls_velocity<double, 3><<<nblk(n, T), T, 0, st>>>(n, kind, vw3, (double*)v);
+    } else {
+        if (dim == 2) k_walls_velocity<float, 2><<<nblk(n, T), T, 0, st>>>(n, kind, vw3, (float*)v);
+        else k_walls_velocity<float, 3><<<nblk(n, T), T, 0, st>>>(n, kind, vw3, (float*)v);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_ids(int n, int32_t* id, cudaStream_t st)
+{
+    k_init_ids<<<nblk(n, 256), 256, 0, st>>>(n, id);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma0(int dim, int n, const double* h, const double* m, double rho0, double* s0,
+                          cudaStream_t st)
+{
+    if (dim == 2) k_sigma0<2><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
+    else k_sigma0<3><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, const int32_t* id, double rho0,
+                           double* dst, cudaStream_t st)
+{
+    if (prec == 64) k_rho_out<double4_32a><<<nblk(n, 256), 256, 0, st>>>(n, (const double4_32a*)vr, kind, id, rho0, dst);
+    else k_rho_out<float4><<<nblk(n, 256), 256, 0, st>>>(n, (const float4*)vr, kind, id, rho0, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st)
+{
+    if (prec == 64) k_scalar_out<double><<<nblk(n, 256), 256, 0, st>>>(n, (const double*)src, id, dst);
+    else k_scalar_out<float><<<nblk(n, 256), 256, 0, st>>>(n, (const float*)src, id, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace sphtv

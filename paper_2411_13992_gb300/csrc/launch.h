@@ -1,0 +1,48 @@
+// launch.h -- internal (C++) launchers of the libsphtv kernels.  Each takes
+// the precision (32 or 64) and dimension (2 or 3) at run time and picks the
+// template instantiation.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sphtv {
+
+// k_cells.cu
+cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const double* dt, int drift, const Grid& G,
+                                  int32_t* key, int32_t* count, uint32_t* err, cudaStream_t st);
+size_t scan_temp_elems(int n);
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* tmp, cudaStream_t st,
+                                  int64_t* launches);
+cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int32_t* start, int32_t* cursor,
+                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, cudaStream_t st,
+                                 int64_t* launches);
+cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
+                           const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st);
+
+// k_pair.cu
+int pair_blocks(int n);
+cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
+                           void* vr, const float4* pos4, const int32_t* cell_of, cudaStream_t st);
+cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
+                          const void* vr, const float4* pos4, const int32_t* cell_of, const double* dt, int kick_on,
+                          int write_ad, void* Rout, void* chi, double* partials, cudaStream_t st);
+cudaError_t launch_finalize(int nblocks, const double* partials, const sph_params& P, double* diag, double* dt,
+                            int count_step, cudaStream_t st);
+
+// k_io.cu
+cudaError_t launch_vec_in(int prec, int dim, int n, const double* src3, void* dst, cudaStream_t st);
+cudaError_t launch_vec_out(int prec, int dim, int n, const void* src, const int32_t* id, double* dst3,
+                           cudaStream_t st);
+cudaError_t launch_walls_velocity(int prec, int dim, int n, const int8_t* kind, const double* vw3, void* v,
+                                  cudaStream_t st);
+cudaError_t launch_init_ids(int n, int32_t* id, cudaStream_t st);
+cudaError_t launch_sigma0(int dim, int n, const double* h, const double* m, double rho0, double* s0,
+                          cudaStream_t st);
+cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, const int32_t* id, double rho0,
+                           double* dst, cudaStream_t st);
+cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st);
+
+}  // namespace sphtv

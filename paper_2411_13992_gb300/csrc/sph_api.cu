@@ -1,0 +1,584 @@
+// sph_api.cu -- host implementation of the libsphtv C ABI (include/sphtv.h).
+//
+// The context is a small host object.  Every device buffer is carved out of
+// the caller's workspace; nothing here allocates device memory.  All work is
+// enqueued on the context's stream; the only host waits are in sph_sync,
+// sph_get_diag and sph_get_state (host destinations).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "sphtv.h"
+
+using namespace sphtv;
+
+struct SetPtrs {
+    StateSet<double> d;
+    StateSet<float> f;
+};
+
+struct sph_ctx {
+    sph_params P;
+    int64_t n;
+    int dim, prec;
+    cudaStream_t st;
+    Grid G;
+    Consts<double> K64;
+    Consts<float> K32;
+    SetPtrs set[2];
+    int cur;
+    int32_t *key, *perm_tmp, *perm, *count, *cursor, *start, *scan_tmp;
+    void* vr;
+    float4* pos4;
+    int32_t* cell;
+    void* R;
+    void* chi;
+    double* partials;
+    double* diag;
+    double* dt;
+    uint32_t* err;
+    double* stage;
+    int have_state, have_cells, ad_given;
+    int64_t launches;
+    double host_dt;
+    // per-kernel timing (sph_profile_begin / sph_profile_end)
+    std::vector<cudaEvent_t>* prof_ev;   // [step][class][begin, end]
+    std::vector<int>* prof_used;         // [step][class] 0/1
+    int prof_max, prof_step;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Carver {
+    char* base;
+    size_t off;
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + kAlign - 1) & ~(kAlign - 1);
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+sph_status check_params(const sph_params* p, int64_t n)
+{
+    if (!p || n < 1 || n > (int64_t)0x7fffffff) return SPH_ERR_ARG;
+    if (p->dim != 2 && p->dim != 3) return SPH_ERR_ARG;
+    if (p->precision != 32 && p->precision != 64) return SPH_ERR_ARG;
+    if (!(p->rho0 > 0) || !(p->c0 > 0) || !(p->eta >= 0)) return SPH_ERR_ARG;
+    if (!(p->h_min > 0) || !(p->h_max >= p->h_min)) return SPH_ERR_ARG;
+    if (p->tv_mode < 0 || p->tv_mode > 2 || p->tv_h < 0 || p->tv_h > 1 || p->h_pair < 0 || p->h_pair > 1)
+        return SPH_ERR_ARG;
+    if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
+    for (int d = 0; d < p->dim; ++d) {
+        if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
+        double nc = std::floor(p->L[d] / (2.0 * p->h_max));
+        if (p->periodic[d] && nc < 3) return SPH_ERR_ARG;
+        if (nc > 1 << 20) return SPH_ERR_ARG;
+    }
+    return SPH_OK;
+}
+
+Grid make_grid(const sph_params* p)
+{
+    Grid G;
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < p->dim) {
+            int nc = (int)std::floor(p->L[d] / (2.0 * p->h_max));
+            if (nc < 1) nc = 1;
+            G.nc[d] = nc;
+            G.periodic[d] = p->periodic[d] ? 1 : 0;
+            G.lo[d] = p->lo[d];
+            G.L[d] = p->L[d];
+            G.hi[d] = p->lo[d] + p->L[d];
+            G.half_L[d] = 0.5 * p->L[d];
+            G.edge[d] = p->L[d] / nc;
+            G.inv_edge[d] = (double)nc / p->L[d];
+        } else {
+            G.nc[d] = 1;
+            G.periodic[d] = 0;
+            G.lo[d] = 0.0;
+            G.L[d] = 1.0;
+            G.hi[d] = 1.0;
+            G.half_L[d] = 0.5;
+            G.edge[d] = 1.0;
+            G.inv_edge[d] = 1.0;
+        }
+        G.edgef[d] = (float)G.edge[d];
+        ncell *= G.nc[d];
+    }
+    G.ncell = (int)ncell;
+    return G;
+}
+
+template <typename Real>
+Consts<Real> make_consts(const sph_params* p)
+{
+    Consts<Real> K;
+    double c2 = p->c0 * p->c0;
+    K.rho0 = (Real)p->rho0;
+    K.c = (Real)p->c0;
+    K.c2 = (Real)c2;
+    K.eta = (Real)p->eta;
+    K.two_eta = (Real)(2.0 * p->eta);
+    K.beta_slope = (Real)p->riemann_eta;
+    K.inv_c = (Real)(1.0 / p->c0);
+    for (int d = 0; d < 3; ++d) K.g[d] = (Real)p->g[d];
+    K.h_min = (Real)p->h_min;
+    K.tv_xi = (Real)p->tv_xi;
+    K.tv_C = (Real)p->tv_C;
+    K.tv_thresh = (Real)p->tv_thresh;
+    K.tv_mode = p->tv_mode;
+    K.tv_h_particle = p->tv_h == SPH_TVH_PARTICLE;
+    K.h_pair_max = p->h_pair == SPH_HPAIR_MAX;
+    K.kahan = p->kahan;
+    return K;
+}
+
+// Lay the buffers out in the workspace (base == nullptr: only measure).
+size_t carve(sph_ctx* c, char* base)
+{
+    Carver W{base, 0};
+    const size_t n = (size_t)c->n;
+    const int D = c->dim;
+    const size_t rs = c->prec == 64 ? 8 : 4;
+    const size_t nc1 = (size_t)c->G.ncell + 1;
+    for (int s = 0; s < 2; ++s) {
+        double* x = W.take<double>(D * n);
+        char* v = W.take<char>(D * n * rs);
+        char* a = W.take<char>(D * n * rs);
+        char* dr = W.take<char>(D * n * rs);
+        double* h = W.take<double>(n);
+        double* m = W.take<double>(n);
+        double* s0 = W.take<double>(n);
+        int32_t* id = W.take<int32_t>(n);
+        int8_t* kind = W.take<int8_t>(n);
+        c->set[s].d = StateSet<double>{x, (double*)v, (double*)a, (double*)dr, h, m, s0, id, kind};
+        c->set[s].f = StateSet<float>{x, (float*)v, (float*)a, (float*)dr, h, m, s0, id, kind};
+    }
+    c->key = W.take<int32_t>(n);
+    c->perm_tmp = W.take<int32_t>(n);
+    c->perm = W.take<int32_t>(n);
+    c->count = W.take<int32_t>(nc1);
+    c->cursor = W.take<int32_t>(nc1);
+    c->start = W.take<int32_t>(nc1);
+    c->scan_tmp = W.take<int32_t>(scan_temp_elems((int)nc1));
+    c->vr = W.take<char>(n * 4 * rs);
+    c->pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
+    c->cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
+    c->R = W.take<char>(D * n * rs);
+    c->chi = W.take<char>(n * rs);
+    c->partials = W.take<double>((size_t)pair_blocks((int)n) * kNPart);
+    c->diag = W.take<double>(DG_COUNT);
+    c->dt = W.take<double>(1);
+    c->err = W.take<uint32_t>(4);
+    c->stage = W.take<double>(3 * n);
+    return (W.off + kAlign - 1) & ~(kAlign - 1);
+}
+
+void* cur_set(sph_ctx* c) { return c->prec == 64 ? (void*)&c->set[c->cur].d : (void*)&c->set[c->cur].f; }
+void* other_set(sph_ctx* c) { return c->prec == 64 ? (void*)&c->set[1 - c->cur].d : (void*)&c->set[1 - c->cur].f; }
+const void* consts(sph_ctx* c) { return c->prec == 64 ? (const void*)&c->K64 : (const void*)&c->K32; }
+
+#define SPH_CU(call)                                 \
+    do {                                             \
+        if ((call) != cudaSuccess) return SPH_ERR_CUDA; \
+    } while (0)
+
+// Event marks around a kernel class when a profile is open and the current
+// step is within its range (the step index advances in sph_step).
+inline cudaError_t prof_mark(sph_ctx* c, int cls, int end)
+{
+    if (!c->prof_ev || c->prof_step < 0 || c->prof_step >= c->prof_max) return cudaSuccess;
+    size_t k = ((size_t)c->prof_step * SPH_K_NCLASS + cls);
+    if (!end) (*c->prof_used)[k] = 1;
+    return cudaEventRecord((*c->prof_ev)[2 * k + end], c->st);
+}
+
+#define SPH_MARK(cls, end) SPH_CU(prof_mark(c, cls, end))
+
+// Kick-drift (optional), cell keys, counting sort, permute.
+sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
+{
+    const int n = (int)c->n;
+    const size_t nc1 = (size_t)c->G.ncell + 1;
+    SPH_MARK(SPH_K_KICKDRIFT, 0);
+    SPH_CU(cudaMemsetAsync(c->count, 0, nc1 * sizeof(int32_t), c->st));
+    SPH_CU(cudaMemsetAsync(c->cursor, 0, nc1 * sizeof(int32_t), c->st));
+    SPH_CU(launch_kick_drift_key(c->prec, c->dim, n, cur_set(c), c->dt, drift, c->G, c->key, c->count, c->err, c->st));
+    ++c->launches;
+    SPH_MARK(SPH_K_KICKDRIFT, 1);
+    SPH_MARK(SPH_K_SCAN, 0);
+    SPH_CU(launch_exclusive_scan(c->count, c->start, (int)nc1, c->scan_tmp, c->st, &c->launches));
+    SPH_MARK(SPH_K_SCAN, 1);
+    const int32_t* id = c->prec == 64 ? c->set[c->cur].d.id : c->set[c->cur].f.id;
+    SPH_MARK(SPH_K_ORDER, 0);
+    SPH_CU(launch_scatter_order(n, c->G.ncell, c->key, c->start, c->cursor, c->perm_tmp, id, c->perm, c->st,
+                                &c->launches));
+    SPH_MARK(SPH_K_ORDER, 1);
+    SPH_MARK(SPH_K_PERMUTE, 0);
+    SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
+                          carry_ad, c->st));
+    ++c->launches;
+    SPH_MARK(SPH_K_PERMUTE, 1);
+    c->cur = 1 - c->cur;
+    return SPH_OK;
+}
+
+// Density, fused forces (+ closing kick), reductions and dt.
+sph_status run_forces(sph_ctx* c, int kick_on, int write_ad, int count_step)
+{
+    const int n = (int)c->n;
+    SPH_MARK(SPH_K_DENSITY, 0);
+    SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->st));
+    SPH_MARK(SPH_K_DENSITY, 1);
+    SPH_MARK(SPH_K_FORCES, 0);
+    SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->dt,
+                         kick_on, write_ad, c->R, c->chi, c->partials, c->st));
+    SPH_MARK(SPH_K_FORCES, 1);
+    SPH_MARK(SPH_K_FINALIZE, 0);
+    SPH_CU(launch_finalize(pair_blocks(n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+    SPH_MARK(SPH_K_FINALIZE, 1);
+    c->launches += 3;
+    return SPH_OK;
+}
+
+bool is_host_ptr(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_default_params(sph_params* p)
+{
+    if (!p) return SPH_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->precision = 64;
+    p->tv_mode = SPH_TV_LIMITED;
+    for (int d = 0; d < 3; ++d) p->L[d] = 1.0;
+    p->rho0 = 1.0;
+    p->c0 = 10.0;
+    p->riemann_eta = 3.0;
+    p->tv_xi = -0.2;
+    p->tv_C = 1.0e3;
+    p->tv_thresh = 5.0e-4;
+    p->cfl_ad = 0.25;
+    p->cfl_ac = 0.6;
+    p->tv_h = SPH_TVH_MIN;
+    p->h_pair = SPH_HPAIR_MEAN;
+    p->kahan = 1;
+    return SPH_OK;
+}
+
+sph_status sph_query_workspace(const sph_params* p, int64_t n, size_t* bytes)
+{
+    sph_status s = check_params(p, n);
+    if (s != SPH_OK) return s;
+    if (!bytes) return SPH_ERR_ARG;
+    sph_ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.P = *p;
+    c.n = n;
+    c.dim = p->dim;
+    c.prec = p->precision;
+    c.G = make_grid(p);
+    *bytes = carve(&c, nullptr);
+    return SPH_OK;
+}
+
+sph_status sph_create(const sph_params* p, int64_t n, void* workspace, size_t bytes, void* stream, sph_ctx** out)
+{
+    if (!out) return SPH_ERR_ARG;
+    *out = nullptr;
+    sph_status s = check_params(p, n);
+    if (s != SPH_OK) return s;
+    if (!workspace || ((uintptr_t)workspace & (kAlign - 1))) return SPH_ERR_WORKSPACE;
+    sph_ctx* c = new (std::nothrow) sph_ctx;
+    if (!c) return SPH_ERR_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->P = *p;
+    c->n = n;
+    c->dim = p->dim;
+    c->prec = p->precision;
+    c->st = (cudaStream_t)stream;
+    c->G = make_grid(p);
+    c->K64 = make_consts<double>(p);
+    c->K32 = make_consts<float>(p);
+    size_t need = carve(c, nullptr);
+    if (bytes < need) {
+        delete c;
+        return SPH_ERR_WORKSPACE;
+    }
+    carve(c, (char*)workspace);
+    if (cudaMemsetAsync(c->err, 0, 4 * sizeof(uint32_t), c->st) != cudaSuccess ||
+        cudaMemsetAsync(c->diag, 0, DG_COUNT * sizeof(double), c->st) != cudaSuccess) {
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    c->host_dt = p->fixed_dt;
+    if (cudaMemcpyAsync(c->dt, &c->host_dt, sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const double* a, const double* dr,
+                         const double* h, const double* m, const int8_t* kind, const double* vw, const double* sigma0)
+{
+    if (!c || !x || !v || !h || !m) return SPH_ERR_ARG;
+    if ((a == nullptr) != (dr == nullptr)) return SPH_ERR_ARG;
+    const size_t n = (size_t)c->n;
+    const size_t vb = 3 * n * sizeof(double);
+    c->cur = 0;
+    StateSet<double>& Sd = c->set[0].d;
+    void* S = cur_set(c);
+    void* sv = c->prec == 64 ? (void*)c->set[0].d.v : (void*)c->set[0].f.v;
+    void* sa = c->prec == 64 ? (void*)c->set[0].d.a : (void*)c->set[0].f.a;
+    void* sdr = c->prec == 64 ? (void*)c->set[0].d.dr : (void*)c->set[0].f.dr;
+    (void)S;
+    const size_t rs = c->prec == 64 ? 8 : 4;
+    SPH_CU(cudaMemcpyAsync(c->stage, x, vb, cudaMemcpyDefault, c->st));
+    SPH_CU(launch_vec_in(64, c->dim, (int)n, c->stage, Sd.x, c->st));
+    SPH_CU(cudaMemcpyAsync(c->stage, v, vb, cudaMemcpyDefault, c->st));
+    SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sv, c->st));
+    if (a) {
+        SPH_CU(cudaMemcpyAsync(c->stage, a, vb, cudaMemcpyDefault, c->st));
+        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sa, c->st));
+        SPH_CU(cudaMemcpyAsync(c->stage, dr, vb, cudaMemcpyDefault, c->st));
+        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sdr, c->st));
+        c->launches += 2;
+    } else {
+        SPH_CU(cudaMemsetAsync(sa, 0, c->dim * n * rs, c->st));
+        SPH_CU(cudaMemsetAsync(sdr, 0, c->dim * n * rs, c->st));
+    }
+    SPH_CU(cudaMemcpyAsync(Sd.h, h, n * sizeof(double), cudaMemcpyDefault, c->st));
+    SPH_CU(cudaMemcpyAsync(Sd.m, m, n * sizeof(double), cudaMemcpyDefault, c->st));
+    if (kind) SPH_CU(cudaMemcpyAsync(Sd.kind, kind, n, cudaMemcpyDefault, c->st));
+    else SPH_CU(cudaMemsetAsync(Sd.kind, 0, n, c->st));
+    if (vw) SPH_CU(cudaMemcpyAsync(c->stage, vw, vb, cudaMemcpyDefault, c->st));
+    SPH_CU(launch_walls_velocity(c->prec, c->dim, (int)n, Sd.kind, vw ? c->stage : nullptr, sv, c->st));
+    if (sigma0) SPH_CU(cudaMemcpyAsync(Sd.s0, sigma0, n * sizeof(double), cudaMemcpyDefault, c->st));
+    else {
+        SPH_CU(launch_sigma0(c->dim, (int)n, Sd.h, Sd.m, c->P.rho0, Sd.s0, c->st));
+        ++c->launches;
+    }
+    SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
+    c->launches += 4;
+    c->have_state = 1;
+    c->have_cells = 0;
+    c->ad_given = a != nullptr;
+    return SPH_OK;
+}
+
+sph_status sph_build_cells(sph_ctx* c)
+{
+    if (!c) return SPH_ERR_ARG;
+    if (!c->have_state) return SPH_ERR_STATE;
+    sph_status s = run_sort(c, 0, c->ad_given);
+    if (s != SPH_OK) return s;
+    s = run_forces(c, 0, !c->ad_given, 0);
+    if (s != SPH_OK) return s;
+    c->have_cells = 1;
+    return SPH_OK;
+}
+
+sph_status sph_step(sph_ctx* c, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return SPH_ERR_ARG;
+    if (!c->have_cells) return SPH_ERR_STATE;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        sph_status s = run_sort(c, 1, 0);
+        if (s != SPH_OK) return s;
+        s = run_forces(c, 1, 1, 1);
+        if (s != SPH_OK) return s;
+        if (c->prof_ev) ++c->prof_step;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_set_dt(sph_ctx* c, double dt)
+{
+    if (!c || !(dt > 0) || !std::isfinite(dt)) return SPH_ERR_ARG;
+    c->host_dt = dt;
+    SPH_CU(cudaMemcpyAsync(c->dt, &c->host_dt, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    SPH_CU(cudaStreamSynchronize(c->st));
+    return SPH_OK;
+}
+
+sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr, double* rho)
+{
+    if (!c) return SPH_ERR_ARG;
+    if (!c->have_state) return SPH_ERR_STATE;
+    const int n = (int)c->n;
+    const size_t vb = 3 * (size_t)n * sizeof(double);
+    const StateSet<double>& Sd = c->set[c->cur].d;
+    const void* sv = c->prec == 64 ? (void*)c->set[c->cur].d.v : (void*)c->set[c->cur].f.v;
+    const void* sa = c->prec == 64 ? (void*)c->set[c->cur].d.a : (void*)c->set[c->cur].f.a;
+    const void* sdr = c->prec == 64 ? (void*)c->set[c->cur].d.dr : (void*)c->set[c->cur].f.dr;
+    bool host = false;
+    struct Out { double* dst; const void* src; int prec; } outs[4] = {{x, Sd.x, 64}, {v, sv, c->prec},
+                                                                    {a, sa, c->prec}, {dr, sdr, c->prec}};
+    for (auto& o : outs) {
+        if (!o.dst) continue;
+        SPH_CU(launch_vec_out(o.prec, c->dim, n, o.src, Sd.id, c->stage, c->st));
+        SPH_CU(cudaMemcpyAsync(o.dst, c->stage, vb, cudaMemcpyDefault, c->st));
+        ++c->launches;
+        host = host || is_host_ptr(o.dst);
+    }
+    if (rho) {
+        if (!c->have_cells) return SPH_ERR_STATE;
+        SPH_CU(launch_rho_out(c->prec, n, c->vr, Sd.kind, Sd.id, c->P.rho0, c->stage, c->st));
+        SPH_CU(cudaMemcpyAsync(rho, c->stage, (size_t)n * sizeof(double), cudaMemcpyDefault, c->st));
+        ++c->launches;
+        host = host || is_host_ptr(rho);
+    }
+    if (host) SPH_CU(cudaStreamSynchronize(c->st));
+    return SPH_OK;
+}
+
+sph_status sph_get_diag(sph_ctx* c, sph_diag* out)
+{
+    if (!c || !out) return SPH_ERR_ARG;
+    double buf[DG_COUNT];
+    SPH_CU(cudaMemcpyAsync(buf, c->diag, sizeof(buf), cudaMemcpyDeviceToHost, c->st));
+    SPH_CU(cudaStreamSynchronize(c->st));
+    out->mass = buf[DG_MASS];
+    for (int d = 0; d < 3; ++d) out->momentum[d] = buf[DG_MOM + d];
+    out->kinetic = buf[DG_KE];
+    out->vmax = buf[DG_VMAX];
+    out->vt_max = buf[DG_VTMAX];
+    out->dr_max = buf[DG_DRMAX];
+    out->n_chi = buf[DG_NCHI];
+    out->dt = buf[DG_DT];
+    out->dt_next = buf[DG_DTNEXT];
+    out->steps = buf[DG_STEPS];
+    return SPH_OK;
+}
+
+sph_status sph_sync(sph_ctx* c)
+{
+    if (!c) return SPH_ERR_ARG;
+    uint32_t e = 0;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemcpy(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return SPH_ERR_CUDA;
+    if (!e) return SPH_OK;
+    if (cudaMemset(c->err, 0, sizeof(uint32_t)) != cudaSuccess) return SPH_ERR_CUDA;
+    if (e & ERRB_NAN) return SPH_ERR_NAN;
+    if (e & ERRB_DOMAIN) return SPH_ERR_DOMAIN;
+    return SPH_ERR_OVERFLOW;
+}
+
+static void prof_free(sph_ctx* c)
+{
+    if (!c->prof_ev) return;
+    for (cudaEvent_t e : *c->prof_ev)
+        if (e) cudaEventDestroy(e);
+    delete c->prof_ev;
+    delete c->prof_used;
+    c->prof_ev = nullptr;
+    c->prof_used = nullptr;
+}
+
+sph_status sph_profile_begin(sph_ctx* c, int32_t max_steps)
+{
+    if (!c || max_steps < 1) return SPH_ERR_ARG;
+    prof_free(c);
+    size_t nev = 2 * (size_t)max_steps * SPH_K_NCLASS;
+    c->prof_ev = new (std::nothrow) std::vector<cudaEvent_t>(nev, nullptr);
+    c->prof_used = new (std::nothrow) std::vector<int>((size_t)max_steps * SPH_K_NCLASS, 0);
+    if (!c->prof_ev || !c->prof_used) {
+        prof_free(c);
+        return SPH_ERR_ARG;
+    }
+    for (auto& e : *c->prof_ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            prof_free(c);
+            return SPH_ERR_CUDA;
+        }
+    }
+    c->prof_max = max_steps;
+    c->prof_step = 0;
+    return SPH_OK;
+}
+
+sph_status sph_profile_end(sph_ctx* c, double* ms, int64_t* count)
+{
+    if (!c) return SPH_ERR_ARG;
+    if (!c->prof_ev) return SPH_ERR_STATE;
+    double acc[SPH_K_NCLASS] = {0};
+    int64_t cnt[SPH_K_NCLASS] = {0};
+    sph_status st = SPH_OK;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) st = SPH_ERR_CUDA;
+    int steps = c->prof_step < c->prof_max ? c->prof_step : c->prof_max;
+    for (int s = 0; s < steps && st == SPH_OK; ++s)
+        for (int k = 0; k < SPH_K_NCLASS; ++k) {
+            size_t i = (size_t)s * SPH_K_NCLASS + k;
+            if (!(*c->prof_used)[i]) continue;
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, (*c->prof_ev)[2 * i], (*c->prof_ev)[2 * i + 1]) != cudaSuccess) {
+                st = SPH_ERR_CUDA;
+                break;
+            }
+            acc[k] += t;
+            ++cnt[k];
+        }
+    prof_free(c);
+    for (int k = 0; k < SPH_K_NCLASS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (count) count[k] = cnt[k];
+    }
+    return st;
+}
+
+const char* sph_kernel_class_name(int32_t k)
+{
+    static const char* names[SPH_K_NCLASS] = {"kick_drift_key", "scan", "scatter_order", "permute", "density",
+                                              "forces", "finalize"};
+    return (k >= 0 && k < SPH_K_NCLASS) ? names[k] : "?";
+}
+
+void sph_destroy(sph_ctx* c)
+{
+    if (!c) return;
+    prof_free(c);
+    delete c;
+}
+
+const char* sph_status_str(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA error";
+    case SPH_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case SPH_ERR_OVERFLOW: return "cell capacity overflow";
+    case SPH_ERR_NAN: return "non-finite particle state";
+    case SPH_ERR_DOMAIN: return "particle outside the domain";
+    case SPH_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""Shared helpers of the GPU parity tests: run the CUDA library and the FP64
+oracle on the same seeded inputs and compare field by field."""
+import numpy as np
+
+import oracle
+import paper_2411_13992_gb300 as sph
+
+
+def oracle_params(c, **kw):
+    return oracle.make_params(c["dim"], c["lo"], c["L"], c["periodic"], c["rho0"], c["c"], c["eta"], c["h_min"],
+                              g=c.get("g", (0, 0, 0)), u_ref=c["u_ref"], **kw)
+
+
+_ORC_KEYS = {"tv_mode": "tv_mode", "riemann_eta": "riemann_eta", "tv_xi": "tv_xi"}
+
+
+def lib_overrides(**kw):
+    out = {}
+    for k, v in kw.items():
+        if k == "tv_h_per_particle":
+            out["tv_h"] = int(bool(v))
+        elif k == "h_pair_max":
+            out["h_pair"] = int(bool(v))
+        else:
+            out[k] = v
+    return out
+
+
+def normwise(a, b):
+    """max_i |a_i - b_i| / max_i |b_i| over rows (vectors) or entries."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.ndim == 2:
+        num = np.linalg.norm(a - b, axis=1).max()
+        den = np.linalg.norm(b, axis=1).max()
+    else:
+        num = np.abs(a - b).max()
+        den = np.abs(b).max()
+    return num / den if den > 0 else num
+
+
+def oracle_trajectory(c, nsteps, keep, mode="cells", **kw):
+    """FP64 oracle run from the case's initial state; returns dt0 and the
+    states at the steps listed in ``keep`` (step 0 = after the initial force
+    pass)."""
+    P = oracle_params(c, **kw)
+    s0 = oracle.sigma0_for(c, c["dim"])
+    fp = oracle.force_pass(P, c, c["x"], c["v"], s0, mode=mode)
+    st = {"x": c["x"].copy(), "v": c["v"].copy(), "a": fp["a"], "dr": fp["dr"], "rho": fp["rho"]}
+    dt = oracle.time_step(P, st["v"], c["kind"])
+    out = {}
+    if 0 in keep:
+        out[0] = st
+    for k in range(1, nsteps + 1):
+        st = oracle.step(P, c, st, s0, dt, mode=mode)
+        if k in keep:
+            out[k] = st
+    return dt, out, P, s0
+
+
+def gpu_one_step(c, state, dt, precision=64, **kw):
+    """Load ``state`` (x, v, a, dr) into the library, take one step of size dt
+    and return the library's state and diagnostics."""
+    sim = sph.Simulation(c, precision=precision, fixed_dt=dt, **lib_overrides(**kw))
+    try:
+        sim.set_state(x=state["x"], v=state["v"], a=state["a"], dr=state["dr"])
+        sim.build_cells()
+        sim.step(1)
+        sim.sync()
+        return sim.get_state(), sim.diag()
+    finally:
+        sim.close()
+
+
+def compare_step(c, state, dt, s0, P, precision=64, mode="cells", **kw):
+    """One step from the same input state on both sides; normwise relative
+    errors per field (displacement for x)."""
+    ref = oracle.step(P, c, state, s0, dt, mode=mode)
+    got, diag = gpu_one_step(c, state, dt, precision, **kw)
+    fl = c["kind"] == 0
+    disp_ref = ref["x"] - state["x"]
+    disp_got = got["x"] - state["x"]
+    L = np.array(c["L"])
+    for arr in (disp_ref, disp_got):      # periodic wrap of the displacement
+        for d in range(c["dim"]):
+            if c["periodic"][d]:
+                arr[:, d] -= L[d] * np.round(arr[:, d] / L[d])
+    err = {
+        "x": normwise(disp_got[fl], disp_ref[fl]),
+        "v": normwise(got["v"][fl], ref["v"][fl]),
+        "a": normwise(got["a"][fl], ref["a"][fl]),
+        "rho": normwise(got["rho"][fl], ref["rho"][fl]),
+        "drho": normwise(got["rho"][fl] - c["rho0"], ref["rho"][fl] - c["rho0"]),
+        "dr_abs": float(np.abs(got["dr"][fl] - ref["dr"][fl]).max()),
+        "dr": normwise(got["dr"][fl], ref["dr"][fl]),
+    }
+    od = oracle.diagnostics(P, ref["v"], c["m"], c["kind"], ref["dr"], ref["chi"], dt)
+    err["ke"] = abs(diag["ke"] - od["ke"]) / od["ke"] if od["ke"] else abs(diag["ke"])
+    err["n_chi_ref"] = int((ref["chi"][fl] > 0).sum())
+    err["n_chi_got"] = diag["n_chi"]
+    s = P.h_min ** 2 * (ref["R"][fl] ** 2).sum(axis=1)
+    err["near_threshold"] = int((np.abs(s - P.tv_thresh) < 1e-9 * P.tv_thresh).sum())
+    return err, ref, got

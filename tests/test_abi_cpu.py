@@ -1,0 +1,115 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/sphtv.h declares, its structs have the layout the
+Python binding assumes, and host-side argument checks reject bad input
+before any device work (no GPU is touched here)."""
+import ctypes
+import json
+import os
+import subprocess
+
+import pytest
+
+import paper_2411_13992_gb300 as sph
+from paper_2411_13992_gb300 import _build, cases
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return sph.load()
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    declared = sph.declared_symbols()
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(lib, name), name
+    for required in ("sph_create", "sph_build_cells", "sph_step", "sph_query_workspace", "sph_set_state",
+                     "sph_get_state", "sph_sync", "sph_destroy"):
+        assert required in declared
+
+
+def test_library_targets_sm_103a_only():
+    with open(_build.__file__) as f:
+        src = f.read()
+    assert "arch=compute_103a,code=sm_103a" in src
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layout_matches_the_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "sphtv.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sph_params), offsetof(sph_params, lo),
+         offsetof(sph_params, fixed_dt), offsetof(sph_params, tv_h), offsetof(sph_params, kahan),
+         sizeof(sph_diag), offsetof(sph_diag, steps));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", _build.INCLUDE, str(prog), "-o", str(exe)], check=True)
+    got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    P, D = sph.SphParams, sph.SphDiag
+    want = [ctypes.sizeof(P), P.lo.offset, P.fixed_dt.offset, P.tv_h.offset, P.kahan.offset, ctypes.sizeof(D),
+            D.steps.offset]
+    assert got == want
+
+
+def test_default_params_are_the_papers_constants(lib):
+    with open(os.path.join(GOLD, "paper_constants.json")) as f:
+        g = json.load(f)
+    p = sph.sph_default_params()
+    for k in ("riemann_eta", "tv_C", "tv_thresh", "tv_xi", "cfl_ad", "cfl_ac"):
+        assert getattr(p, k) == g[k]["value"], k
+    assert p.tv_mode == sph.TV_LIMITED and p.tv_h == sph.TVH_MIN and p.kahan == 1
+
+
+def test_workspace_query_and_argument_checks(lib):
+    c = cases.tgv2d(20)
+    p = sph.params_from_case(c, 64)
+    b64 = sph.sph_query_workspace(p, c["n"])
+    b64_big = sph.sph_query_workspace(p, 4 * c["n"])
+    assert 0 < b64 < b64_big
+    p32 = sph.params_from_case(c, 32)
+    assert 0 < sph.sph_query_workspace(p32, c["n"])
+    bad = [
+        dict(dim=4), dict(precision=16), dict(rho0=0.0), dict(c0=-1.0), dict(eta=-1.0), dict(h_min=0.0),
+        dict(h_max=0.5 * c["h_min"]), dict(tv_mode=3), dict(fixed_dt=-1.0),
+        dict(h_max=0.3),          # fewer than 3 cells along a periodic axis
+    ]
+    for kw in bad:
+        q = sph.params_from_case(c, 64)
+        for k, v in kw.items():
+            setattr(q, k, v)
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_query_workspace(q, c["n"])
+        assert e.value.status == 1, kw
+    with pytest.raises(sph.SphError):
+        sph.sph_query_workspace(p, 0)
+
+
+def test_create_rejects_bad_workspace_without_touching_it(lib):
+    c = cases.tgv2d(20)
+    p = sph.params_from_case(c, 64)
+    need = sph.sph_query_workspace(p, c["n"])
+    for ptr, nbytes in ((0, need), (0x1000 + 8, need), (0x100000, need - 256)):
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_create(p, c["n"], ptr, nbytes, 0)
+        assert e.value.status == 3
+
+
+def test_null_context_and_status_strings(lib):
+    for fn in (lib.sph_build_cells, lib.sph_sync):
+        assert fn(None) == 1
+    assert lib.sph_step(None, 1) == 1
+    assert lib.sph_set_dt(None, 1.0) == 1
+    assert lib.sph_get_diag(None, None) == 1
+    for s in range(8):
+        assert sph.sph_status_str(s) not in ("", "unknown status")
+    assert sph.sph_status_str(99) == "unknown status"
+    assert lib.sph_launch_count(None) == -1
