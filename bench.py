@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Throughput of the transport-velocity WCSPH kick-drift-kick step on GB300.
+
+Workload: 3-D Taylor-Green vortex, periodic [0, 2 pi]^3, 128^3 = 2,097,152
+particles on a jittered lattice, h = 1.3 dp, Re = 1600, c0 = 10 (synthetic,
+seeded).  One step = kick + drift + cell sort + density + fused pair pass
+(Riemann pressure, viscous, limited transport-velocity correction) + closing
+kick + FP64 reductions + dt, all in libsphtv's CUDA kernels.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  value = particle-steps/s of the FP32 form
+over all ranks (each rank steps its own replica; the method is not sharded,
+so N > 1 runs independent replicas, weak scaling).  The FP64 form is timed
+too and reported beside it.  --impl reference times the FP64 CPU oracle on
+the host cores instead (same metric, a bounded sample of the workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (3D TGV 2.1M, FP32 vs FP64 on GB300); adjoint/forward time"
+UNIT = "particle-steps/s"
+WORKLOAD = "3-D Taylor-Green vortex 128^3 = 2,097,152 particles, periodic [0,2pi]^3, Re=1600, h=1.3dp, c0=10"
+
+# Algorithmic cost of the fused pair kernel (k_forces, FP32 form), per ordered
+# interacting pair (i, j), counted from the formulas it evaluates (an FMA is
+# 2 flops; sqrt, reciprocal and division count 1 each):
+#   pair vector and r^2 11, sqrt 1, h_ij and 1/h_ij 3, W'(r) 11,
+#   rho_j and p_j 2, 1/r 1, e_ij and U_l, U_r 15, dU and beta 5, rho_bar 2,
+#   P* 7, 1/(rho_i rho_j) 2, c_p 3, c_v 4, V_j 1, W'/r 1,
+#   per axis: grad W 1, pressure+viscous increment 4, residual increment 1
+#   (x3 = 18), Kahan compensation 4 per accumulator (x6 = 24)          -> 111
+FLOPS_PER_PAIR_FP32 = 111
+# Algorithmic bytes of k_forces per particle (FP32 form, 3-D): read the
+# particle's float4 position + h and float4 {v, rho - rho0} (32 B), mass and
+# kind (9 B), cell index (4 B); write a, dr, v, R (48 B), chi (4 B).  Each
+# neighbour's data is counted once (it is some other particle's own data).
+BYTES_PER_PARTICLE_FORCES = 97
+# Measured-peak fallbacks (used only when MEASURED_PEAKS.json is absent).
+FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES_PER_SM, FP64_LANES_PER_SM = 152, 128, 2
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------ clocks sampler
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if _isnum(r[1])]
+        smax = [float(r[2]) for r in rows if _isnum(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if _isnum(r[3])), default=None)}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+def _gpu_index(torch, dev):
+    """nvidia-smi index of torch device ``dev`` (matched by PCI bus id)."""
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%02x:%02x" % (props.pci_bus_id, props.pci_device_id)
+        out = subprocess.run(["nvidia-smi", "--query-gpu=index,pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout
+        for line in out.strip().splitlines():
+            idx, pci = [t.strip() for t in line.split(",")]
+            if pci.lower().endswith(bus + ".0"):
+                return int(idx)
+    except Exception:  # noqa: BLE001 - best effort
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[0].strip().isdigit():
+        return int(vis.split(",")[0])
+    return dev
+
+
+# ------------------------------------------------------------- distributed
+
+def _dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(value: float, torch=None, dist=None) -> float:
+    """Maximum of a float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, torch=None, dist=None) -> float:
+    if dist is None or not dist.is_initialized():
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_rate(n_side: int, steps: int, warmup: int, threads: int):
+    """FP64 CPU oracle on a 3-D Taylor-Green of n_side^3 particles (same h/dp,
+    same neighbour count per particle as the workload): particle-steps/s over
+    ``steps`` timed steps after ``warmup`` untimed ones."""
+    import oracle
+    from paper_2411_13992_gb300 import cases
+    oracle.build()
+    oracle.set_threads(threads)
+    c = cases.tgv3d(n_side)
+    P = oracle.make_params(3, c["lo"], c["L"], c["periodic"], c["rho0"], c["c"], c["eta"], c["h_min"],
+                           u_ref=c["u_ref"])
+    s0 = oracle.sigma0_for(c, 3)
+    fp = oracle.force_pass(P, c, c["x"], c["v"], s0)
+    st = {"x": c["x"], "v": c["v"], "a": fp["a"], "dr": fp["dr"]}
+    dt = oracle.time_step(P, c["v"], c["kind"])
+    for _ in range(warmup):
+        st = oracle.step(P, c, st, s0, dt)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = oracle.step(P, c, st, s0, dt)
+    el = time.perf_counter() - t0
+    return c["n"] * steps / el, el, c["n"]
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    n_side = args.ref_n
+    rate, el, n = oracle_rate(n_side, args.steps, args.warmup, threads)
+    sample = ("FP64 oracle, cell-list neighbours, OpenMP over particles; 3-D Taylor-Green %d^3 = %d particles "
+              "(same h/dp and neighbours per particle as the 128^3 workload), %d timed steps after %d warm-up"
+              % (n_side, n, args.steps, args.warmup))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "%d^3" % n_side, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- native (GPU)
+
+def _timed_steps(torch, sim, steps, profile=True):
+    """Time ``steps`` steps with CUDA events on the library's stream; with
+    per-kernel events inside the same region."""
+    import paper_2411_13992_gb300 as sph
+    stream = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if profile:
+        sph.sph_profile_begin(sim.ctx, steps)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sph.sph_profile_end(sim.ctx) if profile else None
+    sim.sync()
+    return e0.elapsed_time(e1), prof
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import paper_2411_13992_gb300 as sph
+    from paper_2411_13992_gb300 import cases
+
+    rank, world, local = _dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    case = cases.tgv3d(args.n)
+    n = case["n"]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- FP32 form: the headline number
+    sim = sph.Simulation(case, precision=32)
+    sim.set_state()
+    sim.build_cells()
+    sim.step(args.warmup)
+    sim.sync()
+    launches0 = sim.launches()
+    sampler = ClockSampler(_gpu_index(torch, dev))
+    sampler.start()
+    barrier()
+    ms, prof = _timed_steps(torch, sim, args.steps)
+    barrier()
+    clocks = sampler.stop()
+    launches = sim.launches() - launches0
+    ms_max = max_over_ranks(ms, torch, dist)
+    total = sum_over_ranks(float(n * args.steps), torch, dist)
+    value = total / (ms_max * 1e-3)
+    diag = sim.diag()
+    sim.close()
+
+    # ---- FP64 form, same workload
+    sim64 = sph.Simulation(case, precision=64)
+    sim64.set_state()
+    sim64.build_cells()
+    sim64.step(1)
+    sim64.sync()
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    barrier()
+    ms64, prof64 = _timed_steps(torch, sim64, k64)
+    barrier()
+    ms64 = max_over_ranks(ms64, torch, dist)
+    value64 = sum_over_ranks(float(n * k64), torch, dist) / (ms64 * 1e-3)
+    sim64.close()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = _e2e(torch, sph, case, args, dist)
+
+    # ---- roofline of the dominant kernel (FP32 forces), live event timing
+    peaks, src = _peaks()
+    f_ms, f_cnt = prof["forces"]
+    f_avg_s = f_ms / max(f_cnt, 1) * 1e-3
+    pairs = _pairs_per_launch(case)
+    achieved_tflops = pairs * FLOPS_PER_PAIR_FP32 / f_avg_s / 1e12
+    peak_tflops = fp32_peak_tflops(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    hbm_achieved = n * BYTES_PER_PARTICLE_FORCES / f_avg_s / 1e9
+    traffic = _profiled_traffic()
+    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+            "kernel": "k_forces_f32<3,KSum>", "peak_source": "FP32 FMA units x max SM clock (%s clock)" % src,
+            "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR_FP32,
+            "avg_launch_ms": f_avg_s * 1e3,
+            "hbm_algorithmic_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
+            "hbm_frac": hbm_achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS)}
+    kernels = {k: {"ms_per_step": v[0] / max(v[1], 1), "share": v[0] / max(sum(t[0] for t in prof.values()), 1e-9)}
+               for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, el, nn = oracle_rate(args.cpu_n, 1, 0, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "one FP64 oracle step (cell-list neighbours, OpenMP) of the 3-D Taylor-Green at %d^3 = %d "
+                         "particles, %.1f s" % (args.cpu_n, nn, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "precision": "FP32 pair sums (Kahan), FP64 "
+                       "positions and reductions", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (%.0f MB state per GPU)" % (sph.sph_query_workspace(
+                           sph.params_from_case(case, 32), n) / 1e6)},
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                     "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof64.items()}},
+            "fp32_over_fp64": value / value64,
+            "roofline": roof,
+            "kernels": kernels,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "diag_after": {"ke": diag["ke"], "vmax": diag["vmax"], "n_chi": diag["n_chi"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _pairs_per_launch(case) -> int:
+    """Ordered interacting pairs (r < 2h, j != i) of the workload: every
+    particle of the jittered lattice at h = 1.3 dp has the 80 lattice
+    neighbours with |k|^2 <= 6 (|k| < 2.6); jitter of 1e-3 dp cannot move a
+    pair across 2h (next shell |k|^2 = 8)."""
+    return case["n"] * 80
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the forces kernel from the committed ncu
+    summary, or None when no summary for the current kernel exists."""
+    path = os.path.join(ROOT, "profiles", "forces_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("dram_bytes_per_launch_full")
+    except (OSError, ValueError):
+        return None
+
+
+def _e2e(torch, sph, case, args, dist):
+    """Same metric through the C ABI with host buffers: each step uploads the
+    state from pinned host memory, sorts it, steps once and reads the state
+    back to pinned host memory."""
+    import numpy as np
+    n = case["n"]
+    sim = sph.Simulation(case, precision=32)
+    sim.set_state()
+    sim.build_cells()
+    sim.step(1)
+    pin = {k: torch.empty((n, 3), dtype=torch.float64).pin_memory() for k in ("x", "v", "a", "dr")}
+    h = torch.from_numpy(case["h"]).pin_memory()
+    m = torch.from_numpy(case["m"]).pin_memory()
+    sph.sph_get_state(sim.ctx, pin["x"], pin["v"], pin["a"], pin["dr"], None)
+    k = max(1, min(args.steps, args.e2e_steps))
+
+    def one():
+        sph.sph_set_state(sim.ctx, pin["x"], pin["v"], pin["a"], pin["dr"], h, m, None, None, None)
+        sph.sph_build_cells(sim.ctx)
+        sph.sph_step(sim.ctx, 1)
+        sph.sph_get_state(sim.ctx, pin["x"], pin["v"], pin["a"], pin["dr"], None)
+
+    one()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    el = max_over_ranks(el, torch, dist)
+    sim.sync()
+    sim.close()
+    value = sum_over_ranks(float(n * k), torch, dist) / el
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * 24 + 2 * n * 8,
+            "d2h_bytes_per_step": 4 * n * 24, "steps": k,
+            "path": "sph_set_state (pinned host) + sph_build_cells + sph_step(1) + sph_get_state (pinned host)"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--n", type=int, default=128, help="particles per side of the 3-D Taylor-Green lattice")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-n", type=int, default=128, help="lattice side of the CPU-baseline sample")
+    ap.add_argument("--ref-n", type=int, default=64, help="lattice side of the reference arm's per-step sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -315,6 +315,45 @@ def step(P, case, state, sigma0, dt, mode="cells"):
     return {"x": x, "v": v, "a": a, "dr": dr, "rho": rho, "R": R, "chi": chi}
 
 
+def kick(P, v, a, kind, hdt):
+    """v += hdt a for fluid particles (returns a new array)."""
+    n = len(v)
+    v = _vec(v, n).copy()
+    a = _vec(a, n)
+    kind = _sca(kind, n, np.int8)
+    lib().orc_kick(ctypes.byref(P), n, float(hdt), _d(v), _d(a), kind.ctypes.data_as(_bp))
+    return v
+
+
+def drift(P, x, v, dr, kind, dt):
+    """x += dt v + dr for fluid particles, periodic wrap (returns a new array)."""
+    n = len(x)
+    x = _vec(x, n).copy()
+    v, dr = _vec(v, n), _vec(dr, n)
+    kind = _sca(kind, n, np.int8)
+    lib().orc_drift(ctypes.byref(P), n, float(dt), _d(x), _d(v), _d(dr), kind.ctypes.data_as(_bp))
+    return x
+
+
+def step_reversed_sums(P, case, state, sigma0, dt):
+    """The same kick-drift-kick step as ``step`` with every neighbour sum taken
+    in descending instead of ascending j.  The two results differ only by
+    floating-point summation order: their difference measures the rounding
+    floor of the method's FP64 arithmetic on this state."""
+    n = len(state["x"])
+    h, m, kind, vw = _case_arrays(case, n)
+    hdt = 0.5 * dt
+    v = kick(P, state["v"], state["a"], kind, hdt)
+    x = drift(P, state["x"], v, state["dr"], kind, dt)
+    start, idx = neighbours(P, x, h)
+    ridx = np.concatenate([idx[start[i]:start[i + 1]][::-1] for i in range(n)]) if n else idx
+    nb = (start, ridx)
+    rho, _ = density(P, x, h, kind, sigma0, nb)
+    f = forces(P, x, v, h, m, kind, vw, rho, nb)
+    v = kick(P, v, f["a"], kind, hdt)
+    return {"x": x, "v": v, "a": f["a"], "dr": f["dr"], "rho": rho, "R": f["R"], "chi": f["chi"]}
+
+
 def sigma0_for(case, dim):
     """Per-particle reference sum of Eq. 8: the perfect-lattice sum at the
     particle's own spacing dp = (m / rho0)^(1/D) and smoothing length h."""

@@ -29,7 +29,8 @@ __all__ = [
     "SphParams", "SphDiag", "SphError", "load", "exported_symbols", "declared_symbols",
     "sph_default_params", "sph_query_workspace", "sph_create", "sph_set_state", "sph_build_cells", "sph_step",
     "sph_set_dt", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
-    "sph_launch_count", "params_from_case", "Simulation",
+    "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES",
+    "params_from_case", "Simulation",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
 ]
 
@@ -115,6 +116,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_destroy": (None, [_vp]),
             "sph_status_str": (ctypes.c_char_p, [_i32]),
             "sph_launch_count": (_i64, [_vp]),
+            "sph_profile_begin": (_i32, [_vp, _i32]),
+            "sph_profile_end": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+            "sph_kernel_class_name": (ctypes.c_char_p, [_i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -246,6 +250,25 @@ def sph_status_str(status: int) -> str:
 
 def sph_launch_count(ctx) -> int:
     return int(load().sph_launch_count(ctx))
+
+
+KERNEL_CLASSES = 7
+
+
+def sph_profile_begin(ctx, max_steps: int) -> None:
+    _check(load().sph_profile_begin(ctx, int(max_steps)), "sph_profile_begin")
+
+
+def sph_profile_end(ctx) -> dict:
+    """{kernel class name: (summed ms, timed launches)} of the open profile."""
+    ms = (ctypes.c_double * KERNEL_CLASSES)()
+    cnt = (_i64 * KERNEL_CLASSES)()
+    _check(load().sph_profile_end(ctx, ms, cnt), "sph_profile_end")
+    return {sph_kernel_class_name(k): (float(ms[k]), int(cnt[k])) for k in range(KERNEL_CLASSES)}
+
+
+def sph_kernel_class_name(k: int) -> str:
+    return load().sph_kernel_class_name(int(k)).decode()
 
 
 # ------------------------------------------------------------------ convenience

@@ -121,12 +121,14 @@ struct PlainD {
 
 // ------------------------------------------------------------ cell grid
 
+// Cell coordinate along axis d, clamped to the grid; NaN maps to cell 0 (the
+// kick-drift kernel flags non-finite positions separately).
 __device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
 {
-    int c = (int)floor((x - G.lo[d]) * G.inv_edge[d]);
-    c = c < 0 ? 0 : c;
-    c = c >= G.nc[d] ? G.nc[d] - 1 : c;
-    return c;
+    double t = floor((x - G.lo[d]) * G.inv_edge[d]);
+    if (!(t >= 0.0)) return 0;
+    if (t >= (double)G.nc[d]) return G.nc[d] - 1;
+    return (int)t;
 }
 
 template <int DIM>

@@ -53,15 +53,20 @@ __global__ void k_sigma0(int n, const double* __restrict__ h, const double* __re
     const double vol = m[i] / rho0;
     const double dp = DIM == 2 ? sqrt(vol) : cbrt(vol);
     const double ratio = h[i] / dp;            // smoothing length in units of dp
-    const int K = (int)ceil(2.0 * ratio) + 1;
+    const double reach2 = 4.0 * ratio * ratio;
+    const int K = (int)ceil(2.0 * ratio);
     const double inv = 1.0 / ratio;
+    // One octant of the integer lattice; each point stands for its 2^(number
+    // of non-zero coordinates) mirror images.
     double s = 0.0;
-    const int kz0 = DIM == 3 ? -K : 0, kz1 = DIM == 3 ? K : 0;
-    for (int kz = kz0; kz <= kz1; ++kz)
-        for (int ky = -K; ky <= K; ++ky)
-            for (int kx = -K; kx <= K; ++kx) {
-                double r = sqrt((double)(kx * kx + ky * ky + kz * kz));
-                if (r < 2.0 * ratio) s += wendland_W<DIM, double>(r, inv);
+    const int kz1 = DIM == 3 ? K : 0;
+    for (int kz = 0; kz <= kz1; ++kz)
+        for (int ky = 0; ky <= K; ++ky)
+            for (int kx = 0; kx <= K; ++kx) {
+                double r2 = (double)(kx * kx + ky * ky + kz * kz);
+                if (r2 >= reach2) continue;
+                double mult = (kx ? 2.0 : 1.0) * (ky ? 2.0 : 1.0) * (kz ? 2.0 : 1.0);
+                s += mult * wendland_W<DIM, double>(sqrt(r2), inv);
             }
     s0[i] = s / (DIM == 2 ? dp * dp : dp * dp * dp);
 }

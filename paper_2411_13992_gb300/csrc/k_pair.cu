@@ -434,6 +434,37 @@ __global__ void __launch_bounds__(256) k_forces_f32(int n, const float4* __restr
     block_partials(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
+// ================================================ diagnostics only
+
+// FP64 partials of the diagnostics from the stored v and dr (no pair work):
+// used when the caller supplied a and dr, so no force pass is needed.
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(256) k_diag_only(int n, StateSet<Real> S, double* __restrict__ partials)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part[kNPart];
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) part[k] = 0.0;
+    if (i < n && S.kind[i] == 0) {
+        const double m_i = S.m[i];
+        double v2 = 0.0, dr2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            double v = (double)S.v[(size_t)d * n + i];
+            double dr = (double)S.dr[(size_t)d * n + i];
+            part[1 + d] = m_i * v;
+            v2 += v * v;
+            dr2 += dr * dr;
+        }
+        part[0] = m_i;
+        part[4] = 0.5 * m_i * v2;
+        part[6] = sqrt(v2);
+        part[7] = sqrt(v2);
+        part[8] = sqrt(dr2);
+    }
+    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+}
+
 // =========================================================== finalize
 
 struct DtConsts {
@@ -537,6 +568,21 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
             else SPH_F32_FORCES(3, PlainF);
         }
 #undef SPH_F32_FORCES
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        auto s = *(StateSet<double>*)S;
+        if (dim == 2) k_diag_only<double, 2><<<nblk(n, T), T, 0, st>>>(n, s, partials);
+        else k_diag_only<double, 3><<<nblk(n, T), T, 0, st>>>(n, s, partials);
+    } else {
+        auto s = *(StateSet<float>*)S;
+        if (dim == 2) k_diag_only<float, 2><<<nblk(n, T), T, 0, st>>>(n, s, partials);
+        else k_diag_only<float, 3><<<nblk(n, T), T, 0, st>>>(n, s, partials);
     }
     return cudaGetLastError();
 }

@@ -29,6 +29,7 @@ cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* sta
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const void* vr, const float4* pos4, const int32_t* cell_of, const double* dt, int kick_on,
                           int write_ad, void* Rout, void* chi, double* partials, cudaStream_t st);
+cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st);
 cudaError_t launch_finalize(int nblocks, const double* partials, const sph_params& P, double* diag, double* dt,
                             int count_step, cudaStream_t st);
 

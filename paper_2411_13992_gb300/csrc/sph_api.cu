@@ -234,10 +234,21 @@ sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
     return SPH_OK;
 }
 
-// Density, fused forces (+ closing kick), reductions and dt.
-sph_status run_forces(sph_ctx* c, int kick_on, int write_ad, int count_step)
+// Density, fused forces (+ closing kick), reductions and dt.  With
+// pairs == 0 (a and dr supplied by the caller) only the density and the
+// diagnostics run.
+sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
 {
     const int n = (int)c->n;
+    if (!pairs) {
+        SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
+                              c->st));
+        SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->st));
+        SPH_CU(launch_finalize(pair_blocks(n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+        c->launches += 3;
+        return SPH_OK;
+    }
+    const int write_ad = 1;
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->st));
     SPH_MARK(SPH_K_DENSITY, 1);

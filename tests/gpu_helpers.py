@@ -100,4 +100,8 @@ def compare_step(c, state, dt, s0, P, precision=64, mode="cells", **kw):
     err["n_chi_got"] = diag["n_chi"]
     s = P.h_min ** 2 * (ref["R"][fl] ** 2).sum(axis=1)
     err["near_threshold"] = int((np.abs(s - P.tv_thresh) < 1e-9 * P.tv_thresh).sum())
+    # rounding floor: the oracle against itself with every neighbour sum reversed
+    alt = oracle.step_reversed_sums(P, c, state, s0, dt)
+    err["floor_a"] = normwise(alt["a"][fl], ref["a"][fl])
+    err["floor_dr"] = normwise(alt["dr"][fl], ref["dr"][fl])
     return err, ref, got

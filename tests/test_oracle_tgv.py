@@ -62,3 +62,21 @@ def test_decay_rate_error_shrinks_with_resolution(orc):
         ratio, _, _ = _run(orc, cases.tgv2d(n), 4 * n)
         errs.append(abs(ratio - 1.0))
     assert errs[1] < 0.6 * errs[0], errs
+
+
+def test_reversed_sum_step_differs_only_by_rounding(orc):
+    """The rounding-floor helper takes the same step with neighbour sums in
+    the opposite order: identical drift, and fields equal to rounding."""
+    c = cases.tgv2d(20)
+    P = orc.make_params(2, c["lo"], c["L"], c["periodic"], c["rho0"], c["c"], c["eta"], c["h_min"],
+                        u_ref=c["u_ref"])
+    s0 = orc.sigma0_for(c, 2)
+    fp = orc.force_pass(P, c, c["x"], c["v"], s0)
+    st = {"x": c["x"], "v": c["v"], "a": fp["a"], "dr": fp["dr"]}
+    dt = orc.time_step(P, c["v"], c["kind"])
+    a = orc.step(P, c, st, s0, dt)
+    b = orc.step_reversed_sums(P, c, st, s0, dt)
+    assert np.array_equal(a["x"], b["x"])
+    np.testing.assert_allclose(b["rho"], a["rho"], rtol=1e-14)
+    np.testing.assert_allclose(b["v"], a["v"], rtol=0, atol=1e-13)
+    assert np.abs(b["a"] - a["a"]).max() < 1e-10 * np.abs(a["a"]).max()
