@@ -40,8 +40,8 @@
  *   - Every call returns a status.  Host-detectable errors (bad arguments,
  *     call order, workspace too small, CUDA launch errors) return at once.
  *     Device-detected errors (cell overflow, non-finite values, particle
- *     outside a non-periodic box) set a sticky error word that sph_sync
- *     returns.  Nothing is thrown across the ABI; no call traps the GPU.
+ *     outside a non-periodic box, h outside [h_min, h_max]) set a sticky
+ *     error word that sph_sync returns.  Nothing is thrown across the ABI; no call traps the GPU.
  */
 #ifndef SPHTV_H
 #define SPHTV_H
@@ -67,7 +67,8 @@ typedef enum sph_status {
     SPH_ERR_OVERFLOW = 4,   /* device: a cell held more particles than supported */
     SPH_ERR_NAN = 5,        /* device: non-finite position or velocity */
     SPH_ERR_DOMAIN = 6,     /* device: particle left a non-periodic box */
-    SPH_ERR_STATE = 7       /* call order: e.g. sph_step before sph_build_cells */
+    SPH_ERR_STATE = 7,      /* call order: e.g. sph_step before sph_build_cells */
+    SPH_ERR_INPUT = 8       /* device: a particle's h outside [h_min, h_max] or mass not positive */
 } sph_status;
 
 enum { SPH_TV_OFF = 0, SPH_TV_LIMITED = 1, SPH_TV_UNLIMITED = 2 };

@@ -39,7 +39,7 @@ TVH_MIN, TVH_PARTICLE = 0, 1
 HPAIR_MEAN, HPAIR_MAX = 0, 1
 
 STATUS_NAMES = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_WORKSPACE", 4: "SPH_ERR_OVERFLOW",
-                5: "SPH_ERR_NAN", 6: "SPH_ERR_DOMAIN", 7: "SPH_ERR_STATE"}
+                5: "SPH_ERR_NAN", 6: "SPH_ERR_DOMAIN", 7: "SPH_ERR_STATE", 8: "SPH_ERR_INPUT"}
 
 HEADER = os.path.join(_build.INCLUDE, "sphtv.h")
 

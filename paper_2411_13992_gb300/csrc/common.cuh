@@ -14,7 +14,7 @@ namespace sphtv {
 constexpr double kPi = 3.14159265358979323846;
 
 // Device error word bits (sticky; read back by sph_sync).
-enum : uint32_t { ERRB_OVERFLOW = 1u, ERRB_NAN = 2u, ERRB_DOMAIN = 4u };
+enum : uint32_t { ERRB_OVERFLOW = 1u, ERRB_NAN = 2u, ERRB_DOMAIN = 4u, ERRB_INPUT = 8u };
 
 // Number of FP64 per-block partial values the fused force kernel writes.
 constexpr int kNPart = 10;
@@ -46,6 +46,9 @@ struct Consts {
     Real g[3];
     Real h_min, tv_xi, tv_C, tv_thresh;
     int tv_mode, tv_h_particle, h_pair_max, kahan;
+    // uniform resolution (h_min == h_max): every pair has h_ij = h
+    int uniform_h;
+    Real h_u, inv_h_u, four_h2_u;
 };
 
 // Velocity + density deviation packed per particle for the pair pass:

@@ -185,10 +185,12 @@ __global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, cons
 
 // --------------------------------------------------------------- permute
 
+// FP32 form: pos4 = {offset from the cell origin, h} (uniform resolution:
+// {offset, m}, since h is then a constant), mf = m in FP32, cell_out = key.
 template <typename Real, int DIM, bool CARRY_AD, bool F32POS>
 __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real> src, StateSet<Real> dst,
                           const int32_t* __restrict__ key, Grid G, float4* __restrict__ pos4,
-                          int32_t* __restrict__ cell_out)
+                          int32_t* __restrict__ cell_out, float* __restrict__ mf, int uniform_h)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -206,8 +208,9 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
         }
     }
     double h = src.h[i];
+    double m = src.m[i];
     dst.h[k] = h;
-    dst.m[k] = src.m[i];
+    dst.m[k] = m;
     dst.s0[k] = src.s0[i];
     dst.id[k] = src.id[i];
     dst.kind[k] = src.kind[i];
@@ -218,8 +221,9 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
         float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) o[d] = (float)(xs[d] - (G.lo[d] + (double)c[d] * G.edge[d]));
-        pos4[k] = make_float4(o[0], o[1], o[2], (float)h);
+        pos4[k] = make_float4(o[0], o[1], o[2], uniform_h ? (float)m : (float)h);
         cell_out[k] = kk;
+        mf[k] = (float)m;
     }
 }
 
@@ -257,26 +261,27 @@ cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int
 
 template <typename Real>
 static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
-                      const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st)
+                      const Grid& G, float4* pos4, int32_t* cell, float* mf, int uh, int carry_ad, cudaStream_t st)
 {
     const int T = 256;
     auto s = *(StateSet<Real>*)src;
     auto d = *(StateSet<Real>*)dst;
     constexpr bool F32 = sizeof(Real) == 4;
     if (dim == 2) {
-        if (carry_ad) k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
-        else k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+        if (carry_ad) k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
+        else k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
     } else {
-        if (carry_ad) k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
-        else k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell);
+        if (carry_ad) k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
+        else k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
     }
 }
 
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
-                           const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st)
+                           const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
+                           cudaStream_t st)
 {
-    if (prec == 64) permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, carry_ad, st);
-    else permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, carry_ad, st);
+    if (prec == 64) permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st);
+    else permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st);
     return cudaGetLastError();
 }
 

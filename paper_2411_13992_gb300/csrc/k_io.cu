@@ -80,6 +80,17 @@ __global__ void k_rho_out(int n, const V4* __restrict__ vr, const int8_t* __rest
     dst[id[k]] = kind[k] ? rho0 : rho0 + (double)vr[k].w;
 }
 
+// Every h must lie in [h_min, h_max] (the cell edge is sized by h_max) and
+// every mass must be positive and finite.
+__global__ void k_check_input(int n, const double* __restrict__ h, const double* __restrict__ m, double h_min,
+                              double h_max, uint32_t* err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = h[i] >= h_min && h[i] <= h_max && m[i] > 0.0 && isfinite(m[i]);
+    if (!ok) atomicOr(err, ERRB_INPUT);
+}
+
 template <typename Real>
 __global__ void k_scalar_out(int n, const Real* __restrict__ src, const int32_t* __restrict__ id,
                              double* __restrict__ dst)
@@ -150,6 +161,13 @@ cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, 
 {
     if (prec == 64) k_rho_out<double4_32a><<<nblk(n, 256), 256, 0, st>>>(n, (const double4_32a*)vr, kind, id, rho0, dst);
     else k_rho_out<float4><<<nblk(n, 256), 256, 0, st>>>(n, (const float4*)vr, kind, id, rho0, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,
+                               cudaStream_t st)
+{
+    k_check_input<<<nblk(n, 256), 256, 0, st>>>(n, h, m, h_min, h_max, err);
     return cudaGetLastError();
 }
 

@@ -20,93 +20,13 @@
 // density, c_bar = c; h_ij = (h_i + h_j)/2 (or max); a wall j stands in with
 // rho_j = rho_i, p_j = p_i, V_j = m_j / rho_i and its prescribed velocity.
 //
-// FP64 form: absolute FP64 positions, minimum image per pair, plain sums.
-// FP32 form: FP32 positions relative to the cell origin plus a per
-// neighbour-cell shift, Kahan-compensated FP32 pair sums, FP64 partials.
+// FP64 form (this file): absolute FP64 positions, minimum image per pair,
+// plain sums.  FP32 form: k_pair32.cu.
 #include "common.cuh"
 #include "launch.h"
+#include "pair_physics.cuh"
 
 namespace sphtv {
-
-template <typename Real>
-__device__ __forceinline__ Real pair_h(const Consts<Real>& K, Real hi, Real hj)
-{
-    return K.h_pair_max ? (hi > hj ? hi : hj) : Real(0.5) * (hi + hj);
-}
-
-template <typename Real>
-__device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
-{
-    if (K.tv_mode == SPH_TV_OFF) return Real(0);
-    if (K.tv_mode == SPH_TV_UNLIMITED) return Real(1);
-    if (s > K.tv_thresh) {
-        Real t = K.tv_C * s;
-        return t < Real(1) ? t : Real(1);
-    }
-    return Real(0);
-}
-
-// Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, r = |rv|,
-// dw = W'(r, h_ij)).  Adds into the caller's accumulators.
-template <typename Real, int DIM, typename Acc>
-__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real dw, const Real* vi,
-                                           Real rho_i, Real p_i, const Real* vj, Real w_j, Real m_j, Acc* acc_a,
-                                           Acc* acc_R)
-{
-    const bool wall = isinf(w_j);
-    const Real rho_j = wall ? rho_i : K.rho0 + w_j;
-    const Real p_j = wall ? p_i : K.c2 * w_j;
-    const Real inv_r = Real(1) / r;
-    Real ul = Real(0), ur = Real(0);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        Real e = -rv[d] * inv_r;
-        ul += vi[d] * e;
-        ur += vj[d] * e;
-    }
-    Real du = ul - ur;
-    Real beta = K.beta_slope * (du * K.inv_c);
-    beta = beta > Real(0) ? beta : Real(0);
-    beta = beta < Real(1) ? beta : Real(1);
-    const Real rhobar = Real(0.5) * (rho_i + rho_j);
-    const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
-    const Real inv_rr = Real(1) / (rho_i * rho_j);
-    const Real cp = Real(-2) * m_j * pstar * inv_rr;
-    const Real cv = K.two_eta * m_j * inv_rr * dw * inv_r;
-    const Real V_j = m_j / rho_j;
-    const Real dwr = dw * inv_r;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        Real gw = dwr * rv[d];
-        acc_a[d].add(cp * gw + cv * (vi[d] - vj[d]));
-        acc_R[d].add(V_j * gw);
-    }
-}
-
-// Block reduction of the FP64 partials: 6 sums then 3 maxima.
-__device__ __forceinline__ void block_partials(double* vals, double* out_block)
-{
-    __shared__ double sh[32][kNPart];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < kNPart; ++k) {
-        double x = vals[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double y = __shfl_down_sync(0xffffffffu, x, off);
-            x = (k >= 6 && k <= 8) ? fmax(x, y) : x + y;
-        }
-        if (lane == 0) sh[w][k] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < kNPart) {
-        int k = threadIdx.x;
-        double x = sh[0][k];
-        for (int t = 1; t < nw; ++t) x = (k >= 6 && k <= 8) ? fmax(x, sh[t][k]) : x + sh[t][k];
-        out_block[k] = x;
-    }
-}
-// partial layout: 0 mass, 1-3 momentum, 4 KE, 5 n_chi, 6 vmax, 7 vt_max, 8 dr_max, 9 unused
 
 // ============================================================== FP64 form
 
@@ -264,176 +184,6 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
     block_partials(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
-// ============================================================== FP32 form
-
-template <int DIM, typename Acc>
-__global__ void __launch_bounds__(256) k_density_f32(int n, const float4* __restrict__ pos4,
-                                                     const int32_t* __restrict__ cell_of,
-                                                     const int32_t* __restrict__ start, Grid G, Consts<float> K,
-                                                     StateSet<float> S, float4* __restrict__ vr)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float vi[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
-    if (S.kind[i]) {
-        vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
-        return;
-    }
-    const float4 pi = pos4[i];
-    const float oi[3] = {pi.x, pi.y, pi.z};
-    const float hi = pi.w;
-    int c[3];
-    cell_decode(G, cell_of[i], c);
-    Acc sigma;
-    const int zr = DIM == 3 ? 1 : 0;
-    for (int dz = -zr; dz <= zr; ++dz) {
-        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
-        if (cz < 0) continue;
-        float shz = -(float)dz * G.edgef[2];
-        for (int dy = -1; dy <= 1; ++dy) {
-            int cy = cell_step(G, c[1], dy, 1);
-            if (cy < 0) continue;
-            float shy = -(float)dy * G.edgef[1];
-            for (int dx = -1; dx <= 1; ++dx) {
-                int cx = cell_step(G, c[0], dx, 0);
-                if (cx < 0) continue;
-                float shx = -(float)dx * G.edgef[0];
-                int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                for (int j = start[cell]; j < start[cell + 1]; ++j) {
-                    float4 pj = pos4[j];
-                    float rx = (oi[0] - pj.x) + shx;
-                    float ry = (oi[1] - pj.y) + shy;
-                    float r2 = rx * rx + ry * ry;
-                    if (DIM == 3) {
-                        float rz = (oi[2] - pj.z) + shz;
-                        r2 += rz * rz;
-                    }
-                    float hij = pair_h(K, hi, pj.w);
-                    if (r2 < 4.f * hij * hij) sigma.add(wendland_W<DIM, float>(sqrtf(r2), 1.f / hij));
-                }
-            }
-        }
-    }
-    // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
-    const float s0 = (float)S.s0[i];
-    const float w = K.rho0 * (sigma.value() - s0) / s0;
-    vr[i] = make_float4(vi[0], vi[1], vi[2], w);
-}
-
-template <int DIM, typename Acc>
-__global__ void __launch_bounds__(256) k_forces_f32(int n, const float4* __restrict__ pos4,
-                                                    const int32_t* __restrict__ cell_of,
-                                                    const int32_t* __restrict__ start, Grid G, Consts<float> K,
-                                                    StateSet<float> S, const float4* __restrict__ vr,
-                                                    const double* __restrict__ dt_ptr, int kick_on, int write_ad,
-                                                    float* __restrict__ Rout, float* __restrict__ chi_out,
-                                                    double* __restrict__ partials)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double part[kNPart];
-#pragma unroll
-    for (int k = 0; k < kNPart; ++k) part[k] = 0.0;
-    const double dt = *dt_ptr;
-    const double hdt = kick_on ? 0.5 * dt : 0.0;
-    if (i < n && S.kind[i] == 0) {
-        const float4 pi = pos4[i];
-        const float oi[3] = {pi.x, pi.y, pi.z};
-        const float hi = pi.w;
-        const float4 me = vr[i];
-        const float vi[3] = {me.x, me.y, me.z};
-        const float rho_i = K.rho0 + me.w;
-        const float p_i = K.c2 * me.w;
-        Acc acc_a[DIM], acc_R[DIM];
-        int c[3];
-        cell_decode(G, cell_of[i], c);
-        const int zr = DIM == 3 ? 1 : 0;
-        for (int dz = -zr; dz <= zr; ++dz) {
-            int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
-            if (cz < 0) continue;
-            float shz = -(float)dz * G.edgef[2];
-            for (int dy = -1; dy <= 1; ++dy) {
-                int cy = cell_step(G, c[1], dy, 1);
-                if (cy < 0) continue;
-                float shy = -(float)dy * G.edgef[1];
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int cx = cell_step(G, c[0], dx, 0);
-                    if (cx < 0) continue;
-                    float shx = -(float)dx * G.edgef[0];
-                    int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                    for (int j = start[cell]; j < start[cell + 1]; ++j) {
-                        if (j == i) continue;
-                        float4 pj = pos4[j];
-                        float rv[3] = {(oi[0] - pj.x) + shx, (oi[1] - pj.y) + shy, 0.f};
-                        float r2 = rv[0] * rv[0] + rv[1] * rv[1];
-                        if (DIM == 3) {
-                            rv[2] = (oi[2] - pj.z) + shz;
-                            r2 += rv[2] * rv[2];
-                        }
-                        float hij = pair_h(K, hi, pj.w);
-                        if (!(r2 < 4.f * hij * hij) || r2 == 0.f) continue;
-                        float r = sqrtf(r2);
-                        float dw = wendland_dW<DIM, float>(r, 1.f / hij);
-                        float4 oj = vr[j];
-                        float vj[3] = {oj.x, oj.y, oj.z};
-                        pair_force<float, DIM, Acc>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, (float)S.m[j], acc_a,
-                                                    acc_R);
-                    }
-                }
-            }
-        }
-        float a[3] = {0, 0, 0}, R[3] = {0, 0, 0};
-        float R2 = 0.f;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            a[d] = K.g[d] + acc_a[d].value();
-            R[d] = acc_R[d].value();
-            R2 += R[d] * R[d];
-        }
-        const float htv = K.tv_h_particle ? hi : K.h_min;
-        const float htv2 = htv * htv;
-        const float chi = tv_limiter(K, htv2 * R2);
-        const double m_i = S.m[i];
-        double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            size_t o = (size_t)d * n + i;
-            float dr = K.tv_xi * chi * htv2 * R[d];
-            float vn = __fadd_rn(vi[d], __fmul_rn((float)hdt, a[d]));
-            if (write_ad) {
-                S.a[o] = a[d];
-                S.dr[o] = dr;
-            }
-            S.v[o] = vn;
-            Rout[o] = R[d];
-            part[1 + d] = m_i * (double)vn;
-            v2 += (double)vn * vn;
-            dr2 += (double)dr * dr;
-            double vt = dt > 0.0 ? (double)vn + (double)dr / dt : (double)vn;
-            vt2 += vt * vt;
-        }
-        chi_out[i] = chi;
-        part[0] = m_i;
-        part[4] = 0.5 * m_i * v2;
-        part[5] = chi > 0.f ? 1.0 : 0.0;
-        part[6] = sqrt(v2);
-        part[7] = sqrt(vt2);
-        part[8] = sqrt(dr2);
-    } else if (i < n) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            if (write_ad) {
-                S.a[(size_t)d * n + i] = 0.f;
-                S.dr[(size_t)d * n + i] = 0.f;
-            }
-            Rout[(size_t)d * n + i] = 0.f;
-        }
-        chi_out[i] = 0.f;
-    }
-    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
-}
-
 // ================================================ diagnostics only
 
 // FP64 partials of the diagnostics from the stored v and dr (no pair work):
@@ -515,66 +265,44 @@ __global__ void __launch_bounds__(256) k_finalize(int nblocks, const double* __r
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-int pair_blocks(int n) { return nblk(n, 256); }
+int pair_blocks(int prec, int n) { return prec == 32 ? pair_blocks32(n) : nblk(n, 256); }
 
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
-                           void* vr, const float4* pos4, const int32_t* cell_of, cudaStream_t st)
+                           void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
+                           cudaStream_t st)
 {
     const int T = 256;
-    if (prec == 64) {
-        auto s = *(StateSet<double>*)S;
-        auto k = *(const Consts<double>*)K;
-        if (dim == 2) k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
-        else k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
-    } else {
-        auto s = *(StateSet<float>*)S;
-        auto k = *(const Consts<float>*)K;
-        if (k.kahan) {
-            if (dim == 2) k_density_f32<2, KSum><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, k, s, (float4*)vr);
-            else k_density_f32<3, KSum><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, k, s, (float4*)vr);
-        } else {
-            if (dim == 2) k_density_f32<2, PlainF><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, k, s, (float4*)vr);
-            else k_density_f32<3, PlainF><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, k, s, (float4*)vr);
-        }
-    }
+    if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st);
+    auto s = *(StateSet<double>*)S;
+    auto k = *(const Consts<double>*)K;
+    if (dim == 2) k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
+    else k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
-                          const void* vr, const float4* pos4, const int32_t* cell_of, const double* dt, int kick_on,
-                          int write_ad, void* Rout, void* chi, double* partials, cudaStream_t st)
+                          const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
+                          const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
+                          void* Rout, void* chi, double* partials, cudaStream_t st)
 {
     const int T = 256;
-    if (prec == 64) {
-        auto s = *(StateSet<double>*)S;
-        auto k = *(const Consts<double>*)K;
-        if (dim == 2)
-            k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
-                                                      (double*)Rout, (double*)chi, partials);
-        else
-            k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
-                                                      (double*)Rout, (double*)chi, partials);
-    } else {
-        auto s = *(StateSet<float>*)S;
-        auto k = *(const Consts<float>*)K;
-#define SPH_F32_FORCES(D, A)                                                                                  \
-    k_forces_f32<D, A><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, k, s, (const float4*)vr, dt, kick_on, write_ad, \
-                                                 (float*)Rout, (float*)chi, partials)
-        if (k.kahan) {
-            if (dim == 2) SPH_F32_FORCES(2, KSum);
-            else SPH_F32_FORCES(3, KSum);
-        } else {
-            if (dim == 2) SPH_F32_FORCES(2, PlainF);
-            else SPH_F32_FORCES(3, PlainF);
-        }
-#undef SPH_F32_FORCES
-    }
+    if (prec == 32)
+        return launch_forces32(dim, n, S, start, G, K, mf, vr, pos4, cell_of, nbl, nbc, dt, kick_on, write_ad, Rout,
+                               chi, partials, st);
+    auto s = *(StateSet<double>*)S;
+    auto k = *(const Consts<double>*)K;
+    if (dim == 2)
+        k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
+                                                  (double*)Rout, (double*)chi, partials);
+    else
+        k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
+                                                  (double*)Rout, (double*)chi, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st)
 {
-    const int T = 256;
+    const int T = prec == 32 ? 128 : 256;   // one partials row per block of the forces kernel of that form
     if (prec == 64) {
         auto s = *(StateSet<double>*)S;
         if (dim == 2) k_diag_only<double, 2><<<nblk(n, T), T, 0, st>>>(n, s, partials);

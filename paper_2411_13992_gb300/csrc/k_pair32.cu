@@ -1,0 +1,336 @@
+// k_pair32.cu -- FP32 pair passes of libsphtv (density and fused forces),
+// one thread per cell-sorted particle.
+//
+// The density pass scans the 3^D cells around each particle (cell-relative
+// FP32 positions; lanes that share a cell load the same candidate at the
+// same time), sums sigma, and records the particle's force neighbours in a
+// transposed list in HBM (entry k of particle i at k * n + i, so a warp's
+// list reads are coalesced).  The force pass then runs the pair body over
+// that list only: about 80 neighbours per particle in 3-D instead of about
+// 480 candidates, and no lane waits on another lane's candidate tests.  A
+// particle with more neighbours than the list holds scans its cells again.
+//
+// Pair vectors keep full FP32 precision: r_ij = (o_i - o_j) + s, where o are
+// offsets from each particle's cell origin and s = -(cell step) x edge is
+// exact in FP32.
+//
+// Method (see k_pair.cu for the FP64 form and pair_physics.cuh for the
+// readings of the paper): density Eq. 8 with Eq. 2; pressure Eq. 3, 5, 6;
+// viscous Eq. 7; residual, limiter and displacement Eq. 14-16.
+#include "common.cuh"
+#include "launch.h"
+#include "pair_physics.cuh"
+
+namespace sphtv {
+
+constexpr int kTPB32 = 128;      // threads per block of the FP32 pair kernels
+
+// Support radius squared of a pair: 4 h_ij^2.
+template <bool UNIFORM>
+__device__ __forceinline__ float support2(const Consts<float>& K, float hi, float hj)
+{
+    if (UNIFORM) return K.four_h2_u;
+    float h = pair_h(K, hi, hj);
+    return 4.f * h * h;
+}
+
+// Visit every candidate of the 3^D cells around cell_i (cell-relative FP32
+// positions plus the exact shift of the neighbour cell): f(j, code, pj, r2,
+// rx, ry, rz) with code = stencil index of the neighbour cell.  Lanes of a
+// warp whose particles share a cell read the same j at the same time, so
+// the loads of pos4 are warp broadcasts.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_candidates(const float* oi, int cell_i, const Grid& G,
+                                               const int32_t* __restrict__ start,
+                                               const float4* __restrict__ pos4, F& f)
+{
+    int c[3];
+    cell_decode(G, cell_i, c);
+    const int zr = DIM == 3 ? 1 : 0;
+    for (int dz = -zr; dz <= zr; ++dz) {
+        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+        if (cz < 0) continue;
+        const float shz = -(float)dz * G.edgef[2];
+        for (int dy = -1; dy <= 1; ++dy) {
+            int cy = cell_step(G, c[1], dy, 1);
+            if (cy < 0) continue;
+            const float shy = -(float)dy * G.edgef[1];
+            const int row = G.nc[0] * (cy + G.nc[1] * cz);
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cx = cell_step(G, c[0], dx, 0);
+                if (cx < 0) continue;
+                const float shx = -(float)dx * G.edgef[0];
+                const uint32_t code = (uint32_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                const int cell = cx + row;
+                const int j1 = start[cell + 1];
+                for (int j = start[cell]; j < j1; ++j) {
+                    const float4 pj = pos4[j];
+                    const float rx = (oi[0] - pj.x) + shx;
+                    const float ry = (oi[1] - pj.y) + shy;
+                    float r2 = rx * rx + ry * ry;
+                    float rz = 0.f;
+                    if (DIM == 3) {
+                        rz = (oi[2] - pj.z) + shz;
+                        r2 += rz * rz;
+                    }
+                    f(j, code, pj, r2, rx, ry, rz);
+                }
+            }
+        }
+    }
+}
+
+// Shift of a neighbour cell from its stencil code (as for_candidates forms it).
+__device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* sh)
+{
+    const int dx = (int)(code % 3u) - 1, dy = (int)((code / 3u) % 3u) - 1, dz = (int)(code / 9u) - 1;
+    sh[0] = -(float)dx * G.edgef[0];
+    sh[1] = -(float)dy * G.edgef[1];
+    sh[2] = -(float)dz * G.edgef[2];
+}
+
+// ---------------------------------------------------------------- density
+//
+// sigma_i over all neighbours (self included); also writes the particle's
+// force neighbour list (j != i, 0 < r^2 < 4 h_ij^2) transposed into nbl:
+// entry k of particle i at nbl[k * n + i] = (j << 5) | code, and the count
+// (which may exceed cap: the force kernel then scans the cells itself).
+
+template <int DIM, typename Acc, bool UNIFORM>
+__global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __restrict__ pos4,
+                                                      const int32_t* __restrict__ cell_of,
+                                                      const int32_t* __restrict__ start, Grid G, Consts<float> K,
+                                                      StateSet<float> S, float4* __restrict__ vr,
+                                                      uint32_t* __restrict__ nbl, int32_t* __restrict__ nbc, int cap)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float vi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
+    if (S.kind[i]) {
+        vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
+        nbc[i] = 0;
+        return;
+    }
+    const float4 pi = pos4[i];
+    const float oi[3] = {pi.x, pi.y, pi.z};
+    const float hi = UNIFORM ? K.h_u : pi.w;
+    Acc sigma;
+    int cnt = 0;
+    auto visit = [&](int j, uint32_t code, const float4& pj, float r2, float, float, float) {
+        if (r2 < support2<UNIFORM>(K, hi, pj.w)) {
+            const float inv_h = UNIFORM ? K.inv_h_u : 1.f / pair_h(K, hi, pj.w);
+            sigma.add(wendland_W<DIM, float>(sqrtf(r2), inv_h));
+            if (r2 > 0.f) {
+                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << 5) | code;
+                ++cnt;
+            }
+        }
+    };
+    for_candidates<DIM>(oi, cell_of[i], G, start, pos4, visit);
+    nbc[i] = cnt;
+    // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
+    const float s0 = (float)S.s0[i];
+    const float w = K.rho0 * (sigma.value() - s0) / s0;
+    vr[i] = make_float4(vi[0], vi[1], vi[2], w);
+}
+
+// ------------------------------------------------------------------ forces
+
+template <int DIM, typename Acc, bool UNIFORM>
+__global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __restrict__ pos4,
+                                                     const int32_t* __restrict__ cell_of,
+                                                     const int32_t* __restrict__ start, Grid G, Consts<float> K,
+                                                     StateSet<float> S, const float* __restrict__ mf,
+                                                     const float4* __restrict__ vr, const uint32_t* __restrict__ nbl,
+                                                     const int32_t* __restrict__ nbc, int cap,
+                                                     const double* __restrict__ dt_ptr, int kick_on, int write_ad,
+                                                     float* __restrict__ Rout, float* __restrict__ chi_out,
+                                                     double* __restrict__ partials)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part[kNPart];
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) part[k] = 0.0;
+    const double dt = *dt_ptr;
+    const double hdt = kick_on ? 0.5 * dt : 0.0;
+    if (i < n && S.kind[i] == 0) {
+        const float4 pi = pos4[i];
+        const float oi[3] = {pi.x, pi.y, pi.z};
+        const float hi = UNIFORM ? K.h_u : pi.w;
+        const float4 me = vr[i];
+        const float vi[3] = {me.x, me.y, me.z};
+        const float rho_i = K.rho0 + me.w;
+        const float p_i = K.c2 * me.w;
+        Acc acc_a[DIM], acc_R[DIM];
+        auto pair = [&](int j, const float4& pj, const float* rv, float r2) {
+            const float r = sqrtf(r2);
+            float inv_h, m_j;
+            if (UNIFORM) {
+                inv_h = K.inv_h_u;
+                m_j = pj.w;
+            } else {
+                inv_h = 1.f / pair_h(K, hi, pj.w);
+                m_j = mf[j];
+            }
+            const float dw = wendland_dW<DIM, float>(r, inv_h);
+            const float4 oj = vr[j];
+            const float vj[3] = {oj.x, oj.y, oj.z};
+            pair_force<float, DIM, Acc>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, m_j, acc_a, acc_R);
+        };
+        const int cnt = nbc[i];
+        if (cnt <= cap) {
+            // the neighbour list of the density pass: no candidate tests
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t e = nbl[(size_t)k * n + i];
+                const int j = (int)(e >> 5);
+                const float4 pj = pos4[j];
+                float sh[3];
+                code_shift(G, e & 31u, sh);
+                float rv[3];
+                rv[0] = (oi[0] - pj.x) + sh[0];
+                rv[1] = (oi[1] - pj.y) + sh[1];
+                float r2 = rv[0] * rv[0] + rv[1] * rv[1];
+                rv[2] = 0.f;
+                if (DIM == 3) {
+                    rv[2] = (oi[2] - pj.z) + sh[2];
+                    r2 += rv[2] * rv[2];
+                }
+                pair(j, pj, rv, r2);
+            }
+        } else {
+            // more neighbours than the list holds: scan the cells
+            auto visit = [&](int j, uint32_t, const float4& pj, float r2, float rx, float ry, float rz) {
+                if (r2 < support2<UNIFORM>(K, hi, pj.w) && r2 > 0.f) {
+                    const float rv[3] = {rx, ry, rz};
+                    pair(j, pj, rv, r2);
+                }
+            };
+            for_candidates<DIM>(oi, cell_of[i], G, start, pos4, visit);
+        }
+        float a[3] = {0, 0, 0}, R[3] = {0, 0, 0};
+        float R2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            a[d] = K.g[d] + acc_a[d].value();
+            R[d] = acc_R[d].value();
+            R2 += R[d] * R[d];
+        }
+        const float htv = K.tv_h_particle ? hi : K.h_min;
+        const float htv2 = htv * htv;
+        const float chi = tv_limiter(K, htv2 * R2);
+        const double m_i = S.m[i];
+        double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const size_t o = (size_t)d * n + i;
+            const float dr = K.tv_xi * chi * htv2 * R[d];
+            const float vn = __fadd_rn(vi[d], __fmul_rn((float)hdt, a[d]));
+            if (write_ad) {
+                S.a[o] = a[d];
+                S.dr[o] = dr;
+            }
+            S.v[o] = vn;
+            Rout[o] = R[d];
+            part[1 + d] = m_i * (double)vn;
+            v2 += (double)vn * vn;
+            dr2 += (double)dr * dr;
+            const double vt = dt > 0.0 ? (double)vn + (double)dr / dt : (double)vn;
+            vt2 += vt * vt;
+        }
+        chi_out[i] = chi;
+        part[0] = m_i;
+        part[4] = 0.5 * m_i * v2;
+        part[5] = chi > 0.f ? 1.0 : 0.0;
+        part[6] = sqrt(v2);
+        part[7] = sqrt(vt2);
+        part[8] = sqrt(dr2);
+    } else if (i < n) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            if (write_ad) {
+                S.a[(size_t)d * n + i] = 0.f;
+                S.dr[(size_t)d * n + i] = 0.f;
+            }
+            Rout[(size_t)d * n + i] = 0.f;
+        }
+        chi_out[i] = 0.f;
+    }
+    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+}
+
+// --------------------------------------------------------------- launchers
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+int pair_blocks32(int n) { return nblk(n, kTPB32); }
+
+int nbl_capacity(int dim) { return dim == 3 ? 128 : 96; }
+
+template <int DIM, typename Acc, bool U>
+static void density_t(int n, const float4* pos4, const int32_t* cell_of, const int32_t* start, const Grid& G,
+                      const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl, int32_t* nbc,
+                      cudaStream_t st)
+{
+    k_density32<DIM, Acc, U><<<nblk(n, kTPB32), kTPB32, 0, st>>>(n, pos4, cell_of, start, G, K, S, vr, nbl, nbc,
+                                                                 nbl_capacity(DIM));
+}
+
+template <int DIM, typename Acc, bool U>
+static void forces_t(int n, const float4* pos4, const int32_t* cell_of, const int32_t* start, const Grid& G,
+                     const Consts<float>& K, StateSet<float> S, const float* mf, const float4* vr,
+                     const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
+                     float* Rout, float* chi, double* partials, cudaStream_t st)
+{
+    k_forces32<DIM, Acc, U><<<nblk(n, kTPB32), kTPB32, 0, st>>>(n, pos4, cell_of, start, G, K, S, mf, vr, nbl, nbc,
+                                                                nbl_capacity(DIM), dt, kick_on, write_ad, Rout, chi,
+                                                                partials);
+}
+
+#define SPH_DISPATCH32(FN, ...)                                                   \
+    do {                                                                          \
+        if (K.kahan) {                                                            \
+            if (K.uniform_h) {                                                    \
+                if (dim == 2) FN<2, KSum, true>(__VA_ARGS__);                     \
+                else FN<3, KSum, true>(__VA_ARGS__);                              \
+            } else {                                                              \
+                if (dim == 2) FN<2, KSum, false>(__VA_ARGS__);                    \
+                else FN<3, KSum, false>(__VA_ARGS__);                             \
+            }                                                                     \
+        } else {                                                                  \
+            if (K.uniform_h) {                                                    \
+                if (dim == 2) FN<2, PlainF, true>(__VA_ARGS__);                   \
+                else FN<3, PlainF, true>(__VA_ARGS__);                            \
+            } else {                                                              \
+                if (dim == 2) FN<2, PlainF, false>(__VA_ARGS__);                  \
+                else FN<3, PlainF, false>(__VA_ARGS__);                           \
+            }                                                                     \
+        }                                                                         \
+    } while (0)
+
+cudaError_t launch_density32(int dim, int n, void* Sv, const int32_t* start, const Grid& G, const void* Kv, void* vr,
+                             const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
+                             cudaStream_t st)
+{
+    const StateSet<float> S = *(StateSet<float>*)Sv;
+    const Consts<float>& K = *(const Consts<float>*)Kv;
+    SPH_DISPATCH32(density_t, n, pos4, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces32(int dim, int n, void* Sv, const int32_t* start, const Grid& G, const void* Kv,
+                            const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
+                            const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
+                            void* Rout, void* chi, double* partials, cudaStream_t st)
+{
+    const StateSet<float> S = *(StateSet<float>*)Sv;
+    const Consts<float>& K = *(const Consts<float>*)Kv;
+    SPH_DISPATCH32(forces_t, n, pos4, cell_of, start, G, K, S, mf, (const float4*)vr, nbl, nbc, dt, kick_on,
+                   write_ad, (float*)Rout, (float*)chi, partials, st);
+    return cudaGetLastError();
+}
+
+#undef SPH_DISPATCH32
+
+}  // namespace sphtv

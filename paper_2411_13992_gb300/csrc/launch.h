@@ -20,15 +20,29 @@ cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int
                                  int32_t* perm_tmp, const int32_t* id, int32_t* perm, cudaStream_t st,
                                  int64_t* launches);
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
-                           const Grid& G, float4* pos4, int32_t* cell, int carry_ad, cudaStream_t st);
+                           const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
+                           cudaStream_t st);
 
-// k_pair.cu
-int pair_blocks(int n);
+// k_pair.cu (FP64 form; FP32 calls are forwarded to k_pair32.cu)
+int pair_blocks(int prec, int n);
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
-                           void* vr, const float4* pos4, const int32_t* cell_of, cudaStream_t st);
+                           void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
+                           cudaStream_t st);
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
-                          const void* vr, const float4* pos4, const int32_t* cell_of, const double* dt, int kick_on,
-                          int write_ad, void* Rout, void* chi, double* partials, cudaStream_t st);
+                          const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
+                          const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
+                          void* Rout, void* chi, double* partials, cudaStream_t st);
+
+// k_pair32.cu
+int pair_blocks32(int n);
+int nbl_capacity(int dim);
+cudaError_t launch_density32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K, void* vr,
+                             const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
+                             cudaStream_t st);
+cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
+                            const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
+                            const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
+                            void* Rout, void* chi, double* partials, cudaStream_t st);
 cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st);
 cudaError_t launch_finalize(int nblocks, const double* partials, const sph_params& P, double* diag, double* dt,
                             int count_step, cudaStream_t st);
@@ -44,6 +58,8 @@ cudaError_t launch_sigma0(int dim, int n, const double* h, const double* m, doub
                           cudaStream_t st);
 cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, const int32_t* id, double rho0,
                            double* dst, cudaStream_t st);
+cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,
+                               cudaStream_t st);
 cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st);
 
 }  // namespace sphtv

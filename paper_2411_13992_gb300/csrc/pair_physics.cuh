@@ -1,0 +1,97 @@
+// pair_physics.cuh -- the per-pair arithmetic of the method, shared by the
+// FP64 and FP32 pair kernels: pair smoothing length, the transport-velocity
+// limiter (Eq. 15), one neighbour's contribution to the pressure (Eq. 3,
+// 5-6) and viscous (Eq. 7) accelerations and to the residual of Eq. 14, and
+// the block reduction of the FP64 diagnostics partials.
+//
+// Readings of the paper: e_ij points from i to j (Riemann states U_l, U_r);
+// grad W_ij is grad_i W_ij = W'(r) (x_i - x_j)/r; V_j = m_j / rho_j;
+// rho_bar = (rho_i + rho_j)/2, c_bar = c; a wall neighbour stands in with
+// rho_j = rho_i, p_j = p_i (so V_j = m_j / rho_i) and its prescribed velocity.
+#pragma once
+
+#include "common.cuh"
+
+namespace sphtv {
+
+template <typename Real>
+__device__ __forceinline__ Real pair_h(const Consts<Real>& K, Real hi, Real hj)
+{
+    return K.h_pair_max ? (hi > hj ? hi : hj) : Real(0.5) * (hi + hj);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
+{
+    if (K.tv_mode == SPH_TV_OFF) return Real(0);
+    if (K.tv_mode == SPH_TV_UNLIMITED) return Real(1);
+    if (s > K.tv_thresh) {
+        Real t = K.tv_C * s;
+        return t < Real(1) ? t : Real(1);
+    }
+    return Real(0);
+}
+
+// Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, r = |rv|,
+// dw = W'(r, h_ij)).  Adds into the caller's accumulators.
+template <typename Real, int DIM, typename Acc>
+__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real dw, const Real* vi,
+                                           Real rho_i, Real p_i, const Real* vj, Real w_j, Real m_j, Acc* acc_a,
+                                           Acc* acc_R)
+{
+    const bool wall = isinf(w_j);
+    const Real rho_j = wall ? rho_i : K.rho0 + w_j;
+    const Real p_j = wall ? p_i : K.c2 * w_j;
+    const Real inv_r = Real(1) / r;
+    Real ul = Real(0), ur = Real(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        Real e = -rv[d] * inv_r;
+        ul += vi[d] * e;
+        ur += vj[d] * e;
+    }
+    Real du = ul - ur;
+    Real beta = K.beta_slope * (du * K.inv_c);
+    beta = beta > Real(0) ? beta : Real(0);
+    beta = beta < Real(1) ? beta : Real(1);
+    const Real rhobar = Real(0.5) * (rho_i + rho_j);
+    const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
+    const Real inv_rr = Real(1) / (rho_i * rho_j);
+    const Real cp = Real(-2) * m_j * pstar * inv_rr;
+    const Real cv = K.two_eta * m_j * inv_rr * dw * inv_r;
+    const Real V_j = m_j / rho_j;
+    const Real dwr = dw * inv_r;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        Real gw = dwr * rv[d];
+        acc_a[d].add(cp * gw + cv * (vi[d] - vj[d]));
+        acc_R[d].add(V_j * gw);
+    }
+}
+
+// Block reduction of the FP64 partials: 6 sums then 3 maxima.
+__device__ __forceinline__ void block_partials(double* vals, double* out_block)
+{
+    __shared__ double sh[32][kNPart];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) {
+        double x = vals[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            double y = __shfl_down_sync(0xffffffffu, x, off);
+            x = (k >= 6 && k <= 8) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) sh[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNPart) {
+        int k = threadIdx.x;
+        double x = sh[0][k];
+        for (int t = 1; t < nw; ++t) x = (k >= 6 && k <= 8) ? fmax(x, sh[t][k]) : x + sh[t][k];
+        out_block[k] = x;
+    }
+}
+// partial layout: 0 mass, 1-3 momentum, 4 KE, 5 n_chi, 6 vmax, 7 vt_max, 8 dr_max, 9 unused
+
+}  // namespace sphtv

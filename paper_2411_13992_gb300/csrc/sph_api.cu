@@ -35,6 +35,9 @@ struct sph_ctx {
     void* vr;
     float4* pos4;
     int32_t* cell;
+    float* mf;
+    uint32_t* nbl;      // FP32 form: force neighbour lists [cap][n], transposed
+    int32_t* nbc;       // FP32 form: neighbour count per particle
     void* R;
     void* chi;
     double* partials;
@@ -141,6 +144,10 @@ Consts<Real> make_consts(const sph_params* p)
     K.tv_h_particle = p->tv_h == SPH_TVH_PARTICLE;
     K.h_pair_max = p->h_pair == SPH_HPAIR_MAX;
     K.kahan = p->kahan;
+    K.uniform_h = p->h_min == p->h_max;
+    K.h_u = (Real)p->h_max;
+    K.inv_h_u = (Real)(1.0 / p->h_max);
+    K.four_h2_u = (Real)(4.0 * p->h_max * p->h_max);
     return K;
 }
 
@@ -175,9 +182,12 @@ size_t carve(sph_ctx* c, char* base)
     c->vr = W.take<char>(n * 4 * rs);
     c->pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
     c->cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
+    c->mf = c->prec == 32 ? W.take<float>(n) : nullptr;
+    c->nbl = c->prec == 32 ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
+    c->nbc = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
     c->R = W.take<char>(D * n * rs);
     c->chi = W.take<char>(n * rs);
-    c->partials = W.take<double>((size_t)pair_blocks((int)n) * kNPart);
+    c->partials = W.take<double>((size_t)pair_blocks(c->prec, (int)n) * kNPart);
     c->diag = W.take<double>(DG_COUNT);
     c->dt = W.take<double>(1);
     c->err = W.take<uint32_t>(4);
@@ -227,7 +237,7 @@ sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
     SPH_MARK(SPH_K_ORDER, 1);
     SPH_MARK(SPH_K_PERMUTE, 0);
     SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
-                          carry_ad, c->st));
+                          c->mf, c->K32.uniform_h, carry_ad, c->st));
     ++c->launches;
     SPH_MARK(SPH_K_PERMUTE, 1);
     c->cur = 1 - c->cur;
@@ -242,22 +252,23 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int n = (int)c->n;
     if (!pairs) {
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->st));
+                              c->nbl, c->nbc, c->st));
         SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->st));
-        SPH_CU(launch_finalize(pair_blocks(n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+        SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
         c->launches += 3;
         return SPH_OK;
     }
     const int write_ad = 1;
     SPH_MARK(SPH_K_DENSITY, 0);
-    SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->st));
+    SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->nbl,
+                          c->nbc, c->st));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_FORCES, 0);
-    SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->dt,
-                         kick_on, write_ad, c->R, c->chi, c->partials, c->st));
+    SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->mf, c->vr, c->pos4, c->cell,
+                         c->nbl, c->nbc, c->dt, kick_on, write_ad, c->R, c->chi, c->partials, c->st));
     SPH_MARK(SPH_K_FORCES, 1);
     SPH_MARK(SPH_K_FINALIZE, 0);
-    SPH_CU(launch_finalize(pair_blocks(n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+    SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
     SPH_MARK(SPH_K_FINALIZE, 1);
     c->launches += 3;
     return SPH_OK;
@@ -394,7 +405,8 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
         ++c->launches;
     }
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
-    c->launches += 4;
+    SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
+    c->launches += 5;
     c->have_state = 1;
     c->have_cells = 0;
     c->ad_given = a != nullptr;
@@ -494,6 +506,7 @@ sph_status sph_sync(sph_ctx* c)
     if (cudaMemcpy(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return SPH_ERR_CUDA;
     if (!e) return SPH_OK;
     if (cudaMemset(c->err, 0, sizeof(uint32_t)) != cudaSuccess) return SPH_ERR_CUDA;
+    if (e & ERRB_INPUT) return SPH_ERR_INPUT;
     if (e & ERRB_NAN) return SPH_ERR_NAN;
     if (e & ERRB_DOMAIN) return SPH_ERR_DOMAIN;
     return SPH_ERR_OVERFLOW;
@@ -586,6 +599,7 @@ const char* sph_status_str(sph_status s)
     case SPH_ERR_NAN: return "non-finite particle state";
     case SPH_ERR_DOMAIN: return "particle outside the domain";
     case SPH_ERR_STATE: return "call out of order";
+    case SPH_ERR_INPUT: return "invalid particle data (h outside [h_min, h_max] or mass not positive)";
     }
     return "unknown status";
 }

@@ -109,7 +109,7 @@ def test_null_context_and_status_strings(lib):
     assert lib.sph_step(None, 1) == 1
     assert lib.sph_set_dt(None, 1.0) == 1
     assert lib.sph_get_diag(None, None) == 1
-    for s in range(8):
+    for s in range(9):
         assert sph.sph_status_str(s) not in ("", "unknown status")
     assert sph.sph_status_str(99) == "unknown status"
     assert lib.sph_launch_count(None) == -1

@@ -221,7 +221,8 @@ def test_deterministic_and_order_independent():
         runs.append(g)
     for k in ("x", "v", "a", "rho"):
         assert np.array_equal(runs[0][k], runs[1][k]), k           # bitwise rerun
-        assert normwise(runs[2][k], runs[0][k]) <= 1e-5, k          # input order changes sums only
+        tol = TOL32_FORCE if k == "a" else TOL32_STATE            # input order changes sums only
+        assert normwise(runs[2][k], runs[0][k]) <= tol, k
 
 
 def test_state_round_trip_is_exact():
