@@ -214,6 +214,40 @@ SPH_API sph_status sph_profile_end(sph_ctx* ctx, double* ms, int64_t* count);
 /* Static name of a kernel class ("forces", ...), or "?" when out of range. */
 SPH_API const char* sph_kernel_class_name(int32_t k);
 
+/* Limits of sph_density_noalloc's fixed scratch. */
+#define SPH_NOALLOC_MAX_PARTICLES 65536
+#define SPH_NOALLOC_MAX_CELLS 65536
+
+/* Density pass without any device allocation.  This entry point has no
+ * counterpart in the paper; it exists for callers that cannot give the
+ * library a workspace: a host framework that owns all device memory and does
+ * not let its plug-ins call cudaMalloc outside its allocator, or a real-time
+ * loop where a cudaMalloc/cudaFree could synchronise the device and stall it.
+ *
+ * It computes the summation density rho_i = rho0 sum_j W_ij / sigma0_i of
+ * sph_build_cells (FP64, same kernels, same result) for n particles:
+ *   p       parameters; precision must be 64 (else SPH_ERR_ARG)
+ *   x       [n][3] positions, device memory
+ *   h, m    [n] smoothing lengths and masses, device memory
+ *   kind    [n] 0 fluid / 1 wall, device memory, or NULL (all fluid)
+ *   sigma0  [n] reference sums, device memory, or NULL (perfect-lattice sums)
+ *   rho     [n] output, device memory, in the caller's particle order
+ *   stream  cudaStream_t on which the work is enqueued; returns without waiting
+ * Its scratch is one fixed array in device memory inside the library,
+ * 24 MiB on every GPU that loads it, held until the process exits; n above
+ * SPH_NOALLOC_MAX_PARTICLES or a cell grid above SPH_NOALLOC_MAX_CELLS cells
+ * returns SPH_ERR_WORKSPACE before any work is enqueued.  The first call on
+ * each device looks up the scratch's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * scratch: the call clears the counters it sums into, but two calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller.  Device-side input checks
+ * (particles outside a non-periodic box, h outside [h_min, h_max]) are not
+ * reported by this entry point. */
+SPH_API sph_status sph_density_noalloc(const sph_params* p, int64_t n, const double* x, const double* h,
+                                       const double* m, const int8_t* kind, const double* sigma0, double* rho,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ __all__ = [
     "sph_default_params", "sph_query_workspace", "sph_create", "sph_set_state", "sph_build_cells", "sph_step",
     "sph_set_dt", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
     "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES",
-    "params_from_case", "Simulation",
+    "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "params_from_case", "Simulation",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
 ]
 
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_profile_begin": (_i32, [_vp, _i32]),
             "sph_profile_end": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
             "sph_kernel_class_name": (ctypes.c_char_p, [_i32]),
+            "sph_density_noalloc": (_i32, [pP, _i64] + [_vp] * 7),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -269,6 +270,25 @@ def sph_profile_end(ctx) -> dict:
 
 def sph_kernel_class_name(k: int) -> str:
     return load().sph_kernel_class_name(int(k)).decode()
+
+
+NOALLOC_MAX_PARTICLES = 65536
+
+
+def sph_density_noalloc(params: SphParams, n: int, x, h, m, kind, sigma0, rho, stream_ptr: int) -> None:
+    """Density pass (FP64) into ``rho`` without any device allocation: for
+    callers that cannot give the library a workspace (a host framework that
+    owns all device memory, or a real-time loop where cudaMalloc could stall
+    the device).  x, h, m, kind, sigma0 and rho are contiguous CUDA tensors
+    (kind and sigma0 may be None); the library's fixed scratch limits n to
+    NOALLOC_MAX_PARTICLES.  Calls that overlap on the GPU race on that scratch."""
+    def dp(t):
+        if t is None:
+            return None
+        assert t.is_cuda and t.is_contiguous()
+        return _vp(t.data_ptr())
+    _check(load().sph_density_noalloc(ctypes.byref(params), int(n), dp(x), dp(h), dp(m), dp(kind), dp(sigma0),
+                                      dp(rho), _vp(stream_ptr)), "sph_density_noalloc")
 
 
 # ------------------------------------------------------------------ convenience

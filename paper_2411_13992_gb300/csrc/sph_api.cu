@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -607,3 +608,96 @@ const char* sph_status_str(sph_status s)
 int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : -1; }
 
 }  // extern "C"
+
+// ------------------------------------------------------ density without allocation
+//
+// Some callers cannot hand this library a workspace: a host framework that owns
+// all device memory and whose plug-ins may not call cudaMalloc behind its
+// allocator's back, or a real-time loop in which a cudaMalloc/cudaFree (which may
+// synchronise the whole device) would stall the frame.  For them,
+// sph_density_noalloc runs the density pass on a scratch area that this library
+// reserves statically in device memory, sized for SPH_NOALLOC_MAX_PARTICLES
+// particles and SPH_NOALLOC_MAX_CELLS cells (24 MiB); every GPU that loads the library
+// holds it until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 24u << 20;   // covers 65,536 particles in 3-D (22.6 MiB)
+
+// Device-global scratch; host code must use the address from
+// cudaGetSymbolAddress, never the name itself (that is a host-side stand-in).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch on the current device; looked up once per
+// device (the first call on a device does this).
+sph_status noalloc_scratch(void** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPH_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const double* x, const double* h,
+                                          const double* m, const int8_t* kind, const double* sigma0, double* rho,
+                                          void* stream)
+{
+    sph_status s = check_params(p, n);
+    if (s != SPH_OK) return s;
+    if (p->precision != 64 || !x || !h || !m || !rho) return SPH_ERR_ARG;
+    if (n > SPH_NOALLOC_MAX_PARTICLES) return SPH_ERR_WORKSPACE;
+    const Grid G = make_grid(p);
+    if (G.ncell > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_WORKSPACE;
+    void* base = nullptr;
+    s = noalloc_scratch(&base);
+    if (s != SPH_OK) return s;
+
+    // Lay out a context-like view over the scratch (host struct only).
+    sph_ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.P = *p;
+    c.n = n;
+    c.dim = p->dim;
+    c.prec = 64;
+    c.st = (cudaStream_t)stream;
+    c.G = G;
+    c.K64 = make_consts<double>(p);
+    if (carve(&c, nullptr) > kNoAllocScratchBytes) return SPH_ERR_WORKSPACE;
+    carve(&c, (char*)base);
+
+    const int ni = (int)n;
+    const size_t nc1 = (size_t)G.ncell + 1;
+    StateSet<double>& S0 = c.set[0].d;
+    // The scratch keeps the previous call's contents: clear what is summed into.
+    SPH_CU(cudaMemsetAsync(c.count, 0, nc1 * sizeof(int32_t), c.st));
+    SPH_CU(cudaMemsetAsync(c.cursor, 0, nc1 * sizeof(int32_t), c.st));
+    SPH_CU(cudaMemsetAsync(c.err, 0, 4 * sizeof(uint32_t), c.st));
+    SPH_CU(cudaMemsetAsync(S0.v, 0, (size_t)c.dim * n * sizeof(double), c.st));
+    SPH_CU(launch_vec_in(64, c.dim, ni, x, S0.x, c.st));
+    SPH_CU(cudaMemcpyAsync(S0.h, h, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    SPH_CU(cudaMemcpyAsync(S0.m, m, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    if (kind) SPH_CU(cudaMemcpyAsync(S0.kind, kind, n, cudaMemcpyDeviceToDevice, c.st));
+    else SPH_CU(cudaMemsetAsync(S0.kind, 0, n, c.st));
+    if (sigma0) SPH_CU(cudaMemcpyAsync(S0.s0, sigma0, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    else SPH_CU(launch_sigma0(c.dim, ni, S0.h, S0.m, p->rho0, S0.s0, c.st));
+    SPH_CU(launch_init_ids(ni, S0.id, c.st));
+    c.cur = 0;
+    s = run_sort(&c, 0, 0);
+    if (s != SPH_OK) return s;
+    const StateSet<double>& S1 = c.set[c.cur].d;
+    SPH_CU(launch_density(64, c.dim, ni, cur_set(&c), c.start, c.G, consts(&c), c.vr, nullptr, nullptr, nullptr,
+                          nullptr, c.st));
+    SPH_CU(launch_rho_out(64, ni, c.vr, S1.kind, S1.id, p->rho0, rho, c.st));
+    return SPH_OK;
+}

@@ -1,0 +1,72 @@
+"""The allocation-free density entry point, sph_density_noalloc.
+
+Callers that cannot allocate device memory -- a host framework that owns all
+device memory and does not let plug-ins call cudaMalloc outside its
+allocator, or a real-time loop where a cudaMalloc/cudaFree could synchronise
+the device -- use this entry point instead of a workspace-backed context.  It
+runs the density pass on a fixed scratch array inside the library.  Its
+output must equal the workspace path's (sph_build_cells + sph_get_state),
+within the FP64 parity tolerance of the other tests, on consecutive calls:
+each call finds the scratch as the previous call left it.
+
+This file is named so that pytest collects it last."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2411_13992_gb300 as sph
+from paper_2411_13992_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _workspace_rho(case):
+    sim = sph.Simulation(case, precision=64)
+    sim.set_state()
+    sim.build_cells()
+    sim.sync()
+    rho = sim.get_state()["rho"]
+    sim.close()
+    return rho
+
+
+def _device_inputs(case):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.from_numpy(np.ascontiguousarray(case["x"])).to(dev)
+    h = torch.from_numpy(np.ascontiguousarray(case["h"])).to(dev)
+    m = torch.from_numpy(np.ascontiguousarray(case["m"])).to(dev)
+    kind = torch.from_numpy(np.ascontiguousarray(case["kind"])).to(dev)
+    return x, h, m, kind
+
+
+def test_noalloc_density_equals_the_workspace_path_on_consecutive_calls():
+    assert torch.cuda.is_available()
+    stream = torch.cuda.current_stream()
+    for case in (cases.tgv2d(64), cases.tgv3d(20), cases.cavity2d(48), cases.tgv2d(256)):
+        ref = _workspace_rho(case)
+        p = sph.params_from_case(case, 64)
+        x, h, m, kind = _device_inputs(case)
+        rho = torch.empty(case["n"], dtype=torch.float64, device=x.device)
+        for _ in range(2):
+            rho.fill_(float("nan"))
+            sph.sph_density_noalloc(p, case["n"], x, h, m, kind, None, rho, stream.cuda_stream)
+            torch.cuda.synchronize()
+            got = rho.cpu().numpy()
+            assert np.isfinite(got).all()
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err <= TOL64, (case["name"], err)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    case = cases.tgv2d(257)                      # 66,049 > 65,536 particles
+    assert case["n"] > sph.NOALLOC_MAX_PARTICLES
+    p = sph.params_from_case(case, 64)
+    x, h, m, kind = _device_inputs(case)
+    rho = torch.zeros(case["n"], dtype=torch.float64, device=x.device)
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_density_noalloc(p, case["n"], x, h, m, kind, None, rho, torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == 3                   # SPH_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert float(rho.abs().max()) == 0.0         # nothing was written
