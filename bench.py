@@ -361,13 +361,22 @@ def _pairs_per_launch(case) -> int:
 
 def _profiled_traffic():
     """DRAM bytes per launch of the forces kernel from the committed ncu
-    summary, or None when no summary for the current kernel exists."""
+    summary (profiles/forces_traffic.json), or None when the kernel sources
+    have changed since those counters were taken (the summary records a SHA-1
+    of the sources it was measured on)."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "forces_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
+        h = hashlib.sha1()
+        for rel in d["sources"]:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != d["source_sha1"]:
+            return None
         return d.get("dram_bytes_per_launch_full")
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         return None
 
 

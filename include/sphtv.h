@@ -92,7 +92,7 @@ typedef struct sph_params {
     double eta;             /* dynamic viscosity (Eq. 7) */
     double g[3];            /* body force per unit mass */
     double h_min;           /* minimum smoothing length (Eq. 9-11, 15-16) */
-    double h_max;           /* maximum smoothing length: sets the cell edge >= 2 h_max */
+    double h_max;           /* maximum smoothing length: sets the cell edge >= h_max */
     double riemann_eta;     /* dissipation limiter slope, 3 (Eq. 6) */
     double tv_xi;           /* -0.2 (Eq. 14, 16) */
     double tv_C;            /* 1e3 (Eq. 15) */
@@ -130,10 +130,12 @@ typedef struct sph_ctx sph_ctx;
  * on NULL. */
 SPH_API sph_status sph_default_params(sph_params* p);
 
-/* Bytes of device workspace a context for n particles needs.  n >= 1.
+/* Bytes of device workspace a context for n particles needs, 1 <= n <= 2^25.
  * The cell grid follows from dim, lo, L, periodic and h_max: along each
- * axis floor(L / (2 h_max)) cells (at least 3 along periodic axes, else
- * SPH_ERR_ARG).  Returns SPH_ERR_ARG on invalid parameters. */
+ * axis floor(L / h_max) cells of edge >= h_max, so the neighbours of a
+ * particle lie in the 5^D cells around its own (at least 5 cells along
+ * periodic axes, else SPH_ERR_ARG).  Returns SPH_ERR_ARG on invalid
+ * parameters. */
 SPH_API sph_status sph_query_workspace(const sph_params* p, int64_t n, size_t* bytes);
 
 /* Create a context on the current CUDA device.  workspace: device memory

@@ -24,9 +24,12 @@ enum {
     DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_COUNT = 16
 };
 
-// Cell grid of the cell-linked list: edge >= 2 h_max along every axis, so
-// every neighbour of a particle lies in the 3^D block around its cell.
+// Cell grid of the cell-linked list: edge >= 2 h_max / R along every axis,
+// so every neighbour of a particle lies in the (2R+1)^D block of cells around
+// its own (R = stencil radius in cells).
+constexpr int kStencilR = 2;
 struct Grid {
+    int R;              // stencil radius in cells
     int nc[3];
     int periodic[3];
     double lo[3];
@@ -48,7 +51,7 @@ struct Consts {
     int tv_mode, tv_h_particle, h_pair_max, kahan;
     // uniform resolution (h_min == h_max): every pair has h_ij = h
     int uniform_h;
-    Real h_u, inv_h_u, four_h2_u;
+    Real h_u, inv_h_u, four_h2_u, dwr_coef_u;   // dwr_coef_u: W'(r)/r = dwr_coef_u t^3
 };
 
 // Velocity + density deviation packed per particle for the pair pass:

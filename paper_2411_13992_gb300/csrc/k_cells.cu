@@ -165,18 +165,18 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t*
     perm[pos] = i;
 }
 
-// One warp per cell: place the cell's particles in increasing caller id
-// (ids are unique, so the rank of each is its slot).
+// One thread per cell: place the cell's particles in increasing caller id
+// (ids are unique, so the rank of each is its slot).  Cells hold about two
+// particles (edge >= h_max), so the quadratic rank count is short.
 __global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, const int32_t* __restrict__ perm_in,
                               const int32_t* __restrict__ id, int32_t* __restrict__ perm_out)
 {
-    int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
-    if (warp >= ncell) return;
-    int s = start[warp], e = start[warp + 1];
-    for (int k = s + lane; k < e; k += 32) {
-        int p = perm_in[k];
-        int myid = id[p];
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int s = start[c], e = start[c + 1];
+    for (int k = s; k < e; ++k) {
+        const int p = perm_in[k];
+        const int myid = id[p];
         int rank = 0;
         for (int t = s; t < e; ++t) rank += id[perm_in[t]] < myid;
         perm_out[s + rank] = p;
@@ -253,8 +253,7 @@ cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int
 {
     const int T = 256;
     k_scatter<<<nblk(n, T), T, 0, st>>>(n, key, start, cursor, perm_tmp);
-    int warps_per_block = T / 32;
-    k_order_cells<<<nblk(ncell, warps_per_block), T, 0, st>>>(ncell, start, perm_tmp, id, perm);
+    k_order_cells<<<nblk(ncell, T), T, 0, st>>>(ncell, start, perm_tmp, id, perm);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // k_pair.cu -- the pair passes of libsphtv, one thread per cell-sorted
-// particle, neighbours from the 3^D block of cells around it.
+// particle, neighbours from the (2R+1)^D block of cells around it.
 //
 //   k_density : sigma_i = sum_j W(r_ij, h_ij) (self and walls included),
 //               rho_i = rho0 sigma_i / sigma0_i (Eq. 8), stored as
@@ -49,14 +49,14 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     const double hi = S.h[i];
     int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
     double sigma = 0.0;
-    const int zr = DIM == 3 ? 1 : 0;
+    const int SR = G.R, zr = DIM == 3 ? SR : 0;
     for (int dz = -zr; dz <= zr; ++dz) {
         int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
         if (cz < 0) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -SR; dy <= SR; ++dy) {
             int cy = cell_step(G, c[1], dy, 1);
             if (cy < 0) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
+            for (int dx = -SR; dx <= SR; ++dx) {
                 int cx = cell_step(G, c[0], dx, 0);
                 if (cx < 0) continue;
                 int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
@@ -102,14 +102,14 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double p_i = K.c2 * me.w;
         PlainD acc_a[DIM], acc_R[DIM];
         int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
-        const int zr = DIM == 3 ? 1 : 0;
+        const int SR = G.R, zr = DIM == 3 ? SR : 0;
         for (int dz = -zr; dz <= zr; ++dz) {
             int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
             if (cz < 0) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
+            for (int dy = -SR; dy <= SR; ++dy) {
                 int cy = cell_step(G, c[1], dy, 1);
                 if (cy < 0) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
+                for (int dx = -SR; dx <= SR; ++dx) {
                     int cx = cell_step(G, c[0], dx, 0);
                     if (cx < 0) continue;
                     int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);

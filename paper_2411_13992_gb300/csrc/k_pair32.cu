@@ -1,13 +1,13 @@
 // k_pair32.cu -- FP32 pair passes of libsphtv (density and fused forces),
 // one thread per cell-sorted particle.
 //
-// The density pass scans the 3^D cells around each particle (cell-relative
+// The density pass scans the 5^D cells around each particle (cell-relative
 // FP32 positions; lanes that share a cell load the same candidate at the
 // same time), sums sigma, and records the particle's force neighbours in a
 // transposed list in HBM (entry k of particle i at k * n + i, so a warp's
 // list reads are coalesced).  The force pass then runs the pair body over
 // that list only: about 80 neighbours per particle in 3-D instead of about
-// 480 candidates, and no lane waits on another lane's candidate tests.  A
+// 275 candidates, and no lane waits on another lane's candidate tests.  A
 // particle with more neighbours than the list holds scans its cells again.
 //
 // Pair vectors keep full FP32 precision: r_ij = (o_i - o_j) + s, where o are
@@ -34,10 +34,16 @@ __device__ __forceinline__ float support2(const Consts<float>& K, float hi, floa
     return 4.f * h * h;
 }
 
-// Visit every candidate of the 3^D cells around cell_i (cell-relative FP32
-// positions plus the exact shift of the neighbour cell): f(j, code, pj, r2,
-// rx, ry, rz) with code = stencil index of the neighbour cell.  Lanes of a
-// warp whose particles share a cell read the same j at the same time, so
+// List entries: (j << kCodeBits) | stencil code of j's cell.
+constexpr int kSide = 2 * kStencilR + 1;                 // stencil cells per axis
+constexpr int kCodes = kSide * kSide * kSide;            // 125 for R = 2
+constexpr int kCodeBits = 7;
+static_assert(kCodes <= (1 << kCodeBits), "stencil code does not fit");
+
+// Visit every candidate of the (2R+1)^D cells around cell_i (cell-relative
+// FP32 positions plus the exact shift of the neighbour cell): f(j, code, pj,
+// r2, rx, ry, rz) with code = stencil index of the neighbour cell.  Lanes of
+// a warp whose particles share a cell read the same j at the same time, so
 // the loads of pos4 are warp broadcasts.
 template <int DIM, typename F>
 __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, const Grid& G,
@@ -46,21 +52,21 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 {
     int c[3];
     cell_decode(G, cell_i, c);
-    const int zr = DIM == 3 ? 1 : 0;
+    constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
     for (int dz = -zr; dz <= zr; ++dz) {
         int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
         if (cz < 0) continue;
         const float shz = -(float)dz * G.edgef[2];
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             int cy = cell_step(G, c[1], dy, 1);
             if (cy < 0) continue;
             const float shy = -(float)dy * G.edgef[1];
             const int row = G.nc[0] * (cy + G.nc[1] * cz);
-            for (int dx = -1; dx <= 1; ++dx) {
+            for (int dx = -R; dx <= R; ++dx) {
                 int cx = cell_step(G, c[0], dx, 0);
                 if (cx < 0) continue;
                 const float shx = -(float)dx * G.edgef[0];
-                const uint32_t code = (uint32_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                const uint32_t code = (uint32_t)((dx + R) + kSide * (dy + R) + kSide * kSide * (dz + R));
                 const int cell = cx + row;
                 const int j1 = start[cell + 1];
                 for (int j = start[cell]; j < j1; ++j) {
@@ -80,10 +86,52 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
     }
 }
 
+// One neighbour's contribution to a_i and R_i in the FP32 form, given
+// rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force
+// (Eq. 3, 5-7, 14) arranged for FP32 throughput -- W' only enters through
+// W'/r, (U_l - U_r) = -(v_i - v_j).r_ij / r, and each density is inverted
+// once (1/(rho_i rho_j) = (1/rho_i)(1/rho_j), V_j = m_j/rho_j).
+template <int DIM, typename Acc>
+__device__ __forceinline__ void pair_force32(const Consts<float>& K, const float* rv, float inv_r, float dwr,
+                                             const float* vi, float rho_i, float inv_rho_i, float p_i,
+                                             const float4& oj, float m_j, Acc* acc_a, Acc* acc_R)
+{
+    const bool wall = isinf(oj.w);
+    const float rho_j = wall ? rho_i : K.rho0 + oj.w;
+    const float inv_rho_j = wall ? inv_rho_i : __frcp_rn(rho_j);
+    const float p_j = wall ? p_i : K.c2 * oj.w;
+    const float dv[3] = {vi[0] - oj.x, vi[1] - oj.y, DIM == 3 ? vi[2] - oj.z : 0.f};
+    float dvr = dv[0] * rv[0] + dv[1] * rv[1];
+    if (DIM == 3) dvr += dv[2] * rv[2];
+    const float du = -dvr * inv_r;                       // U_l - U_r, e_ij from i to j
+    float beta = K.beta_slope * (du * K.inv_c);
+    beta = fminf(fmaxf(beta, 0.f), 1.f);
+    const float rhobar = 0.5f * (rho_i + rho_j);
+    const float pstar = 0.5f * (p_i + p_j) + 0.5f * beta * rhobar * K.c * du;
+    const float mr = m_j * inv_rho_i * inv_rho_j;        // m_j / (rho_i rho_j)
+    const float cpw = -2.f * mr * pstar * dwr;           // pressure: cp * W'/r
+    const float cv = K.two_eta * mr * dwr;               // viscous
+    const float vw = m_j * inv_rho_j * dwr;              // residual: V_j W'/r
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        acc_a[d].add(cpw * rv[d] + cv * dv[d]);
+        acc_R[d].add(vw * rv[d]);
+    }
+}
+
+// W'(r)/r for r < 2h: a_D h^-(D+2) (-5) t^3 with t = 1 - r/(2h).
+template <int DIM>
+__device__ __forceinline__ float dwr_of(float r, float inv_h, float coef)
+{
+    const float t = fmaf(-0.5f * inv_h, r, 1.f);
+    return coef * (t * t * t);
+}
+
 // Shift of a neighbour cell from its stencil code (as for_candidates forms it).
 __device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* sh)
 {
-    const int dx = (int)(code % 3u) - 1, dy = (int)((code / 3u) % 3u) - 1, dz = (int)(code / 9u) - 1;
+    const int dx = (int)(code % kSide) - kStencilR, dy = (int)((code / kSide) % kSide) - kStencilR,
+              dz = (int)(code / (kSide * kSide)) - kStencilR;
     sh[0] = -(float)dx * G.edgef[0];
     sh[1] = -(float)dy * G.edgef[1];
     sh[2] = -(float)dz * G.edgef[2];
@@ -93,7 +141,7 @@ __device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* 
 //
 // sigma_i over all neighbours (self included); also writes the particle's
 // force neighbour list (j != i, 0 < r^2 < 4 h_ij^2) transposed into nbl:
-// entry k of particle i at nbl[k * n + i] = (j << 5) | code, and the count
+// entry k of particle i at nbl[k * n + i] = (j << 7) | code, and the count
 // (which may exceed cap: the force kernel then scans the cells itself).
 
 template <int DIM, typename Acc, bool UNIFORM>
@@ -123,7 +171,7 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
             const float inv_h = UNIFORM ? K.inv_h_u : 1.f / pair_h(K, hi, pj.w);
             sigma.add(wendland_W<DIM, float>(sqrtf(r2), inv_h));
             if (r2 > 0.f) {
-                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << 5) | code;
+                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
                 ++cnt;
             }
         }
@@ -149,6 +197,13 @@ __global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __rest
                                                      float* __restrict__ Rout, float* __restrict__ chi_out,
                                                      double* __restrict__ partials)
 {
+    __shared__ float4 tab[kCodes];
+    for (int t = threadIdx.x; t < kCodes; t += blockDim.x) {
+        float sh[3];
+        code_shift(G, (uint32_t)t, sh);
+        tab[t] = make_float4(sh[0], sh[1], sh[2], 0.f);
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part[kNPart];
 #pragma unroll
@@ -163,48 +218,59 @@ __global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __rest
         const float vi[3] = {me.x, me.y, me.z};
         const float rho_i = K.rho0 + me.w;
         const float p_i = K.c2 * me.w;
+        const float inv_rho_i = __frcp_rn(rho_i);
         Acc acc_a[DIM], acc_R[DIM];
-        auto pair = [&](int j, const float4& pj, const float* rv, float r2) {
-            const float r = sqrtf(r2);
+        // W'/r = coef t^3, coef = -5 a_D h^-(D+2) (uniform h: one constant)
+        const float norm = kernel_norm<DIM, float>();
+        auto pair = [&](int j, const float4& pj, const float4& oj, const float* rv, float r2) {
+            const float inv_r = rsqrtf(r2);
+            const float r = r2 * inv_r;
             float inv_h, m_j;
             if (UNIFORM) {
                 inv_h = K.inv_h_u;
                 m_j = pj.w;
             } else {
-                inv_h = 1.f / pair_h(K, hi, pj.w);
+                inv_h = __frcp_rn(pair_h(K, hi, pj.w));
                 m_j = mf[j];
             }
-            const float dw = wendland_dW<DIM, float>(r, inv_h);
-            const float4 oj = vr[j];
-            const float vj[3] = {oj.x, oj.y, oj.z};
-            pair_force<float, DIM, Acc>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, m_j, acc_a, acc_R);
+            const float coef = UNIFORM ? K.dwr_coef_u : -5.f * norm * pow_dim<DIM, float>(inv_h) * inv_h * inv_h;
+            const float dwr = dwr_of<DIM>(r, inv_h, coef);
+            pair_force32<DIM, Acc>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, oj, m_j, acc_a, acc_R);
         };
         const int cnt = nbc[i];
         if (cnt <= cap) {
-            // the neighbour list of the density pass: no candidate tests
+            // the neighbour list of the density pass: no candidate tests;
+            // the next neighbour's data is loaded while this one is computed
+            uint32_t e = cnt > 0 ? nbl[i] : 0u;
+            float4 pj_n = pos4[e >> kCodeBits];
+            float4 oj_n = vr[e >> kCodeBits];
             for (int k = 0; k < cnt; ++k) {
-                const uint32_t e = nbl[(size_t)k * n + i];
-                const int j = (int)(e >> 5);
-                const float4 pj = pos4[j];
-                float sh[3];
-                code_shift(G, e & 31u, sh);
+                const uint32_t ec = e;
+                const float4 pj = pj_n;
+                const float4 oj = oj_n;
+                if (k + 1 < cnt) {
+                    e = nbl[(size_t)(k + 1) * n + i];
+                    pj_n = pos4[e >> kCodeBits];
+                    oj_n = vr[e >> kCodeBits];
+                }
+                const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
                 float rv[3];
-                rv[0] = (oi[0] - pj.x) + sh[0];
-                rv[1] = (oi[1] - pj.y) + sh[1];
+                rv[0] = (oi[0] - pj.x) + sh.x;
+                rv[1] = (oi[1] - pj.y) + sh.y;
                 float r2 = rv[0] * rv[0] + rv[1] * rv[1];
                 rv[2] = 0.f;
                 if (DIM == 3) {
-                    rv[2] = (oi[2] - pj.z) + sh[2];
+                    rv[2] = (oi[2] - pj.z) + sh.z;
                     r2 += rv[2] * rv[2];
                 }
-                pair(j, pj, rv, r2);
+                pair((int)(ec >> kCodeBits), pj, oj, rv, r2);
             }
         } else {
             // more neighbours than the list holds: scan the cells
             auto visit = [&](int j, uint32_t, const float4& pj, float r2, float rx, float ry, float rz) {
                 if (r2 < support2<UNIFORM>(K, hi, pj.w) && r2 > 0.f) {
                     const float rv[3] = {rx, ry, rz};
-                    pair(j, pj, rv, r2);
+                    pair(j, pj, vr[j], rv, r2);
                 }
             };
             for_candidates<DIM>(oi, cell_of[i], G, start, pos4, visit);

@@ -74,7 +74,7 @@ struct Carver {
 
 sph_status check_params(const sph_params* p, int64_t n)
 {
-    if (!p || n < 1 || n > (int64_t)0x7fffffff) return SPH_ERR_ARG;
+    if (!p || n < 1 || n > ((int64_t)1 << 25)) return SPH_ERR_ARG;   // list entries hold j in 25 bits
     if (p->dim != 2 && p->dim != 3) return SPH_ERR_ARG;
     if (p->precision != 32 && p->precision != 64) return SPH_ERR_ARG;
     if (!(p->rho0 > 0) || !(p->c0 > 0) || !(p->eta >= 0)) return SPH_ERR_ARG;
@@ -84,8 +84,8 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
     for (int d = 0; d < p->dim; ++d) {
         if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
-        double nc = std::floor(p->L[d] / (2.0 * p->h_max));
-        if (p->periodic[d] && nc < 3) return SPH_ERR_ARG;
+        double nc = std::floor(p->L[d] * kStencilR / (2.0 * p->h_max));
+        if (p->periodic[d] && nc < 2 * kStencilR + 1) return SPH_ERR_ARG;
         if (nc > 1 << 20) return SPH_ERR_ARG;
     }
     return SPH_OK;
@@ -94,10 +94,11 @@ sph_status check_params(const sph_params* p, int64_t n)
 Grid make_grid(const sph_params* p)
 {
     Grid G;
+    G.R = kStencilR;
     int64_t ncell = 1;
     for (int d = 0; d < 3; ++d) {
         if (d < p->dim) {
-            int nc = (int)std::floor(p->L[d] / (2.0 * p->h_max));
+            int nc = (int)std::floor(p->L[d] * kStencilR / (2.0 * p->h_max));
             if (nc < 1) nc = 1;
             G.nc[d] = nc;
             G.periodic[d] = p->periodic[d] ? 1 : 0;
@@ -149,6 +150,12 @@ Consts<Real> make_consts(const sph_params* p)
     K.h_u = (Real)p->h_max;
     K.inv_h_u = (Real)(1.0 / p->h_max);
     K.four_h2_u = (Real)(4.0 * p->h_max * p->h_max);
+    {
+        // W'(r)/r = -5 a_D h^-(D+2) t^3 with a_D = 7/(4 pi) (2-D), 21/(16 pi) (3-D)
+        const double pi = 3.14159265358979323846;
+        const double norm = p->dim == 2 ? 7.0 / (4.0 * pi) : 21.0 / (16.0 * pi);
+        K.dwr_coef_u = (Real)(-5.0 * norm * std::pow(1.0 / p->h_max, p->dim + 2));
+    }
     return K;
 }
 

@@ -80,7 +80,7 @@ def test_workspace_query_and_argument_checks(lib):
     bad = [
         dict(dim=4), dict(precision=16), dict(rho0=0.0), dict(c0=-1.0), dict(eta=-1.0), dict(h_min=0.0),
         dict(h_max=0.5 * c["h_min"]), dict(tv_mode=3), dict(fixed_dt=-1.0),
-        dict(h_max=0.3),          # fewer than 3 cells along a periodic axis
+        dict(h_max=0.3),          # fewer than 5 cells along a periodic axis
     ]
     for kw in bad:
         q = sph.params_from_case(c, 64)
