@@ -147,6 +147,13 @@ def lib():
                                                   ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
                 "orc_step": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
                                             ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]),
+                "orc_kernel_d2W": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+                "orc_riemann_dbeta": (ctypes.c_double, [_pp, ctypes.c_double]),
+                "orc_tv_dlimiter": (ctypes.c_double, [_pp, ctypes.c_double]),
+                "orc_step_adjoint": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
+                                                    ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
+                "orc_force_pass_adjoint": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
+                                                          ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -352,6 +359,74 @@ def step_reversed_sums(P, case, state, sigma0, dt):
     f = forces(P, x, v, h, m, kind, vw, rho, nb)
     v = kick(P, v, f["a"], kind, hdt)
     return {"x": x, "v": v, "a": f["a"], "dr": f["dr"], "rho": rho, "R": f["R"], "chi": f["chi"]}
+
+
+def kernel_d2W(r, h, dim):
+    return lib().orc_kernel_d2W(float(r), float(h), int(dim))
+
+
+def step_adjoint(P, case, state, sigma0, dt, cot, mode="cells"):
+    """Reverse of ``step`` (neighbour lists and dt frozen).  ``state`` is the
+    step's input (x, v, a, dr); ``cot`` holds the cotangents of its outputs
+    (x, v, a, dr).  Returns (cotangents of the inputs, d/d eta)."""
+    n = len(state["x"])
+    x, v = _vec(state["x"], n), _vec(state["v"], n)
+    a, dr = _vec(state["a"], n), _vec(state["dr"], n)
+    h, m, kind, vw = _case_arrays(case, n)
+    s0 = _sca(sigma0, n)
+    xb, vb = _vec(cot["x"], n).copy(), _vec(cot["v"], n).copy()
+    ab, drb = _vec(cot["a"], n).copy(), _vec(cot["dr"], n).copy()
+    eb = ctypes.c_double(0.0)
+    rc = lib().orc_step_adjoint(ctypes.byref(P), n, _d(x), _d(v), _d(a), _d(dr), _d(h), _d(m),
+                                kind.ctypes.data_as(_bp), _d(vw), _d(s0), float(dt), {"brute": 0, "cells": 1}[mode],
+                                _d(xb), _d(vb), _d(ab), _d(drb), ctypes.byref(eb))
+    if rc:
+        raise MemoryError("oracle step adjoint failed")
+    return {"x": xb, "v": vb, "a": ab, "dr": drb}, eb.value
+
+
+def force_pass_adjoint(P, case, x, v, sigma0, abar, drbar, mode="cells"):
+    """Reverse of ``force_pass``: cotangents of (x, v) and d/d eta from those
+    of (a, dr)."""
+    n = len(x)
+    x, v = _vec(x, n), _vec(v, n)
+    h, m, kind, vw = _case_arrays(case, n)
+    s0 = _sca(sigma0, n)
+    A, D = _vec(abar, n), _vec(drbar, n)
+    xb, vb = np.zeros((n, 3)), np.zeros((n, 3))
+    eb = ctypes.c_double(0.0)
+    rc = lib().orc_force_pass_adjoint(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp),
+                                      _d(vw), _d(s0), {"brute": 0, "cells": 1}[mode], _d(A), _d(D), _d(xb), _d(vb),
+                                      ctypes.byref(eb))
+    if rc:
+        raise MemoryError("oracle force-pass adjoint failed")
+    return xb, vb, eb.value
+
+
+def rollout(P, case, x0, v0, sigma0, dt, nsteps, mode="cells"):
+    """Initial force pass on (x0, v0), then ``nsteps`` steps: the states
+    [s_0, ..., s_T] (each a dict x, v, a, dr, ...)."""
+    fp = force_pass(P, case, x0, v0, sigma0, mode)
+    st = {"x": _vec(x0, len(x0)).copy(), "v": _vec(v0, len(v0)).copy(), "a": fp["a"], "dr": fp["dr"],
+          "rho": fp["rho"]}
+    out = [st]
+    for _ in range(nsteps):
+        st = step(P, case, st, sigma0, dt, mode)
+        out.append(st)
+    return out
+
+
+def rollout_adjoint(P, case, states, sigma0, dt, cot_T, mode="cells"):
+    """Gradients of a loss with cotangents ``cot_T`` (x, v, a, dr of the last
+    state) back to (x0, v0) and eta, through every step and the initial
+    force pass."""
+    cot = {k: np.array(v, dtype=np.float64) for k, v in cot_T.items()}
+    eta_bar = 0.0
+    for k in range(len(states) - 1, 0, -1):
+        cot, eb = step_adjoint(P, case, states[k - 1], sigma0, dt, cot, mode)
+        eta_bar += eb
+    xb, vb, eb = force_pass_adjoint(P, case, states[0]["x"], states[0]["v"], sigma0, cot["a"], cot["dr"], mode)
+    return cot["x"] + xb, cot["v"] + vb, eta_bar + eb
 
 
 def sigma0_for(case, dim):

@@ -552,3 +552,219 @@ int orc_step(const orc_params* P, int64_t n, double* x, double* v, double* a, do
     orc_kick(P, n, hdt, v, a, kind);
     return 0;
 }
+
+/* ===================================================================
+ * Adjoint (reverse mode) of the step with the neighbour lists and dt
+ * frozen.  Not in the paper: derived by hand from the formulas above.
+ * Subgradients at the kinks: d beta/d dU = eta_R / c inside
+ * 0 < eta_R dU / c < 1 and 0 elsewhere (Eq. 6); d chi / d s = C inside
+ * thresh < s < 1/C and 0 elsewhere (Eq. 15, limited form).
+ * =================================================================== */
+
+/* d^2 W / dr^2 of the Wendland C2 kernel. */
+double orc_kernel_d2W(double r, double h, int dim)
+{
+    double q = r / h;
+    if (q >= 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return kernel_alpha(h, dim) / (h * h) * (-5.0) * t * t * (1.0 - 2.0 * q);
+}
+
+double orc_riemann_dbeta(const orc_params* P, double du)
+{
+    double b = P->riemann_eta * du / P->c;
+    return (b > 0.0 && b < 1.0) ? P->riemann_eta / P->c : 0.0;
+}
+
+double orc_tv_dlimiter(const orc_params* P, double s)
+{
+    if (P->tv_mode != 1) return 0.0;
+    return (s > P->tv_thresh && P->tv_C * s < 1.0) ? P->tv_C : 0.0;
+}
+
+/* Reverse of orc_density + orc_forces at fixed neighbour lists.  Given the
+ * cotangents Abar of a and Dbar of dr (fluid particles), add to xbar the
+ * cotangents of the positions, to vbar those of the velocities the forces
+ * used, and to *etabar that of the dynamic viscosity.  rho and R are the
+ * forward values on the same positions. */
+void orc_forces_adjoint(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                        const double* m, const int8_t* kind, const double* vw, const double* rho,
+                        const double* sigma0, const int64_t* start, const int64_t* idx, const double* R,
+                        const double* Abar, const double* Dbar, double* xbar, double* vbar, double* etabar)
+{
+    const double c = P->c, c2 = c * c;
+    double* rhob = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* Rb = (double*)calloc((size_t)(n > 0 ? 3 * n : 1), sizeof(double));
+    double etab = 0.0;
+    /* 1. transport-velocity displacement dr = xi chi(s) H^2 R, s = H^2 |R|^2 */
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        double H = P->tv_h_per_particle ? h[i] : P->h_min;
+        double H2 = H * H;
+        const double* Ri = R + 3 * i;
+        const double* Di = Dbar + 3 * i;
+        double s = H2 * dot3(Ri, Ri);
+        double chi = orc_tv_limiter(P, s), dchi = orc_tv_dlimiter(P, s);
+        double DR = dot3(Di, Ri);
+        for (int d = 0; d < 3; ++d) Rb[3 * i + d] = P->tv_xi * H2 * (chi * Di[d] + dchi * DR * 2.0 * H2 * Ri[d]);
+    }
+    /* 2. pair terms of a_i and R_i */
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        const double rho_i = rho[i];
+        const double p_i = c2 * (rho_i - P->rho0);
+        const double* vi = v + 3 * i;
+        const double* Ai = Abar + 3 * i;
+        const double* Rbi = Rb + 3 * i;
+        for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+            int64_t j = idx[k];
+            if (j == i) continue;
+            double rij[3];
+            orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+            double q = norm3(rij);
+            if (q == 0.0) continue;
+            double hij = orc_pair_h(P, h[i], h[j]);
+            double w = orc_kernel_dW(q, hij, P->dim);
+            double w2 = orc_kernel_d2W(q, hij, P->dim);
+            double u[3], dv[3];
+            int wall = kind[j] != 0;
+            double rho_j = wall ? rho_i : rho[j];
+            double p_j = wall ? p_i : c2 * (rho_j - P->rho0);
+            const double* vj = wall ? vw + 3 * j : v + 3 * j;
+            for (int d = 0; d < 3; ++d) {
+                u[d] = rij[d] / q;
+                dv[d] = vi[d] - vj[d];
+            }
+            double dU = -dot3(dv, u);                       /* U_l - U_r */
+            double beta = orc_riemann_beta(P, -dot3(vi, u), -dot3(vj, u));
+            double dbeta = orc_riemann_dbeta(P, dU);
+            double rbar_ = 0.5 * (rho_i + rho_j);
+            double pstar = 0.5 * (p_i + p_j) + 0.5 * beta * rbar_ * c * dU;
+            double K = m[j] / (rho_i * rho_j);
+            double Au = dot3(Ai, u), Adv = dot3(Ai, dv), Ru = dot3(Rbi, u);
+            double Pb = -2.0 * K * w * Au;
+            double Kb = -2.0 * pstar * w * Au + 2.0 * P->eta * (w / q) * Adv;
+            double wb = -2.0 * K * pstar * Au + (m[j] / rho_j) * Ru;
+            double wqb = 2.0 * K * P->eta * Adv;
+            etab += 2.0 * K * (w / q) * Adv;
+            double dUb = Pb * 0.5 * rbar_ * c * (beta + dU * dbeta);
+            double rbarb = Pb * 0.5 * beta * c * dU;
+            double ub[3], dvb[3], rb[3];
+            for (int d = 0; d < 3; ++d) {
+                ub[d] = -2.0 * K * pstar * w * Ai[d] + (m[j] / rho_j) * w * Rbi[d] - dUb * dv[d];
+                dvb[d] = 2.0 * K * P->eta * (w / q) * Ai[d] - dUb * u[d];
+            }
+            double rho_i_b = -K / rho_i * Kb + 0.5 * rbarb + c2 * 0.5 * Pb;
+            double rho_j_b = -K / rho_j * Kb + 0.5 * rbarb + c2 * 0.5 * Pb - (m[j] / (rho_j * rho_j)) * w * Ru;
+            rhob[i] += rho_i_b;
+            if (wall) rhob[i] += rho_j_b;          /* rho_j stands for rho_i, p_j for p_i */
+            else rhob[j] += rho_j_b;
+            double uu = dot3(ub, u);
+            for (int d = 0; d < 3; ++d)
+                rb[d] = (ub[d] - uu * u[d]) / q + w2 * wb * u[d] + (w2 / q - w / (q * q)) * wqb * u[d];
+            for (int d = 0; d < 3; ++d) {
+                xbar[3 * i + d] += rb[d];
+                vbar[3 * i + d] += dvb[d];
+                if (!wall) {
+                    xbar[3 * j + d] -= rb[d];
+                    vbar[3 * j + d] -= dvb[d];
+                }
+            }
+        }
+    }
+    /* 3. density summation rho_i = rho0 sigma_i / sigma0_i */
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        double sb = rhob[i] * P->rho0 / sigma0[i];
+        for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+            int64_t j = idx[k];
+            if (j == i) continue;
+            double rij[3];
+            orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+            double q = norm3(rij);
+            if (q == 0.0) continue;
+            double w = orc_kernel_dW(q, orc_pair_h(P, h[i], h[j]), P->dim);
+            for (int d = 0; d < 3; ++d) {
+                double g = sb * w * rij[d] / q;
+                xbar[3 * i + d] += g;
+                if (!kind[j]) xbar[3 * j + d] -= g;
+            }
+        }
+    }
+    *etabar += etab;
+    free(rhob);
+    free(Rb);
+}
+
+/* Adjoint of orc_step.  On entry xbar, vbar, abar, drbar hold the
+ * cotangents of the step's outputs (x', v', a', dr'); on return those of its
+ * inputs (x, v, a, dr).  *etabar is incremented.  The forward internals are
+ * recomputed from the inputs x, v, a, dr (unchanged).  Walls get zeros. */
+int orc_step_adjoint(const orc_params* P, int64_t n, const double* x, const double* v, const double* a,
+                     const double* dr, const double* h, const double* m, const int8_t* kind, const double* vw,
+                     const double* sigma0, double dt, int mode, double* xbar, double* vbar, double* abar,
+                     double* drbar, double* etabar)
+{
+    size_t nb = (size_t)(n > 0 ? 3 * n : 1) * sizeof(double);
+    double* xp = (double*)malloc(nb);
+    double* vh = (double*)malloc(nb);
+    double* A = (double*)malloc(nb);
+    double* Rf = (double*)malloc(nb);
+    double* af = (double*)malloc(nb);
+    double* drf = (double*)malloc(nb);
+    double* rho = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!xp || !vh || !A || !Rf || !af || !drf || !rho) return -1;
+    memcpy(xp, x, nb);
+    memcpy(vh, v, nb);
+    double hdt = 0.5 * dt;
+    orc_kick(P, n, hdt, vh, a, kind);
+    orc_drift(P, n, dt, xp, vh, dr, kind);
+    nbrlist L;
+    if (nbr_build(P, n, xp, h, mode, &L)) return -1;
+    orc_density(P, n, xp, h, kind, sigma0, L.start, L.idx, rho, NULL);
+    orc_forces(P, n, xp, vh, h, m, kind, vw, rho, L.start, L.idx, af, Rf, NULL, drf);
+    /* v' = vh + hdt a'  ->  abar' += hdt vbar', vhbar = vbar' */
+    for (int64_t i = 0; i < 3 * n; ++i) A[i] = abar[i] + hdt * vbar[i];
+    /* vbar now holds vhbar; xbar holds xbar' */
+    orc_forces_adjoint(P, n, xp, vh, h, m, kind, vw, rho, sigma0, L.start, L.idx, Rf, A, drbar, xbar, vbar,
+                       etabar);
+    /* x' = x + dt vh + dr ;  vh = v + hdt a */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            int64_t o = 3 * i + d;
+            if (kind[i]) {
+                xbar[o] = vbar[o] = abar[o] = drbar[o] = 0.0;
+                continue;
+            }
+            drbar[o] = xbar[o];
+            vbar[o] += dt * xbar[o];
+            abar[o] = hdt * vbar[o];
+        }
+    }
+    nbr_free(&L);
+    free(xp); free(vh); free(A); free(Rf); free(af); free(drf); free(rho);
+    return 0;
+}
+
+/* Adjoint of the initial force pass (a, dr from x, v): given Abar, Dbar,
+ * add to xbar and vbar and increment *etabar. */
+int orc_force_pass_adjoint(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                           const double* m, const int8_t* kind, const double* vw, const double* sigma0, int mode,
+                           const double* Abar, const double* Dbar, double* xbar, double* vbar, double* etabar)
+{
+    size_t nb = (size_t)(n > 0 ? 3 * n : 1) * sizeof(double);
+    double* Rf = (double*)malloc(nb);
+    double* af = (double*)malloc(nb);
+    double* drf = (double*)malloc(nb);
+    double* rho = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!Rf || !af || !drf || !rho) return -1;
+    nbrlist L;
+    if (nbr_build(P, n, x, h, mode, &L)) return -1;
+    orc_density(P, n, x, h, kind, sigma0, L.start, L.idx, rho, NULL);
+    orc_forces(P, n, x, v, h, m, kind, vw, rho, L.start, L.idx, af, Rf, NULL, drf);
+    orc_forces_adjoint(P, n, x, v, h, m, kind, vw, rho, sigma0, L.start, L.idx, Rf, Abar, Dbar, xbar, vbar,
+                       etabar);
+    nbr_free(&L);
+    free(Rf); free(af); free(drf); free(rho);
+    return 0;
+}
