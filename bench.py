@@ -297,6 +297,9 @@ def run_native(args):
     # ---- end to end through the C ABI with host buffers
     e2e = _e2e(torch, sph, case, args, dist)
 
+    # ---- adjoint / forward time on the adjoint workload
+    adjoint = _adjoint_ratio(torch, sph, cases) if not args.no_adjoint else None
+
     # ---- roofline of the dominant kernel (FP32 forces), live event timing
     peaks, src = _peaks()
     f_ms, f_cnt = prof["forces"]
@@ -339,6 +342,7 @@ def run_native(args):
             "roofline": roof,
             "kernels": kernels,
             "e2e": e2e,
+            "adjoint": adjoint,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -420,6 +424,43 @@ def _e2e(torch, sph, case, args, dist):
             "path": "sph_set_state (pinned host) + sph_build_cells + sph_step(1) + sph_get_state (pinned host)"}
 
 
+def _adjoint_ratio(torch, sph, cases):
+    """Backward / forward time of a checkpointed rollout: 2-D Taylor-Green
+    256^2 = 65,536 particles, 50 steps, checkpoints every 10 steps, loss =
+    final kinetic energy, FP32 forward and adjoint.  Forward = the rollout
+    with its checkpoint copies; backward = segment replays + reverse steps +
+    the adjoint of the initial force pass (gradients w.r.t. v0 and nu)."""
+    c = cases.tgv2d(256)
+    nsteps, every = 50, 10
+    sim = sph.Simulation(c, precision=32, fixed_dt=2.77e-4, adjoint_steps=every)
+    dev = sim.device
+    x0 = torch.tensor(c["x"], dtype=torch.float64, device=dev)
+    m = torch.tensor(c["m"], dtype=torch.float64, device=dev)
+
+    def once():
+        v0 = torch.tensor(c["v"], dtype=torch.float64, device=dev, requires_grad=True)
+        nu = torch.tensor(c["nu"], dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xT, vT = sph.Rollout.apply(x0, v0, nu, sim, nsteps, every)
+        ke = 0.5 * (m[:, None] * vT ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ke.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1
+
+    once()
+    runs = [once() for _ in range(3)]
+    fwd = min(r[0] for r in runs)
+    bwd = min(r[1] for r in runs)
+    sim.close()
+    return {"workload": "2-D Taylor-Green 256^2 = 65,536 particles, 50 steps, checkpoints every 10, FP32",
+            "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "adjoint_over_forward": bwd / fwd,
+            "timing": "host wall clock around synchronised calls, best of 3 after 1 warm-up"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,6 +473,7 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=128, help="lattice side of the CPU-baseline sample")
     ap.add_argument("--ref-n", type=int, default=64, help="lattice side of the reference arm's per-step sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -104,7 +104,8 @@ typedef struct sph_params {
     int32_t tv_h;           /* SPH_TVH_*: h in Eq. 14-16 is h_min (paper) or h_i */
     int32_t h_pair;         /* SPH_HPAIR_*: h_ij = (h_i+h_j)/2 (default) or max */
     int32_t kahan;          /* FP32 form: 1 = compensated pair sums (default) */
-    int32_t reserved;
+    int32_t adjoint_steps;  /* longest segment sph_step_adjoint will replay
+                               (0: no adjoint buffers in the workspace) */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -170,6 +171,10 @@ SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
 /* Override the step size of the next step (> 0). */
 SPH_API sph_status sph_set_dt(sph_ctx* ctx, double dt);
 
+/* Set the dynamic viscosity eta (>= 0, Eq. 7) used from the next launch on
+ * (for example to evaluate a rollout at another viscosity). */
+SPH_API sph_status sph_set_eta(sph_ctx* ctx, double eta);
+
 /* Copy the state out in the caller's original particle order.  Any pointer
  * may be NULL.  x, v, a, dr: [n][3]; rho: [n] (walls report rho0).  Waits
  * for the copy when a destination is host memory. */
@@ -215,6 +220,44 @@ SPH_API sph_status sph_profile_end(sph_ctx* ctx, double* ms, int64_t* count);
 
 /* Static name of a kernel class ("forces", ...), or "?" when out of range. */
 SPH_API const char* sph_kernel_class_name(int32_t k);
+
+/* Adjoint of a segment of nsteps steps (reverse mode), with every step's
+ * neighbour set and step size frozen (not in the paper; the derivatives of
+ * Eq. 2-8 and 14-16 are taken by hand).  Subgradients at the kinks: the
+ * Riemann limiter (Eq. 6) has d beta / d dU = eta_R / c inside
+ * 0 < eta_R dU / c < 1 and 0 elsewhere; the transport-velocity limiter
+ * (Eq. 15) has d chi / d s = C inside thresh < s < 1/C and 0 elsewhere.
+ *
+ *   x0, v0, a0, dr0  [n][3] checkpoint state at the start of the segment, in
+ *                    the caller's order (host or device), e.g. from
+ *                    sph_get_state at that step of the forward run
+ *   nsteps           1 <= nsteps <= params.adjoint_steps
+ *   xbar, vbar, abar, drbar  [n][3] (host or device, caller order): on entry
+ *                    the cotangents of the state after the segment, on
+ *                    return those of the checkpoint state
+ *   etabar           on return d(loss)/d(eta) accumulated over the segment
+ *                    (host double; may be NULL)
+ * The library replays the segment from the checkpoint (the cell sort is
+ * deterministic, so the replay reproduces the forward run bit for bit),
+ * keeping per-step values in its workspace, then runs the reverse steps.
+ * On return the context holds the replayed state after the segment.  The
+ * FP32 form computes pair derivatives in FP32 with compensated sums and
+ * keeps the cotangents in FP64.  Waits for the stream.  SPH_ERR_ARG for
+ * nsteps outside [1, adjoint_steps] or NULL arrays. */
+SPH_API sph_status sph_step_adjoint(sph_ctx* ctx, const double* x0, const double* v0, const double* a0,
+                                    const double* dr0, int32_t nsteps, double* xbar, double* vbar, double* abar,
+                                    double* drbar, double* etabar);
+
+/* Adjoint of the initial force pass of sph_build_cells (a and dr from x and
+ * v, no a/dr given): with abar, drbar the cotangents of that pass's a and dr
+ * ([n][3], caller order), ADD the cotangents of x and v to xbar and vbar and
+ * write d/d(eta) to *etabar (may be NULL).  Loads x and v into the context
+ * (as sph_set_state + sph_build_cells would, with the smoothing lengths,
+ * masses, kinds and prescribed wall velocities of the last sph_set_state;
+ * the walls' entries of v are ignored).  Waits for the stream.
+ * Requires params.adjoint_steps >= 1. */
+SPH_API sph_status sph_force_pass_adjoint(sph_ctx* ctx, const double* x, const double* v, const double* abar,
+                                          const double* drbar, double* xbar, double* vbar, double* etabar);
 
 /* Limits of sph_density_noalloc's fixed scratch. */
 #define SPH_NOALLOC_MAX_PARTICLES 65536

@@ -28,9 +28,10 @@ from . import _build
 __all__ = [
     "SphParams", "SphDiag", "SphError", "load", "exported_symbols", "declared_symbols",
     "sph_default_params", "sph_query_workspace", "sph_create", "sph_set_state", "sph_build_cells", "sph_step",
-    "sph_set_dt", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
+    "sph_set_dt", "sph_set_eta", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
     "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES",
-    "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "params_from_case", "Simulation",
+    "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint",
+    "params_from_case", "Simulation", "Rollout",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
 ]
 
@@ -56,7 +57,8 @@ class SphParams(ctypes.Structure):
         ("tv_xi", ctypes.c_double), ("tv_C", ctypes.c_double), ("tv_thresh", ctypes.c_double),
         ("cfl_ad", ctypes.c_double), ("cfl_ac", ctypes.c_double), ("u_ref", ctypes.c_double),
         ("fixed_dt", ctypes.c_double),
-        ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32),
+        ("adjoint_steps", ctypes.c_int32),
     ]
 
 
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_build_cells": (_i32, [_vp]),
             "sph_step": (_i32, [_vp, _i32]),
             "sph_set_dt": (_i32, [_vp, ctypes.c_double]),
+            "sph_set_eta": (_i32, [_vp, ctypes.c_double]),
             "sph_get_state": (_i32, [_vp] + [_vp] * 5),
             "sph_get_diag": (_i32, [_vp, ctypes.POINTER(SphDiag)]),
             "sph_sync": (_i32, [_vp]),
@@ -120,6 +123,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_profile_end": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
             "sph_kernel_class_name": (ctypes.c_char_p, [_i32]),
             "sph_density_noalloc": (_i32, [pP, _i64] + [_vp] * 7),
+            "sph_step_adjoint": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
+                                        ctypes.POINTER(ctypes.c_double)]),
+            "sph_force_pass_adjoint": (_i32, [_vp] + [_vp] * 6 + [ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -218,6 +224,10 @@ def sph_set_dt(ctx, dt: float) -> None:
     _check(load().sph_set_dt(ctx, float(dt)), "sph_set_dt")
 
 
+def sph_set_eta(ctx, eta: float) -> None:
+    _check(load().sph_set_eta(ctx, float(eta)), "sph_set_eta")
+
+
 def sph_get_state(ctx, x=None, v=None, a=None, dr=None, rho=None) -> None:
     """Write into caller-provided buffers (numpy or torch, contiguous float64)."""
     def p(t):
@@ -289,6 +299,47 @@ def sph_density_noalloc(params: SphParams, n: int, x, h, m, kind, sigma0, rho, s
         return _vp(t.data_ptr())
     _check(load().sph_density_noalloc(ctypes.byref(params), int(n), dp(x), dp(h), dp(m), dp(kind), dp(sigma0),
                                       dp(rho), _vp(stream_ptr)), "sph_density_noalloc")
+
+
+def _p64(t, keep):
+    """Pointer to a contiguous float64 array (numpy or torch, host or CUDA)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        assert t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+        return _vp(t.data_ptr())
+    arr = np.ascontiguousarray(t, dtype=np.float64)
+    keep.append(arr)
+    return _vp(arr.ctypes.data)
+
+
+def sph_step_adjoint(ctx, x0, v0, a0, dr0, nsteps: int, xbar, vbar, abar, drbar) -> float:
+    """Reverse of ``nsteps`` steps from the checkpoint (x0, v0, a0, dr0).
+    xbar, vbar, abar, drbar ([n][3] float64, numpy or torch, written in place)
+    hold the cotangents of the state after the segment on entry and those of
+    the checkpoint on return.  Returns d/d(eta) over the segment."""
+    keep = []
+    eta = ctypes.c_double(0.0)
+    for t in (xbar, vbar, abar, drbar):
+        if not hasattr(t, "data_ptr"):
+            assert isinstance(t, np.ndarray) and t.flags["C_CONTIGUOUS"] and t.dtype == np.float64
+    ptr = lambda t: _p64(t, keep) if hasattr(t, "data_ptr") else _vp(t.ctypes.data)
+    _check(load().sph_step_adjoint(ctx, _p64(x0, keep), _p64(v0, keep), _p64(a0, keep), _p64(dr0, keep),
+                                   int(nsteps), ptr(xbar), ptr(vbar), ptr(abar), ptr(drbar), ctypes.byref(eta)),
+           "sph_step_adjoint")
+    return eta.value
+
+
+def sph_force_pass_adjoint(ctx, x, v, abar, drbar, xbar, vbar) -> float:
+    """Reverse of the initial force pass on (x, v): ADD the cotangents of x
+    and v to xbar, vbar (in place) given those of a and dr; returns
+    d/d(eta)."""
+    keep = []
+    eta = ctypes.c_double(0.0)
+    ptr = lambda t: _p64(t, keep) if hasattr(t, "data_ptr") else _vp(t.ctypes.data)
+    _check(load().sph_force_pass_adjoint(ctx, _p64(x, keep), _p64(v, keep), _p64(abar, keep), _p64(drbar, keep),
+                                         ptr(xbar), ptr(vbar), ctypes.byref(eta)), "sph_force_pass_adjoint")
+    return eta.value
 
 
 # ------------------------------------------------------------------ convenience
@@ -372,3 +423,74 @@ class Simulation:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+class Rollout:
+    """Differentiable rollout through libsphtv: (x0, v0, nu) -> (x_T, v_T).
+
+    Forward: initial force pass on (x0, v0), then ``nsteps`` kick-drift-kick
+    steps of the context's fixed dt, keeping the state every ``every`` steps
+    (device FP64 tensors).  Backward: the library's hand-written adjoint,
+    segment by segment from the last checkpoint (each segment is replayed
+    from its checkpoint inside sph_step_adjoint), then the adjoint of the
+    initial force pass; d/d(nu) = rho0 d/d(eta).  Neighbour sets and dt are
+    frozen per step.  Use ``Rollout.apply(x0, v0, nu, sim, nsteps, every)``
+    with a Simulation created with fixed_dt > 0 and adjoint_steps >= every.
+    """
+
+    @staticmethod
+    def _function():
+        import torch
+
+        class _Rollout(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, x0, v0, nu, sim, nsteps, every):
+                dev = sim.device
+                x0d = x0.detach().to(device=dev, dtype=torch.float64).contiguous()
+                v0d = v0.detach().to(device=dev, dtype=torch.float64).contiguous()
+                sph_set_eta(sim.ctx, float(nu) * sim.params.rho0)
+                c = sim.case
+                sph_set_state(sim.ctx, x0d, v0d, None, None, c["h"], c["m"], c.get("kind"), c.get("vw"), None)
+                sph_build_cells(sim.ctx)
+                ckpts = []
+                done = 0
+                while done < nsteps:
+                    seg = min(every, nsteps - done)
+                    st = {k: torch.empty((sim.n, 3), dtype=torch.float64, device=dev) for k in ("x", "v", "a", "dr")}
+                    sph_get_state(sim.ctx, st["x"], st["v"], st["a"], st["dr"], None)
+                    ckpts.append((st, seg))
+                    sph_step(sim.ctx, seg)
+                    done += seg
+                xT = torch.empty((sim.n, 3), dtype=torch.float64, device=dev)
+                vT = torch.empty_like(xT)
+                sph_get_state(sim.ctx, xT, vT, None, None, None)
+                fctx.sim, fctx.ckpts, fctx.x0, fctx.v0 = sim, ckpts, x0d, v0d
+                fctx.in_dev, fctx.in_dtype = x0.device, x0.dtype
+                return xT, vT
+
+            @staticmethod
+            def backward(fctx, gx, gv):
+                sim = fctx.sim
+                dev = sim.device
+                z = lambda g: (torch.zeros((sim.n, 3), dtype=torch.float64, device=dev) if g is None
+                               else g.detach().to(device=dev, dtype=torch.float64).contiguous().clone())
+                xb, vb = z(gx), z(gv)
+                ab = torch.zeros_like(xb)
+                drb = torch.zeros_like(xb)
+                etab = 0.0
+                for st, seg in reversed(fctx.ckpts):
+                    etab += sph_step_adjoint(sim.ctx, st["x"], st["v"], st["a"], st["dr"], seg, xb, vb, ab, drb)
+                etab += sph_force_pass_adjoint(sim.ctx, fctx.x0, fctx.v0, ab, drb, xb, vb)
+                gnu = torch.tensor(etab * sim.params.rho0, dtype=torch.float64)
+                return (xb.to(fctx.in_dev, fctx.in_dtype), vb.to(fctx.in_dev, fctx.in_dtype), gnu, None, None, None)
+
+        return _Rollout
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, x0, v0, nu, sim, nsteps: int, every: int):
+        if cls._fn is None:
+            cls._fn = cls._function()
+        return cls._fn.apply(x0, v0, nu, sim, nsteps, every)
+

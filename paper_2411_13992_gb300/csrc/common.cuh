@@ -94,6 +94,16 @@ __device__ __forceinline__ Real wendland_dW(Real r, Real inv_h)
     return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * inv_h * (Real(-5) * q) * (t * t * t);
 }
 
+// d^2W/dr^2 (r, h) for r < 2h.
+template <int DIM, typename Real>
+__device__ __forceinline__ Real wendland_d2W(Real r, Real inv_h)
+{
+    Real q = r * inv_h;
+    Real t = Real(1) - Real(0.5) * q;
+    return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * inv_h * inv_h * Real(-5) * (t * t) *
+           (Real(1) - Real(2) * q);
+}
+
 // ------------------------------------------------------- compensated sum
 
 struct KSum {

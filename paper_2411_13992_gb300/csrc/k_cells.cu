@@ -65,7 +65,10 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
     if (e) atomicOr(err, e);
     int k = cell_index<DIM>(G, xs);
     key[i] = k;
-    atomicAdd(&count[k], 1);
+    // Lanes of a warp are neighbours in the cell order and mostly share a
+    // cell: one atomic per distinct cell in the warp.
+    const unsigned peers = __match_any_sync(__activemask(), k);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[k], __popc(peers));
 }
 
 // ------------------------------------------------------- exclusive scan
@@ -160,8 +163,17 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t*
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int k = key[i];
-    int pos = start[k] + atomicAdd(&cursor[k], 1);
+    const int k = key[i];
+    // warp-aggregated slot reservation (the order inside a cell is fixed
+    // afterwards by k_order_cells)
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[k], __popc(peers));
+    base = __shfl_sync(act, base, leader);
+    const int pos = start[k] + base + __popc(peers & ((1u << lane) - 1u));
     perm[pos] = i;
 }
 

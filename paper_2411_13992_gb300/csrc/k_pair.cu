@@ -217,6 +217,24 @@ __global__ void __launch_bounds__(256) k_diag_only(int n, StateSet<Real> S, doub
 
 // =========================================================== finalize
 
+// First level of the diagnostics reduction: block b folds rows
+// [b * chunk, (b + 1) * chunk) of the per-block partials into row b of out,
+// in a fixed order (the result does not depend on timing).
+__global__ void __launch_bounds__(256) k_reduce_rows(int nrows, int chunk, const double* __restrict__ in,
+                                                     double* __restrict__ out)
+{
+    double acc[kNPart];
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) acc[k] = 0.0;
+    const int r0 = blockIdx.x * chunk, r1 = min(nrows, r0 + chunk);
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const double* p = in + (size_t)r * kNPart;
+#pragma unroll
+        for (int k = 0; k < kNPart; ++k) acc[k] = (k >= 6 && k <= 8) ? fmax(acc[k], p[k]) : acc[k] + p[k];
+    }
+    block_partials(acc, out + (size_t)blockIdx.x * kNPart);
+}
+
 struct DtConsts {
     double eta, rho0, h_min, u_ref, cfl_ad, cfl_ac, c, fixed_dt;
 };
@@ -315,11 +333,20 @@ cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int nblocks, const double* partials, const sph_params& P, double* diag, double* dt,
-                            int count_step, cudaStream_t st)
+int reduce_rows_blocks() { return 256; }
+
+cudaError_t launch_finalize(int nblocks, const double* partials, double* rows, const sph_params& P, double* diag,
+                            double* dt, int count_step, cudaStream_t st)
 {
     DtConsts D{P.eta, P.rho0, P.h_min, P.u_ref, P.cfl_ad, P.cfl_ac, P.c0, P.fixed_dt};
-    k_finalize<<<1, 256, 0, st>>>(nblocks, partials, D, diag, dt, count_step);
+    const int G = reduce_rows_blocks();
+    if (nblocks > 4 * G) {
+        const int chunk = (nblocks + G - 1) / G;
+        k_reduce_rows<<<G, 256, 0, st>>>(nblocks, chunk, partials, rows);
+        k_finalize<<<1, 256, 0, st>>>(G, rows, D, diag, dt, count_step);
+    } else {
+        k_finalize<<<1, 256, 0, st>>>(nblocks, partials, D, diag, dt, count_step);
+    }
     return cudaGetLastError();
 }
 

@@ -10,6 +10,31 @@
 
 namespace sphtv {
 
+// Forward values of one step kept for the adjoint (device pointers).
+struct TapeView {
+    const int32_t* id;
+    const int8_t* kind;
+    const double* x;
+    const double* h;
+    const double* m;
+    const double* s0;
+    const void* vr;
+    const void* R;
+    const int32_t* start;
+    const float4* pos4;
+    const int32_t* cell;
+    const double* dt;
+};
+
+// Adjoint buffers: cotangents in the caller's order ([3][n] FP64) and
+// per-step scratch in the sorted order.
+struct AdjView {
+    double *xc, *vc, *ac, *drc;
+    void *Ab, *Rb, *xbp, *vbp, *sigb;
+    double* partials;
+    double* eta;
+};
+
 // k_cells.cu
 cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const double* dt, int drift, const Grid& G,
                                   int32_t* key, int32_t* count, uint32_t* err, cudaStream_t st);
@@ -44,8 +69,9 @@ cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const
                             const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
                             void* Rout, void* chi, double* partials, cudaStream_t st);
 cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st);
-cudaError_t launch_finalize(int nblocks, const double* partials, const sph_params& P, double* diag, double* dt,
-                            int count_step, cudaStream_t st);
+int reduce_rows_blocks();
+cudaError_t launch_finalize(int nblocks, const double* partials, double* rows, const sph_params& P, double* diag,
+                            double* dt, int count_step, cudaStream_t st);
 
 // k_io.cu
 cudaError_t launch_vec_in(int prec, int dim, int n, const double* src3, void* dst, cudaStream_t st);
@@ -61,5 +87,12 @@ cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, 
 cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,
                                cudaStream_t st);
 cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st);
+
+// k_adjoint.cu
+int adj_pair_blocks(int n);
+cudaError_t launch_adjoint_step(int prec, int dim, int n, const TapeView& V, const Grid& G, const void* K,
+                                const AdjView& A, int step_mode, cudaStream_t st);
+cudaError_t launch_aos_to_soa(int n, const double* src3, double* dst, cudaStream_t st);
+cudaError_t launch_soa_to_aos(int n, const double* src, double* dst3, cudaStream_t st);
 
 }  // namespace sphtv

@@ -22,6 +22,20 @@ struct SetPtrs {
     StateSet<float> f;
 };
 
+// One step's forward values kept for the adjoint.
+struct TapeSlot {
+    int32_t* id;
+    int8_t* kind;
+    double* x;
+    double *h, *m, *s0;
+    void* vr;
+    void* R;
+    int32_t* start;
+    float4* pos4;
+    int32_t* cell;
+    double* dt;
+};
+
 struct sph_ctx {
     sph_params P;
     int64_t n;
@@ -42,6 +56,7 @@ struct sph_ctx {
     void* R;
     void* chi;
     double* partials;
+    double* rows;        // first-level reduction of the partials
     double* diag;
     double* dt;
     uint32_t* err;
@@ -49,6 +64,13 @@ struct sph_ctx {
     int have_state, have_cells, ad_given;
     int64_t launches;
     double host_dt;
+    // adjoint (params.adjoint_steps > 0): tape slots, the per-particle
+    // constants in the caller's order, cotangents and scratch
+    TapeSlot* tape;
+    double *orig_h, *orig_m, *orig_s0;
+    double* orig_vw;      // [n][3] prescribed wall velocities
+    int8_t* orig_kind;
+    AdjView adj;
     // per-kernel timing (sph_profile_begin / sph_profile_end)
     std::vector<cudaEvent_t>* prof_ev;   // [step][class][begin, end]
     std::vector<int>* prof_used;         // [step][class] 0/1
@@ -82,6 +104,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->tv_mode < 0 || p->tv_mode > 2 || p->tv_h < 0 || p->tv_h > 1 || p->h_pair < 0 || p->h_pair > 1)
         return SPH_ERR_ARG;
     if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
+    if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
     for (int d = 0; d < p->dim; ++d) {
         if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
         double nc = std::floor(p->L[d] * kStencilR / (2.0 * p->h_max));
@@ -196,10 +219,47 @@ size_t carve(sph_ctx* c, char* base)
     c->R = W.take<char>(D * n * rs);
     c->chi = W.take<char>(n * rs);
     c->partials = W.take<double>((size_t)pair_blocks(c->prec, (int)n) * kNPart);
+    c->rows = W.take<double>((size_t)reduce_rows_blocks() * kNPart);
     c->diag = W.take<double>(DG_COUNT);
     c->dt = W.take<double>(1);
     c->err = W.take<uint32_t>(4);
     c->stage = W.take<double>(3 * n);
+    const int K = c->P.adjoint_steps;
+    if (K > 0) {
+        c->orig_h = W.take<double>(n);
+        c->orig_m = W.take<double>(n);
+        c->orig_s0 = W.take<double>(n);
+        c->orig_vw = W.take<double>(3 * n);
+        c->orig_kind = W.take<int8_t>(n);
+        for (int t = 0; t < K; ++t) {
+            TapeSlot sl;
+            sl.id = W.take<int32_t>(n);
+            sl.kind = W.take<int8_t>(n);
+            sl.x = W.take<double>(D * n);
+            sl.h = W.take<double>(n);
+            sl.m = W.take<double>(n);
+            sl.s0 = W.take<double>(n);
+            sl.vr = W.take<char>(n * 4 * rs);
+            sl.R = W.take<char>(D * n * rs);
+            sl.start = W.take<int32_t>(nc1);
+            sl.pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
+            sl.cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
+            sl.dt = W.take<double>(1);
+            if (base && c->tape) c->tape[t] = sl;
+        }
+        AdjView& A = c->adj;
+        A.xc = W.take<double>(3 * n);
+        A.vc = W.take<double>(3 * n);
+        A.ac = W.take<double>(3 * n);
+        A.drc = W.take<double>(3 * n);
+        A.Ab = W.take<char>(D * n * rs);
+        A.Rb = W.take<char>(D * n * rs);
+        A.xbp = W.take<char>(D * n * rs);
+        A.vbp = W.take<char>(D * n * rs);
+        A.sigb = W.take<char>(n * rs);
+        A.partials = W.take<double>((size_t)adj_pair_blocks((int)n) * kNPart);
+        A.eta = W.take<double>(1);
+    }
     return (W.off + kAlign - 1) & ~(kAlign - 1);
 }
 
@@ -262,7 +322,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
                               c->nbl, c->nbc, c->st));
         SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->st));
-        SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+        SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->rows, c->P, c->diag, c->dt, count_step, c->st));
         c->launches += 3;
         return SPH_OK;
     }
@@ -276,7 +336,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
                          c->nbl, c->nbc, c->dt, kick_on, write_ad, c->R, c->chi, c->partials, c->st));
     SPH_MARK(SPH_K_FORCES, 1);
     SPH_MARK(SPH_K_FINALIZE, 0);
-    SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->P, c->diag, c->dt, count_step, c->st));
+    SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->rows, c->P, c->diag, c->dt, count_step, c->st));
     SPH_MARK(SPH_K_FINALIZE, 1);
     c->launches += 3;
     return SPH_OK;
@@ -291,6 +351,104 @@ bool is_host_ptr(const void* p)
     }
     return attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
 }
+
+
+// ------------------------------------------------------------------ adjoint
+
+// Load a state (caller order) with the per-particle constants of the last
+// sph_set_state.  a and dr may be NULL (then computed by the force pass).
+sph_status reload_state(sph_ctx* c, const double* x, const double* v, const double* a, const double* dr)
+{
+    const size_t n = (size_t)c->n;
+    const size_t vb = 3 * n * sizeof(double);
+    const size_t rs = c->prec == 64 ? 8 : 4;
+    c->cur = 0;
+    StateSet<double>& Sd = c->set[0].d;
+    void* sv = c->prec == 64 ? (void*)c->set[0].d.v : (void*)c->set[0].f.v;
+    void* sa = c->prec == 64 ? (void*)c->set[0].d.a : (void*)c->set[0].f.a;
+    void* sdr = c->prec == 64 ? (void*)c->set[0].d.dr : (void*)c->set[0].f.dr;
+    SPH_CU(cudaMemcpyAsync(c->stage, x, vb, cudaMemcpyDefault, c->st));
+    SPH_CU(launch_vec_in(64, c->dim, (int)n, c->stage, Sd.x, c->st));
+    SPH_CU(cudaMemcpyAsync(c->stage, v, vb, cudaMemcpyDefault, c->st));
+    SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sv, c->st));
+    if (a) {
+        SPH_CU(cudaMemcpyAsync(c->stage, a, vb, cudaMemcpyDefault, c->st));
+        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sa, c->st));
+        SPH_CU(cudaMemcpyAsync(c->stage, dr, vb, cudaMemcpyDefault, c->st));
+        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sdr, c->st));
+        c->launches += 2;
+    } else {
+        SPH_CU(cudaMemsetAsync(sa, 0, c->dim * n * rs, c->st));
+        SPH_CU(cudaMemsetAsync(sdr, 0, c->dim * n * rs, c->st));
+    }
+    SPH_CU(cudaMemcpyAsync(Sd.h, c->orig_h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(Sd.m, c->orig_m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(Sd.s0, c->orig_s0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(Sd.kind, c->orig_kind, n, cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(launch_walls_velocity(c->prec, c->dim, (int)n, Sd.kind, c->orig_vw, sv, c->st));
+    SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
+    c->launches += 4;
+    c->have_state = 1;
+    c->have_cells = 0;
+    c->ad_given = a != nullptr;
+    return SPH_OK;
+}
+
+// Copy the current step's forward values into tape slot t (dt is copied by
+// the caller before the step runs).
+sph_status save_tape(sph_ctx* c, int t)
+{
+    const size_t n = (size_t)c->n;
+    const size_t rs = c->prec == 64 ? 8 : 4;
+    const size_t nc1 = (size_t)c->G.ncell + 1;
+    const StateSet<double>& S = c->set[c->cur].d;
+    TapeSlot& T = c->tape[t];
+    SPH_CU(cudaMemcpyAsync(T.id, S.id, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.kind, S.kind, n, cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.x, S.x, c->dim * n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.h, S.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.m, S.m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.s0, S.s0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.vr, c->vr, n * 4 * rs, cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.R, c->R, c->dim * n * rs, cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(T.start, c->start, nc1 * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+    if (c->prec == 32) {
+        SPH_CU(cudaMemcpyAsync(T.pos4, c->pos4, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->st));
+        SPH_CU(cudaMemcpyAsync(T.cell, c->cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+    }
+    return SPH_OK;
+}
+
+TapeView tape_view(const TapeSlot& T)
+{
+    return TapeView{T.id, T.kind, T.x, T.h, T.m, T.s0, T.vr, T.R, T.start, T.pos4, T.cell, T.dt};
+}
+
+// Caller [n][3] cotangents -> [3][n] FP64 (z row zeroed in 2-D), and back.
+sph_status cot_in(sph_ctx* c, const double* src, double* dst)
+{
+    const size_t n = (size_t)c->n;
+    SPH_CU(cudaMemcpyAsync(c->stage, src, 3 * n * sizeof(double), cudaMemcpyDefault, c->st));
+    SPH_CU(launch_aos_to_soa((int)n, c->stage, dst, c->st));
+    if (c->dim == 2) SPH_CU(cudaMemsetAsync(dst + 2 * n, 0, n * sizeof(double), c->st));
+    ++c->launches;
+    return SPH_OK;
+}
+
+sph_status cot_out(sph_ctx* c, const double* src, double* dst)
+{
+    const size_t n = (size_t)c->n;
+    SPH_CU(launch_soa_to_aos((int)n, src, c->stage, c->st));
+    SPH_CU(cudaMemcpyAsync(dst, c->stage, 3 * n * sizeof(double), cudaMemcpyDefault, c->st));
+    ++c->launches;
+    return SPH_OK;
+}
+
+#define SPH_TRY(call)                    \
+    do {                                 \
+        sph_status s_ = (call);          \
+        if (s_ != SPH_OK) return s_;     \
+    } while (0)
 
 }  // namespace
 
@@ -357,6 +515,13 @@ sph_status sph_create(const sph_params* p, int64_t n, void* workspace, size_t by
         delete c;
         return SPH_ERR_WORKSPACE;
     }
+    if (p->adjoint_steps > 0) {
+        c->tape = new (std::nothrow) TapeSlot[p->adjoint_steps];
+        if (!c->tape) {
+            delete c;
+            return SPH_ERR_ARG;
+        }
+    }
     carve(c, (char*)workspace);
     if (cudaMemsetAsync(c->err, 0, 4 * sizeof(uint32_t), c->st) != cudaSuccess ||
         cudaMemsetAsync(c->diag, 0, DG_COUNT * sizeof(double), c->st) != cudaSuccess) {
@@ -407,6 +572,10 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     else SPH_CU(cudaMemsetAsync(Sd.kind, 0, n, c->st));
     if (vw) SPH_CU(cudaMemcpyAsync(c->stage, vw, vb, cudaMemcpyDefault, c->st));
     SPH_CU(launch_walls_velocity(c->prec, c->dim, (int)n, Sd.kind, vw ? c->stage : nullptr, sv, c->st));
+    if (c->P.adjoint_steps > 0) {
+        if (vw) SPH_CU(cudaMemcpyAsync(c->orig_vw, c->stage, vb, cudaMemcpyDeviceToDevice, c->st));
+        else SPH_CU(cudaMemsetAsync(c->orig_vw, 0, vb, c->st));
+    }
     if (sigma0) SPH_CU(cudaMemcpyAsync(Sd.s0, sigma0, n * sizeof(double), cudaMemcpyDefault, c->st));
     else {
         SPH_CU(launch_sigma0(c->dim, (int)n, Sd.h, Sd.m, c->P.rho0, Sd.s0, c->st));
@@ -415,6 +584,12 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
     c->launches += 5;
+    if (c->P.adjoint_steps > 0) {
+        SPH_CU(cudaMemcpyAsync(c->orig_h, Sd.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        SPH_CU(cudaMemcpyAsync(c->orig_m, Sd.m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        SPH_CU(cudaMemcpyAsync(c->orig_s0, Sd.s0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        SPH_CU(cudaMemcpyAsync(c->orig_kind, Sd.kind, n, cudaMemcpyDeviceToDevice, c->st));
+    }
     c->have_state = 1;
     c->have_cells = 0;
     c->ad_given = a != nullptr;
@@ -453,6 +628,15 @@ sph_status sph_set_dt(sph_ctx* c, double dt)
     c->host_dt = dt;
     SPH_CU(cudaMemcpyAsync(c->dt, &c->host_dt, sizeof(double), cudaMemcpyHostToDevice, c->st));
     SPH_CU(cudaStreamSynchronize(c->st));
+    return SPH_OK;
+}
+
+sph_status sph_set_eta(sph_ctx* c, double eta)
+{
+    if (!c || !(eta >= 0) || !std::isfinite(eta)) return SPH_ERR_ARG;
+    c->P.eta = eta;
+    c->K64 = make_consts<double>(&c->P);
+    c->K32 = make_consts<float>(&c->P);
     return SPH_OK;
 }
 
@@ -593,6 +777,7 @@ void sph_destroy(sph_ctx* c)
 {
     if (!c) return;
     prof_free(c);
+    delete[] c->tape;
     delete c;
 }
 
@@ -610,6 +795,68 @@ const char* sph_status_str(sph_status s)
     case SPH_ERR_INPUT: return "invalid particle data (h outside [h_min, h_max] or mass not positive)";
     }
     return "unknown status";
+}
+
+sph_status sph_step_adjoint(sph_ctx* c, const double* x0, const double* v0, const double* a0, const double* dr0,
+                            int32_t nsteps, double* xbar, double* vbar, double* abar, double* drbar, double* etabar)
+{
+    if (!c || !x0 || !v0 || !a0 || !dr0 || !xbar || !vbar || !abar || !drbar) return SPH_ERR_ARG;
+    if (c->P.adjoint_steps < 1 || nsteps < 1 || nsteps > c->P.adjoint_steps) return SPH_ERR_ARG;
+    if (!c->have_state) return SPH_ERR_STATE;
+    SPH_TRY(reload_state(c, x0, v0, a0, dr0));
+    SPH_TRY(sph_build_cells(c));
+    for (int t = 0; t < nsteps; ++t) {
+        SPH_CU(cudaMemcpyAsync(c->tape[t].dt, c->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        SPH_TRY(run_sort(c, 1, 0));
+        SPH_TRY(run_forces(c, 1, 1, 1));
+        SPH_TRY(save_tape(c, t));
+    }
+    AdjView& A = c->adj;
+    SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
+    SPH_TRY(cot_in(c, xbar, A.xc));
+    SPH_TRY(cot_in(c, vbar, A.vc));
+    SPH_TRY(cot_in(c, abar, A.ac));
+    SPH_TRY(cot_in(c, drbar, A.drc));
+    for (int t = nsteps - 1; t >= 0; --t) {
+        SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), c->G, consts(c), A, 1, c->st));
+        c->launches += 4;
+    }
+    SPH_TRY(cot_out(c, A.xc, xbar));
+    SPH_TRY(cot_out(c, A.vc, vbar));
+    SPH_TRY(cot_out(c, A.ac, abar));
+    SPH_TRY(cot_out(c, A.drc, drbar));
+    double eta = 0.0;
+    SPH_CU(cudaMemcpyAsync(&eta, A.eta, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SPH_CU(cudaStreamSynchronize(c->st));
+    if (etabar) *etabar = eta;
+    return SPH_OK;
+}
+
+sph_status sph_force_pass_adjoint(sph_ctx* c, const double* x, const double* v, const double* abar,
+                                  const double* drbar, double* xbar, double* vbar, double* etabar)
+{
+    if (!c || !x || !v || !abar || !drbar || !xbar || !vbar) return SPH_ERR_ARG;
+    if (c->P.adjoint_steps < 1) return SPH_ERR_ARG;
+    if (!c->have_state) return SPH_ERR_STATE;
+    SPH_TRY(reload_state(c, x, v, nullptr, nullptr));
+    SPH_TRY(sph_build_cells(c));
+    SPH_TRY(save_tape(c, 0));
+    SPH_CU(cudaMemsetAsync(c->tape[0].dt, 0, sizeof(double), c->st));
+    AdjView& A = c->adj;
+    SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
+    SPH_TRY(cot_in(c, xbar, A.xc));
+    SPH_TRY(cot_in(c, vbar, A.vc));
+    SPH_TRY(cot_in(c, abar, A.ac));
+    SPH_TRY(cot_in(c, drbar, A.drc));
+    SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[0]), c->G, consts(c), A, 0, c->st));
+    c->launches += 4;
+    SPH_TRY(cot_out(c, A.xc, xbar));
+    SPH_TRY(cot_out(c, A.vc, vbar));
+    double eta = 0.0;
+    SPH_CU(cudaMemcpyAsync(&eta, A.eta, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SPH_CU(cudaStreamSynchronize(c->st));
+    if (etabar) *etabar = eta;
+    return SPH_OK;
 }
 
 int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : -1; }
@@ -674,6 +921,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     sph_ctx c;
     std::memset(&c, 0, sizeof(c));
     c.P = *p;
+    c.P.adjoint_steps = 0;
     c.n = n;
     c.dim = p->dim;
     c.prec = 64;

@@ -1,0 +1,142 @@
+"""GPU adjoint (sph_step_adjoint, sph_force_pass_adjoint, Rollout) against
+the oracle's FP64 adjoint and against central finite differences.
+
+Tolerances (normwise relative, per cotangent field):
+  FP64 form vs the oracle adjoint: 1e-12 (both FP64; they differ only in the
+    order of the pair sums; measured 1e-14 .. 4e-14).
+  FP32 form vs the oracle adjoint: 1e-4 (FP32 pair derivatives with
+    compensated sums, FP64 cotangents; measured 2e-6 .. 2.3e-5).
+  Rollout gradient (KE after 50 steps of the 2-D Taylor-Green 256^2, FP32
+    forward and adjoint, checkpoints every 10 steps) vs central differences
+    of the FP64 forward (relative step 1e-4): 1e-4 for the viscosity and for
+    a random direction of the initial velocity (measured ~1e-7).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2411_13992_gb300 as sph
+from paper_2411_13992_gb300 import cases
+
+from gpu_helpers import lib_overrides, normwise, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available()
+    oracle.set_threads(16)
+
+
+def _case(kind):
+    if kind == "tgv":
+        return cases.tgv2d(16, jitter_dp=0.12, seed=3)
+    if kind == "cavity":
+        return cases.cavity2d(12, U=1.0, jitter_dp=0.12, seed=3)
+    return cases.tgv3d(8, jitter_dp=0.12, seed=3)
+
+
+def _weights(c, rng):
+    n, D = c["n"], c["dim"]
+    w = {k: np.zeros((n, 3)) for k in ("x", "v", "a", "dr")}
+    for k, scale in (("x", 1.0), ("v", 1.0), ("a", 1e-2), ("dr", 1e3)):
+        w[k][:, :D] = rng.standard_normal((n, D)) * scale
+    return w
+
+
+def _library_gradients(c, prec, dt, T, wts, **kw):
+    sim = sph.Simulation(c, precision=prec, fixed_dt=dt, adjoint_steps=T, **lib_overrides(**kw))
+    try:
+        sim.set_state()
+        sim.build_cells()
+        s0 = sim.get_state()
+        xb, vb, ab, drb = (np.ascontiguousarray(wts[k].copy()) for k in ("x", "v", "a", "dr"))
+        eb = sph.sph_step_adjoint(sim.ctx, s0["x"], s0["v"], s0["a"], s0["dr"], T, xb, vb, ab, drb)
+        eb += sph.sph_force_pass_adjoint(sim.ctx, c["x"], c["v"], ab, drb, xb, vb)
+        sim.sync()
+        return xb, vb, eb
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("kind", ["tgv", "cavity", "3d"])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-4)])
+def test_adjoint_matches_the_oracle_adjoint(kind, prec, tol):
+    c = _case(kind)
+    P = oracle_params(c)
+    s0 = oracle.sigma0_for(c, c["dim"])
+    dt = 0.5 * oracle.time_step(P, c["v"], c["kind"])
+    T = 3
+    wts = _weights(c, np.random.default_rng(11))
+    states = oracle.rollout(P, c, c["x"], c["v"], s0, dt, T)
+    xr, vr, er = oracle.rollout_adjoint(P, c, states, s0, dt, wts)
+    xb, vb, eb = _library_gradients(c, prec, dt, T, wts)
+    fl = c["kind"] == 0
+    ex, ev = normwise(xb[fl], xr[fl]), normwise(vb[fl], vr[fl])
+    ee = abs(eb - er) / abs(er)
+    print(kind, prec, "x %.2e v %.2e eta %.2e" % (ex, ev, ee))
+    assert ex <= tol and ev <= tol and ee <= tol, (ex, ev, ee)
+
+
+def test_adjoint_with_unlimited_correction_and_variable_resolution():
+    c = cases.cylinder2d(D=1.0, res=10, box=(3.0, 2.0), center=(1.0, 1.0), refine=(0.6, 2.4, 0.4, 1.6),
+                         band_dp=2.0, jitter_dp=0.05)
+    opts = {"tv_mode": oracle.TV_UNLIMITED}
+    P = oracle_params(c, **opts)
+    s0 = oracle.sigma0_for(c, 2)
+    dt = 0.5 * oracle.time_step(P, c["v"], c["kind"])
+    wts = _weights(c, np.random.default_rng(5))
+    states = oracle.rollout(P, c, c["x"], c["v"], s0, dt, 2)
+    xr, vr, er = oracle.rollout_adjoint(P, c, states, s0, dt, wts)
+    xb, vb, eb = _library_gradients(c, 64, dt, 2, wts, **opts)
+    fl = c["kind"] == 0
+    assert normwise(xb[fl], xr[fl]) <= 1e-12
+    assert normwise(vb[fl], vr[fl]) <= 1e-12
+    assert abs(eb - er) <= 1e-12 * abs(er)
+
+
+def _ke_rollout_fp64(c, dt, nsteps, v0, nu):
+    sim = sph.Simulation(c, precision=64, fixed_dt=dt, eta=c["rho0"] * nu)
+    try:
+        sim.set_state(v=v0)
+        sim.build_cells()
+        sim.step(nsteps)
+        sim.sync()
+        g = sim.get_state()
+        return 0.5 * (c["m"][:, None] * g["v"] ** 2).sum()
+    finally:
+        sim.close()
+
+
+def test_rollout_gradients_match_central_differences():
+    """The adjoint workload: 2-D Taylor-Green 256^2, 50 steps, checkpoints
+    every 10, loss = final kinetic energy; FP32 forward and adjoint."""
+    c = cases.tgv2d(256)
+    nu = c["nu"]
+    dt = 2.77e-4
+    nsteps, every = 50, 10
+    sim = sph.Simulation(c, precision=32, fixed_dt=dt, adjoint_steps=every)
+    dev = sim.device
+    x0 = torch.tensor(c["x"], dtype=torch.float64, device=dev)
+    v0 = torch.tensor(c["v"], dtype=torch.float64, device=dev, requires_grad=True)
+    nu_t = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+    m = torch.tensor(c["m"], dtype=torch.float64, device=dev)
+    xT, vT = sph.Rollout.apply(x0, v0, nu_t, sim, nsteps, every)
+    ke = 0.5 * (m[:, None] * vT ** 2).sum()
+    ke.backward()
+    g_nu = float(nu_t.grad)
+    rng = np.random.default_rng(2)
+    dv = np.zeros_like(c["v"])
+    dv[:, :2] = rng.standard_normal((c["n"], 2))
+    g_v = float((v0.grad.cpu().numpy() * dv).sum())
+    sim.close()
+    e = 1e-4
+    fd_nu = (_ke_rollout_fp64(c, dt, nsteps, c["v"], nu * (1 + e)) -
+             _ke_rollout_fp64(c, dt, nsteps, c["v"], nu * (1 - e))) / (2 * e * nu)
+    fd_v = (_ke_rollout_fp64(c, dt, nsteps, c["v"] + e * dv, nu) -
+            _ke_rollout_fp64(c, dt, nsteps, c["v"] - e * dv, nu)) / (2 * e)
+    print("nu: adjoint %.8g fd %.8g | v: adjoint %.8g fd %.8g" % (g_nu, fd_nu, g_v, fd_v))
+    assert abs(g_nu - fd_nu) <= 1e-4 * abs(fd_nu)
+    assert abs(g_v - fd_v) <= 1e-4 * abs(fd_v)
