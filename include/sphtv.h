@@ -71,7 +71,7 @@ typedef enum sph_status {
     SPH_ERR_INPUT = 8       /* device: a particle's h outside [h_min, h_max] or mass not positive */
 } sph_status;
 
-enum { SPH_TV_OFF = 0, SPH_TV_LIMITED = 1, SPH_TV_UNLIMITED = 2 };
+enum { SPH_TV_OFF = 0, SPH_TV_LIMITED = 1, SPH_TV_UNLIMITED = 2, SPH_TV_BACKGROUND = 3 };
 enum { SPH_TVH_MIN = 0, SPH_TVH_PARTICLE = 1 };
 enum { SPH_HPAIR_MEAN = 0, SPH_HPAIR_MAX = 1 };
 
@@ -83,7 +83,10 @@ typedef struct sph_params {
                                Kahan compensation, FP32 cell-relative positions,
                                FP64 positions for the drift and FP64 reductions */
     int32_t periodic[3];    /* 1: periodic along that axis */
-    int32_t tv_mode;        /* SPH_TV_*: none / limited (Eq. 16) / unlimited (Eq. 14) */
+    int32_t tv_mode;        /* SPH_TV_*: none / limited (Eq. 16) / unlimited (Eq. 14) /
+                               background pressure p0 = rho0 c^2 (Eq. 12): the drift
+                               adds dt^2/2 a_bg, a_bg = -2 sum_j m_j p0/(rho_i rho_j) grad W_ij,
+                               with the dt of the step that computed it */
     double lo[3];           /* domain lower corner */
     double L[3];            /* domain lengths; every particle must stay in
                                [lo, lo+L] along non-periodic axes */
@@ -243,7 +246,8 @@ SPH_API const char* sph_kernel_class_name(int32_t k);
  * On return the context holds the replayed state after the segment.  The
  * FP32 form computes pair derivatives in FP32 with compensated sums and
  * keeps the cotangents in FP64.  Waits for the stream.  SPH_ERR_ARG for
- * nsteps outside [1, adjoint_steps] or NULL arrays. */
+ * nsteps outside [1, adjoint_steps], NULL arrays, or tv_mode
+ * SPH_TV_BACKGROUND (no adjoint for that mode). */
 SPH_API sph_status sph_step_adjoint(sph_ctx* ctx, const double* x0, const double* v0, const double* a0,
                                     const double* dr0, int32_t nsteps, double* xbar, double* vbar, double* abar,
                                     double* drbar, double* etabar);

@@ -46,7 +46,7 @@ _LIBPATH = os.path.join(_BUILD, "libsph_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-TV_NONE, TV_LIMITED, TV_UNLIMITED = 0, 1, 2
+TV_NONE, TV_LIMITED, TV_UNLIMITED, TV_BACKGROUND = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +88,7 @@ class Params(ctypes.Structure):
         ("cfl_ad", ctypes.c_double),
         ("cfl_ac", ctypes.c_double),
         ("u_ref", ctypes.c_double),
+        ("dt_tv", ctypes.c_double),
     ]
 
 
@@ -350,6 +351,8 @@ def step_reversed_sums(P, case, state, sigma0, dt):
     n = len(state["x"])
     h, m, kind, vw = _case_arrays(case, n)
     hdt = 0.5 * dt
+    saved_dt_tv = P.dt_tv
+    P.dt_tv = dt
     v = kick(P, state["v"], state["a"], kind, hdt)
     x = drift(P, state["x"], v, state["dr"], kind, dt)
     start, idx = neighbours(P, x, h)
@@ -358,6 +361,7 @@ def step_reversed_sums(P, case, state, sigma0, dt):
     rho, _ = density(P, x, h, kind, sigma0, nb)
     f = forces(P, x, v, h, m, kind, vw, rho, nb)
     v = kick(P, v, f["a"], kind, hdt)
+    P.dt_tv = saved_dt_tv
     return {"x": x, "v": v, "a": f["a"], "dr": f["dr"], "rho": rho, "R": f["R"], "chi": f["chi"]}
 
 

@@ -72,7 +72,8 @@ typedef struct {
     double g[3];               /* body force per unit mass */
     double h_min;              /* minimum smoothing length (Eq. 9-11, 15-16) */
     double riemann_eta;        /* slope of the dissipation limiter (Eq. 6) */
-    int32_t tv_mode;           /* 0 none, 1 limited (Eq. 16), 2 unlimited (Eq. 14) */
+    int32_t tv_mode;           /* 0 none, 1 limited (Eq. 16), 2 unlimited (Eq. 14),
+                                  3 background pressure p0 = rho0 c^2 (Eq. 12) */
     int32_t tv_h_per_particle; /* 0: h = h_min in Eq. 14-16, 1: h = h_i */
     double tv_xi;              /* coefficient xi of Eq. 14 / 16 */
     double tv_C;               /* limiter constant C (Eq. 15) */
@@ -81,6 +82,7 @@ typedef struct {
     int32_t pad0;
     double cfl_ad, cfl_ac;     /* Eq. 9, 11 */
     double u_ref;              /* reference velocity (Eq. 10) */
+    double dt_tv;              /* step size in the background-pressure mode (tv_mode 3) */
 } orc_params;
 
 static int g_threads = 1;
@@ -374,7 +376,7 @@ double orc_riemann_pstar(const orc_params* P, double pl, double pr, double rhoba
 double orc_tv_limiter(const orc_params* P, double s)
 {
     if (P->tv_mode == 0) return 0.0;
-    if (P->tv_mode == 2) return 1.0;
+    if (P->tv_mode == 2 || P->tv_mode == 3) return 1.0;
     if (s > P->tv_thresh) return fmin(P->tv_C * s, 1.0);
     return 0.0;
 }
@@ -428,10 +430,14 @@ void orc_forces(const orc_params* P, int64_t n, const double* x, const double* v
         double htv = P->tv_h_per_particle ? h[i] : P->h_min;
         double s = htv * htv * dot3(Ri, Ri);
         double ch = orc_tv_limiter(P, s);
+        /* Eq. 12 in kick-drift-kick: the background-pressure acceleration
+         * a_bg = -2 sum_j m_j p0 / (rho_i rho_j) grad W_ij = -(2 p0 / rho_i) R_i
+         * moves the particle by dt^2/2 a_bg in the drift. */
+        double bg = -(P->dt_tv * P->dt_tv * (P->rho0 * c2) / rho_i);
         for (int d = 0; d < 3; ++d) {
             a[3 * i + d] = ai[d];
             R[3 * i + d] = Ri[d];
-            dr[3 * i + d] = P->tv_xi * ch * htv * htv * Ri[d];
+            dr[3 * i + d] = P->tv_mode == 3 ? bg * Ri[d] : P->tv_xi * ch * htv * htv * Ri[d];
         }
         if (chi) chi[i] = ch;
     }
@@ -546,10 +552,12 @@ int orc_step(const orc_params* P, int64_t n, double* x, double* v, double* a, do
              double* rho, double* R, double* chi)
 {
     double hdt = 0.5 * dt;
-    orc_kick(P, n, hdt, v, a, kind);
-    orc_drift(P, n, dt, x, v, dr, kind);
-    if (orc_force_pass(P, n, x, v, h, m, kind, vw, sigma0, mode, rho, a, R, chi, dr)) return -1;
-    orc_kick(P, n, hdt, v, a, kind);
+    orc_params Q = *P;
+    Q.dt_tv = dt;       /* the background-pressure displacement uses this step's dt */
+    orc_kick(&Q, n, hdt, v, a, kind);
+    orc_drift(&Q, n, dt, x, v, dr, kind);
+    if (orc_force_pass(&Q, n, x, v, h, m, kind, vw, sigma0, mode, rho, a, R, chi, dr)) return -1;
+    orc_kick(&Q, n, hdt, v, a, kind);
     return 0;
 }
 
@@ -705,6 +713,7 @@ int orc_step_adjoint(const orc_params* P, int64_t n, const double* x, const doub
                      const double* sigma0, double dt, int mode, double* xbar, double* vbar, double* abar,
                      double* drbar, double* etabar)
 {
+    if (P->tv_mode == 3) return -2;     /* the background-pressure mode has no adjoint here */
     size_t nb = (size_t)(n > 0 ? 3 * n : 1) * sizeof(double);
     double* xp = (double*)malloc(nb);
     double* vh = (double*)malloc(nb);
@@ -752,6 +761,7 @@ int orc_force_pass_adjoint(const orc_params* P, int64_t n, const double* x, cons
                            const double* m, const int8_t* kind, const double* vw, const double* sigma0, int mode,
                            const double* Abar, const double* Dbar, double* xbar, double* vbar, double* etabar)
 {
+    if (P->tv_mode == 3) return -2;
     size_t nb = (size_t)(n > 0 ? 3 * n : 1) * sizeof(double);
     double* Rf = (double*)malloc(nb);
     double* af = (double*)malloc(nb);

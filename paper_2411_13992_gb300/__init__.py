@@ -32,10 +32,10 @@ __all__ = [
     "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES",
     "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint",
     "params_from_case", "Simulation", "Rollout",
-    "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
+    "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TV_BACKGROUND", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
 ]
 
-TV_OFF, TV_LIMITED, TV_UNLIMITED = 0, 1, 2
+TV_OFF, TV_LIMITED, TV_UNLIMITED, TV_BACKGROUND = 0, 1, 2, 3
 TVH_MIN, TVH_PARTICLE = 0, 1
 HPAIR_MEAN, HPAIR_MAX = 0, 1
 

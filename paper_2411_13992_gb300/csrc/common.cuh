@@ -137,14 +137,21 @@ struct PlainD {
 
 // ------------------------------------------------------------ cell grid
 
-// Cell coordinate along axis d, clamped to the grid; NaN maps to cell 0 (the
-// kick-drift kernel flags non-finite positions separately).
+// Cell coordinate along axis d, clamped to the grid.  Truncation equals
+// floor for t >= 0, and negative t clamps to 0 either way; the conversion
+// saturates large values and maps NaN to 0 (the kick-drift kernel flags
+// non-finite positions separately).  Two FP64 operations and a conversion:
+// GB300's FP64 pipe is narrow.
 __device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
 {
-    double t = floor((x - G.lo[d]) * G.inv_edge[d]);
-    if (!(t >= 0.0)) return 0;
-    if (t >= (double)G.nc[d]) return G.nc[d] - 1;
-    return (int)t;
+    const int c = __double2int_rz(__dsub_rn(x, G.lo[d]) * G.inv_edge[d]);
+    return min(max(c, 0), G.nc[d] - 1);
+}
+
+// x is finite (not inf or NaN), tested on the exponent bits.
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
 
 template <int DIM>

@@ -52,15 +52,14 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
                 if (xn < G.lo[d]) xn = __dadd_rn(xn, G.L[d]);
                 else if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
             }
-            if (!isfinite(xn) || !isfinite((double)vh)) e |= ERRB_NAN;
             xs[d] = xn;
             S.x[o] = xn;
         }
     }
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        if (!isfinite(xs[d])) { e |= ERRB_NAN; xs[d] = G.lo[d]; }
-        else if (xs[d] < G.lo[d] || xs[d] > G.hi[d]) e |= ERRB_DOMAIN;
+        if (!finite_bits(xs[d])) e |= ERRB_NAN;
+        else if (!G.periodic[d] && (xs[d] < G.lo[d] || xs[d] > G.hi[d])) e |= ERRB_DOMAIN;
     }
     if (e) atomicOr(err, e);
     int k = cell_index<DIM>(G, xs);

@@ -145,11 +145,14 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double htv2 = htv * htv;
         const double chi = tv_limiter(K, htv2 * R2);
         const double m_i = S.m[i];
+        // Eq. 12 (background pressure p0 = rho0 c^2): dr = dt^2/2 a_bg = -(dt^2 p0 / rho_i) R_i
+        const double bg = -(dt * dt * (K.rho0 * K.c2) / rho_i);
+        const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
         double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             size_t o = (size_t)d * n + i;
-            double dr = K.tv_xi * chi * htv2 * R[d];
+            double dr = bgmode ? bg * R[d] : K.tv_xi * chi * htv2 * R[d];
             double vn = __dadd_rn(vi[d], __dmul_rn(hdt, a[d]));
             if (write_ad) {
                 S.a[o] = a[d];

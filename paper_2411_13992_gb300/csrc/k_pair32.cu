@@ -287,11 +287,14 @@ __global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __rest
         const float htv2 = htv * htv;
         const float chi = tv_limiter(K, htv2 * R2);
         const double m_i = S.m[i];
+        // Eq. 12 (background pressure p0 = rho0 c^2): dr = -(dt^2 p0 / rho_i) R_i
+        const float bg = (float)(-(dt * dt * (double)(K.rho0 * K.c2)) / (double)rho_i);
+        const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
         double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const size_t o = (size_t)d * n + i;
-            const float dr = K.tv_xi * chi * htv2 * R[d];
+            const float dr = bgmode ? bg * R[d] : K.tv_xi * chi * htv2 * R[d];
             const float vn = __fadd_rn(vi[d], __fmul_rn((float)hdt, a[d]));
             if (write_ad) {
                 S.a[o] = a[d];

@@ -24,7 +24,7 @@ template <typename Real>
 __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
 {
     if (K.tv_mode == SPH_TV_OFF) return Real(0);
-    if (K.tv_mode == SPH_TV_UNLIMITED) return Real(1);
+    if (K.tv_mode == SPH_TV_UNLIMITED || K.tv_mode == SPH_TV_BACKGROUND) return Real(1);
     if (s > K.tv_thresh) {
         Real t = K.tv_C * s;
         return t < Real(1) ? t : Real(1);

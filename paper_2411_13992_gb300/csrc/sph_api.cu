@@ -101,7 +101,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->precision != 32 && p->precision != 64) return SPH_ERR_ARG;
     if (!(p->rho0 > 0) || !(p->c0 > 0) || !(p->eta >= 0)) return SPH_ERR_ARG;
     if (!(p->h_min > 0) || !(p->h_max >= p->h_min)) return SPH_ERR_ARG;
-    if (p->tv_mode < 0 || p->tv_mode > 2 || p->tv_h < 0 || p->tv_h > 1 || p->h_pair < 0 || p->h_pair > 1)
+    if (p->tv_mode < 0 || p->tv_mode > 3 || p->tv_h < 0 || p->tv_h > 1 || p->h_pair < 0 || p->h_pair > 1)
         return SPH_ERR_ARG;
     if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
     if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
@@ -802,6 +802,7 @@ sph_status sph_step_adjoint(sph_ctx* c, const double* x0, const double* v0, cons
 {
     if (!c || !x0 || !v0 || !a0 || !dr0 || !xbar || !vbar || !abar || !drbar) return SPH_ERR_ARG;
     if (c->P.adjoint_steps < 1 || nsteps < 1 || nsteps > c->P.adjoint_steps) return SPH_ERR_ARG;
+    if (c->P.tv_mode == SPH_TV_BACKGROUND) return SPH_ERR_ARG;
     if (!c->have_state) return SPH_ERR_STATE;
     SPH_TRY(reload_state(c, x0, v0, a0, dr0));
     SPH_TRY(sph_build_cells(c));
@@ -836,7 +837,7 @@ sph_status sph_force_pass_adjoint(sph_ctx* c, const double* x, const double* v, 
                                   const double* drbar, double* xbar, double* vbar, double* etabar)
 {
     if (!c || !x || !v || !abar || !drbar || !xbar || !vbar) return SPH_ERR_ARG;
-    if (c->P.adjoint_steps < 1) return SPH_ERR_ARG;
+    if (c->P.adjoint_steps < 1 || c->P.tv_mode == SPH_TV_BACKGROUND) return SPH_ERR_ARG;
     if (!c->have_state) return SPH_ERR_STATE;
     SPH_TRY(reload_state(c, x, v, nullptr, nullptr));
     SPH_TRY(sph_build_cells(c));

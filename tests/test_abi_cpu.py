@@ -79,7 +79,7 @@ def test_workspace_query_and_argument_checks(lib):
     assert 0 < sph.sph_query_workspace(p32, c["n"])
     bad = [
         dict(dim=4), dict(precision=16), dict(rho0=0.0), dict(c0=-1.0), dict(eta=-1.0), dict(h_min=0.0),
-        dict(h_max=0.5 * c["h_min"]), dict(tv_mode=3), dict(fixed_dt=-1.0),
+        dict(h_max=0.5 * c["h_min"]), dict(tv_mode=4), dict(fixed_dt=-1.0), dict(adjoint_steps=-1),
         dict(h_max=0.3),          # fewer than 5 cells along a periodic axis
     ]
     for kw in bad:

@@ -77,6 +77,17 @@ def test_fp64_step_parity_tgv2d(tgv2d_traj, k):
     _assert64(err)
 
 
+@pytest.mark.parametrize("mode", [oracle.TV_UNLIMITED, oracle.TV_BACKGROUND, oracle.TV_NONE])
+def test_fp64_step_parity_other_correction_modes(tgv2d_traj, mode):
+    c, dt, states, P0, s0 = tgv2d_traj
+    P = oracle_params(c, tv_mode=mode)
+    for k in (20, 100):
+        err, _, _ = compare_step(c, states[k], dt, s0, P, precision=64, tv_mode=mode)
+        _assert64(err)
+        err, _, _ = compare_step(c, states[k], dt, s0, P, precision=32, tv_mode=mode)
+        _assert32(err)
+
+
 @pytest.mark.parametrize("k", [0, 20, 100])
 def test_fp32_step_parity_tgv2d(tgv2d_traj, k):
     c, dt, states, P, s0 = tgv2d_traj
@@ -145,7 +156,7 @@ def _small_cylinder():
 
 
 @pytest.mark.parametrize("opts", [{}, {"tv_h_per_particle": True}, {"h_pair_max": True},
-                                  {"tv_mode": oracle.TV_UNLIMITED}])
+                                  {"tv_mode": oracle.TV_UNLIMITED}, {"tv_mode": oracle.TV_BACKGROUND}])
 def test_step_parity_variable_resolution(opts):
     c = _small_cylinder()
     assert c["h_max"] > 1.5 * c["h_min"]

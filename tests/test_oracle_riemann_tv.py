@@ -92,3 +92,21 @@ def test_time_step_hand_values(orc):
         v[2, 0] = 0.3 * case["vmax"]
         dt = orc.time_step(P, v, np.zeros(3, np.int8))
         assert dt == pytest.approx(case["dt"], rel=1e-12), case["why"]
+
+
+def test_background_pressure_mode_equals_uniform_pressure_force(orc):
+    """Eq. 12: the transport correction of Adami's formulation is the
+    acceleration of a uniform background pressure p0 = rho0 c^2, applied as
+    the displacement dt^2/2 a_bg in the drift.  With every particle at rest
+    and rho = 2 rho0 (so the EOS gives p = rho0 c^2 = p0 everywhere), the
+    pressure force of Eq. 3 is exactly that acceleration."""
+    from paper_2411_13992_gb300 import cases
+    c = cases.lattice_block(2, 12, dp=0.1, jitter_dp=0.2, seed=4)
+    P = orc.make_params(2, c["lo"], c["L"], c["periodic"], 1.0, 10.0, 0.0, c["h_min"], tv_mode=3)
+    P.dt_tv = 1.7e-3
+    nb = orc.neighbours(P, c["x"], c["h"])
+    rho = np.full(c["n"], 2.0)
+    f = orc.forces(P, c["x"], np.zeros((c["n"], 3)), c["h"], c["m"], c["kind"], c["vw"], rho, nb)
+    np.testing.assert_allclose(f["dr"], 0.5 * P.dt_tv ** 2 * f["a"], rtol=0,
+                               atol=1e-13 * np.abs(0.5 * P.dt_tv ** 2 * f["a"]).max())
+    assert np.abs(f["dr"]).max() > 0
