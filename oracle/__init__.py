@@ -343,6 +343,14 @@ def drift(P, x, v, dr, kind, dt):
     return x
 
 
+def reverse_segments(start, idx):
+    """The CSR neighbour lists with every particle's list reversed."""
+    counts = np.diff(start)
+    seg = np.repeat(np.arange(len(counts)), counts)
+    k = np.arange(len(idx))
+    return np.ascontiguousarray(idx[start[seg] + start[seg + 1] - 1 - k])
+
+
 def step_reversed_sums(P, case, state, sigma0, dt):
     """The same kick-drift-kick step as ``step`` with every neighbour sum taken
     in descending instead of ascending j.  The two results differ only by
@@ -356,8 +364,7 @@ def step_reversed_sums(P, case, state, sigma0, dt):
     v = kick(P, state["v"], state["a"], kind, hdt)
     x = drift(P, state["x"], v, state["dr"], kind, dt)
     start, idx = neighbours(P, x, h)
-    ridx = np.concatenate([idx[start[i]:start[i + 1]][::-1] for i in range(n)]) if n else idx
-    nb = (start, ridx)
+    nb = (start, reverse_segments(start, idx))
     rho, _ = density(P, x, h, kind, sigma0, nb)
     f = forces(P, x, v, h, m, kind, vw, rho, nb)
     v = kick(P, v, f["a"], kind, hdt)

@@ -86,6 +86,22 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
     }
 }
 
+// 1/x and sqrt(x) to ~1 ulp on the special-function unit (x > 0, normal):
+// the FP32 form needs neither the IEEE-rounded division nor square root.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One neighbour's contribution to a_i and R_i in the FP32 form, given
 // rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force
 // (Eq. 3, 5-7, 14) arranged for FP32 throughput -- W' only enters through
@@ -98,7 +114,7 @@ __device__ __forceinline__ void pair_force32(const Consts<float>& K, const float
 {
     const bool wall = isinf(oj.w);
     const float rho_j = wall ? rho_i : K.rho0 + oj.w;
-    const float inv_rho_j = wall ? inv_rho_i : __frcp_rn(rho_j);
+    const float inv_rho_j = wall ? inv_rho_i : rcp_approx(rho_j);
     const float p_j = wall ? p_i : K.c2 * oj.w;
     const float dv[3] = {vi[0] - oj.x, vi[1] - oj.y, DIM == 3 ? vi[2] - oj.z : 0.f};
     float dvr = dv[0] * rv[0] + dv[1] * rv[1];
@@ -125,6 +141,76 @@ __device__ __forceinline__ float dwr_of(float r, float inv_h, float coef)
 {
     const float t = fmaf(-0.5f * inv_h, r, 1.f);
     return coef * (t * t * t);
+}
+
+// The same visit as for_candidates, walked row by row: for each (dy, dz) the
+// cells cx-R .. cx+R are contiguous in the cell order, so the row is one run
+// of particles (two runs across a periodic x boundary) whose x shift and
+// stencil code advance at each cell boundary.  Fewer and more uniform loops
+// than one loop per cell when cells hold only a few particles.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_candidates_rows(const float* oi, int cell_i, const Grid& G,
+                                                    const int32_t* __restrict__ start,
+                                                    const float4* __restrict__ pos4, F& f)
+{
+    int c[3];
+    cell_decode(G, cell_i, c);
+    constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
+    const int ncx = G.nc[0];
+    // runs along x: first cell (x coordinate), number of cells, x step of the first cell
+    int rc0[2], rn[2], rdx[2], nrun;
+    {
+        int a = c[0] - R, b = c[0] + R;
+        if (!G.periodic[0] || (a >= 0 && b < ncx)) {
+            a = a < 0 ? 0 : a;
+            b = b >= ncx ? ncx - 1 : b;
+            rc0[0] = a; rn[0] = b - a + 1; rdx[0] = a - c[0]; nrun = 1;
+        } else if (a < 0) {
+            rc0[0] = ncx + a; rn[0] = -a; rdx[0] = a - c[0];
+            rc0[1] = 0; rn[1] = b + 1; rdx[1] = -c[0]; nrun = 2;
+        } else {
+            rc0[0] = a; rn[0] = ncx - a; rdx[0] = a - c[0];
+            rc0[1] = 0; rn[1] = b - ncx + 1; rdx[1] = ncx - c[0]; nrun = 2;
+        }
+    }
+    for (int dz = -zr; dz <= zr; ++dz) {
+        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+        if (cz < 0) continue;
+        const float shz = -(float)dz * G.edgef[2];
+        for (int dy = -R; dy <= R; ++dy) {
+            int cy = cell_step(G, c[1], dy, 1);
+            if (cy < 0) continue;
+            const float shy = -(float)dy * G.edgef[1];
+            const int row = ncx * (cy + G.nc[1] * cz);
+            const uint32_t code_row = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
+            for (int r = 0; r < nrun; ++r) {
+                int cell = row + rc0[r];
+                int dx = rdx[r];
+                int j = start[cell];
+                const int jend = start[cell + rn[r]];
+                int nb = start[cell + 1];
+                float shx = -(float)dx * G.edgef[0];
+                for (; j < jend; ++j) {
+                    while (j >= nb) {          // next non-empty cell of the run
+                        ++cell;
+                        ++dx;
+                        nb = start[cell + 1];
+                        shx = -(float)dx * G.edgef[0];
+                    }
+                    const float4 pj = pos4[j];
+                    const float rx = (oi[0] - pj.x) + shx;
+                    const float ry = (oi[1] - pj.y) + shy;
+                    float r2 = rx * rx + ry * ry;
+                    float rz = 0.f;
+                    if (DIM == 3) {
+                        rz = (oi[2] - pj.z) + shz;
+                        r2 += rz * rz;
+                    }
+                    f(j, code_row + (uint32_t)dx, pj, r2, rx, ry, rz);
+                }
+            }
+        }
+    }
 }
 
 // Shift of a neighbour cell from its stencil code (as for_candidates forms it).
@@ -169,14 +255,14 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     auto visit = [&](int j, uint32_t code, const float4& pj, float r2, float, float, float) {
         if (r2 < support2<UNIFORM>(K, hi, pj.w)) {
             const float inv_h = UNIFORM ? K.inv_h_u : 1.f / pair_h(K, hi, pj.w);
-            sigma.add(wendland_W<DIM, float>(sqrtf(r2), inv_h));
+            sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), inv_h));
             if (r2 > 0.f) {
                 if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
                 ++cnt;
             }
         }
     };
-    for_candidates<DIM>(oi, cell_of[i], G, start, pos4, visit);
+    for_candidates_rows<DIM>(oi, cell_of[i], G, start, pos4, visit);
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
     const float s0 = (float)S.s0[i];
@@ -187,7 +273,7 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
 // ------------------------------------------------------------------ forces
 
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __restrict__ pos4,
                                                      const int32_t* __restrict__ cell_of,
                                                      const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                      StateSet<float> S, const float* __restrict__ mf,
@@ -218,7 +304,7 @@ __global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __rest
         const float vi[3] = {me.x, me.y, me.z};
         const float rho_i = K.rho0 + me.w;
         const float p_i = K.c2 * me.w;
-        const float inv_rho_i = __frcp_rn(rho_i);
+        const float inv_rho_i = rcp_approx(rho_i);
         Acc acc_a[DIM], acc_R[DIM];
         // W'/r = coef t^3, coef = -5 a_D h^-(D+2) (uniform h: one constant)
         const float norm = kernel_norm<DIM, float>();
@@ -239,20 +325,24 @@ __global__ void __launch_bounds__(kTPB32) k_forces32(int n, const float4* __rest
         };
         const int cnt = nbc[i];
         if (cnt <= cap) {
-            // the neighbour list of the density pass: no candidate tests;
-            // the next neighbour's data is loaded while this one is computed
-            uint32_t e = cnt > 0 ? nbl[i] : 0u;
-            float4 pj_n = pos4[e >> kCodeBits];
-            float4 oj_n = vr[e >> kCodeBits];
+            // the neighbour list of the density pass: no candidate tests.
+            // Software pipeline: the list entry two ahead and the neighbour
+            // data one ahead are in flight while this pair is computed.
+            const uint32_t* lp = nbl + i;
+            uint32_t e_cur = cnt > 0 ? lp[0] : 0u;
+            uint32_t e_nxt = cnt > 1 ? lp[(size_t)n] : 0u;
+            float4 pj_n = pos4[e_cur >> kCodeBits];
+            float4 oj_n = vr[e_cur >> kCodeBits];
             for (int k = 0; k < cnt; ++k) {
-                const uint32_t ec = e;
+                const uint32_t ec = e_cur;
                 const float4 pj = pj_n;
                 const float4 oj = oj_n;
                 if (k + 1 < cnt) {
-                    e = nbl[(size_t)(k + 1) * n + i];
-                    pj_n = pos4[e >> kCodeBits];
-                    oj_n = vr[e >> kCodeBits];
+                    pj_n = pos4[e_nxt >> kCodeBits];
+                    oj_n = vr[e_nxt >> kCodeBits];
                 }
+                e_cur = e_nxt;
+                e_nxt = (k + 2 < cnt) ? lp[(size_t)(k + 2) * n] : 0u;
                 const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
                 float rv[3];
                 rv[0] = (oi[0] - pj.x) + sh.x;
