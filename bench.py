@@ -44,6 +44,17 @@ WORKLOAD = "3-D Taylor-Green vortex 128^3 = 2,097,152 particles, periodic [0,2pi
 #   per axis: grad W 1, pressure+viscous increment 4, residual increment 1
 #   (x3 = 18), Kahan compensation 4 per accumulator (x6 = 24)          -> 111
 FLOPS_PER_PAIR_FP32 = 111
+# Algorithmic cost of the density pass (k_density32, FP32 form) per
+# interacting pair, self included: pair vector and r^2 11, sqrt 1,
+# W = a_D h^-D t^4 (2q + 1) with q = r/h, t = 1 - q/2: 9, Kahan 4     -> 25.
+# The candidate tests of the cell scan (about 184 per particle in 3-D, for
+# 81 pairs) are implementation overhead and are not counted.
+FLOPS_PER_PAIR_DENSITY32 = 25
+# Algorithmic bytes of k_density32 per particle: read the float4 position,
+# v (12 B), kind (1 B), sigma0 (8 B), cell index (4 B); write the float4
+# {v, rho - rho0} and the neighbour count (4 B).  The neighbour list it
+# writes (about 80 x 4 B) is an implementation artefact, not counted.
+BYTES_PER_PARTICLE_DENSITY = 61
 # Algorithmic bytes of k_forces per particle (FP32 form, 3-D): read the
 # particle's float4 position + h and float4 {v, rho - rho0} (32 B), mass and
 # kind (9 B), cell index (4 B); write a, dr, v, R (48 B), chi (4 B).  Each
@@ -63,9 +74,36 @@ def _peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
+# The FP64 form evaluates the same formulas with plain (uncompensated) sums.
+FLOPS_PER_PAIR_FP64 = FLOPS_PER_PAIR_FP32 - 24
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_fma_peak(torch, sph, precision: int, target_ms: float = 20.0, reps: int = 3) -> float:
+    """FMA throughput (TFLOP/s) of this GPU from the library's sph_fma_peak
+    launch: 8 blocks of 256 threads per SM, iterations sized to about
+    target_ms, best of reps launches, CUDA events on the launching stream."""
+    dev = torch.cuda.current_device()
+    blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(blocks * 256, dtype=torch.float32 if precision == 32 else torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = sph.sph_fma_peak(precision, blocks, iters, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        return flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    iters = 256
+    rate = run(iters)
+    iters = max(256, int(rate * 1e12 * target_ms * 1e-3 / (16.0 * blocks * 256)))
+    return max(run(iters) for _ in range(reps))
 
 
 # ------------------------------------------------------------ clocks sampler
@@ -300,22 +338,29 @@ def run_native(args):
     # ---- adjoint / forward time on the adjoint workload
     adjoint = _adjoint_ratio(torch, sph, cases) if not args.no_adjoint else None
 
-    # ---- roofline of the dominant kernel (FP32 forces), live event timing
+    # ---- rooflines of the two pair kernels (live event timing); the line's
+    # "roofline" is the one that takes the larger share of the step
     peaks, src = _peaks()
-    f_ms, f_cnt = prof["forces"]
-    f_avg_s = f_ms / max(f_cnt, 1) * 1e-3
+    hbm_gbs = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     pairs = _pairs_per_launch(case)
-    achieved_tflops = pairs * FLOPS_PER_PAIR_FP32 / f_avg_s / 1e12
-    peak_tflops = fp32_peak_tflops(peaks.get("sm_max_mhz", SM_MAX_MHZ))
-    hbm_achieved = n * BYTES_PER_PARTICLE_FORCES / f_avg_s / 1e9
-    traffic = _profiled_traffic()
-    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak_tflops, "traffic": traffic,
-            "kernel": "k_forces_f32<3,KSum>", "peak_source": "FP32 FMA units x max SM clock (%s clock)" % src,
-            "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR_FP32,
-            "avg_launch_ms": f_avg_s * 1e3,
-            "hbm_algorithmic_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
-            "hbm_frac": hbm_achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS)}
+    peak_tflops = measured_fma_peak(torch, sph, 32)
+    dfma_tflops = measured_fma_peak(torch, sph, 64)
+    units_tflops = fp32_peak_tflops(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    peak_note = ("measured: FP32 FMA microbenchmark (sph_fma_peak) on this GPU; unit counts x max SM clock give "
+                 "%.1f TFLOP/s; HBM peak %s" % (units_tflops, src))
+    roof_d = _alu_roofline("density", "k_density32<3,KSum,uniform>", prof, pairs + n, FLOPS_PER_PAIR_DENSITY32,
+                           BYTES_PER_PARTICLE_DENSITY, n, peak_tflops, hbm_gbs)
+    roof_f = _alu_roofline("forces", "k_forces32<3,KSum,uniform>", prof, pairs, FLOPS_PER_PAIR_FP32,
+                           BYTES_PER_PARTICLE_FORCES, n, peak_tflops, hbm_gbs)
+    for r in (roof_d, roof_f):
+        r["peak_source"] = peak_note
+    f64_ms, f64_cnt = prof64["forces"]
+    f64_tflops = pairs * FLOPS_PER_PAIR_FP64 / (f64_ms / max(f64_cnt, 1) * 1e-3) / 1e12
+    roof_f["fp64_forces"] = {"achieved": f64_tflops, "peak": dfma_tflops, "frac": f64_tflops / dfma_tflops,
+                             "flops_per_pair": FLOPS_PER_PAIR_FP64,
+                             "peak_source": "measured: FP64 FMA microbenchmark (sph_fma_peak)"}
+    dominant = prof["density"][0] >= prof["forces"][0]
+    roof, roof_other = (roof_d, roof_f) if dominant else (roof_f, roof_d)
     kernels = {k: {"ms_per_step": v[0] / max(v[1], 1), "share": v[0] / max(sum(t[0] for t in prof.values()), 1e-9)}
                for k, v in prof.items()}
 
@@ -340,6 +385,7 @@ def run_native(args):
                      "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof64.items()}},
             "fp32_over_fp64": value / value64,
             "roofline": roof,
+            "roofline_other_pair_kernel": roof_other,
             "kernels": kernels,
             "e2e": e2e,
             "adjoint": adjoint,
@@ -363,13 +409,13 @@ def _pairs_per_launch(case) -> int:
     return case["n"] * 80
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the forces kernel from the committed ncu
-    summary (profiles/forces_traffic.json), or None when the kernel sources
-    have changed since those counters were taken (the summary records a SHA-1
-    of the sources it was measured on)."""
+def _profiled_traffic(kernel: str):
+    """DRAM bytes per launch of a pair kernel ("density" or "forces") from
+    the committed ncu summary (profiles/pair_traffic.json), or None when the
+    kernel sources have changed since those counters were taken (the summary
+    records a SHA-1 of the sources it was measured on)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "forces_traffic.json")
+    path = os.path.join(ROOT, "profiles", "pair_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -379,9 +425,20 @@ def _profiled_traffic():
                 h.update(f.read())
         if h.hexdigest() != d["source_sha1"]:
             return None
-        return d.get("dram_bytes_per_launch_full")
+        return d["kernels"][kernel]["dram_bytes_per_launch_full"]
     except (OSError, ValueError, KeyError):
         return None
+
+
+def _alu_roofline(name, kernel, prof, pairs, flops_per_pair, bytes_per_particle, n, peak_tflops, hbm_gbs):
+    ms, cnt = prof[name]
+    avg_s = ms / max(cnt, 1) * 1e-3
+    achieved = pairs * flops_per_pair / avg_s / 1e12
+    hbm = n * bytes_per_particle / avg_s / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": _profiled_traffic(name), "kernel": kernel,
+            "pairs_per_launch": pairs, "flops_per_pair": flops_per_pair, "avg_launch_ms": avg_s * 1e3,
+            "hbm_algorithmic_gbs": hbm, "hbm_peak_gbs": hbm_gbs, "hbm_frac": hbm / hbm_gbs}
 
 
 def _e2e(torch, sph, case, args, dist):

@@ -224,6 +224,21 @@ SPH_API sph_status sph_profile_end(sph_ctx* ctx, double* ms, int64_t* count);
 /* Static name of a kernel class ("forces", ...), or "?" when out of range. */
 SPH_API const char* sph_kernel_class_name(int32_t k);
 
+/* Measurement aid (not in the paper): the fused multiply-add throughput of
+ * this GPU, the denominator of the pair kernels' ALU roofline.  Enqueues on
+ * `stream` one launch of `blocks` blocks x 256 threads; each thread runs
+ * `iters` rounds of 8 independent FMA chains in the precision given (32:
+ * float, 64: double) and writes one value to sink[thread] so that the work
+ * is live.
+ *   sink    device memory, blocks * 256 elements of float (32) or double (64)
+ *   flops   host; receives the floating-point operations of the launch
+ *           (blocks * 256 * iters * 8 FMAs, an FMA counting 2)
+ * The caller times the launch with CUDA events on the same stream; the call
+ * does not wait.  SPH_ERR_ARG for precision not 32 or 64, blocks < 1,
+ * iters < 1 or a NULL pointer; SPH_ERR_CUDA if the launch fails. */
+SPH_API sph_status sph_fma_peak(int32_t precision, int32_t blocks, int32_t iters, void* sink, void* stream,
+                                double* flops);
+
 /* Adjoint of a segment of nsteps steps (reverse mode), with every step's
  * neighbour set and step size frozen (not in the paper; the derivatives of
  * Eq. 2-8 and 14-16 are taken by hand).  Subgradients at the kinks: the

@@ -29,7 +29,7 @@ __all__ = [
     "SphParams", "SphDiag", "SphError", "load", "exported_symbols", "declared_symbols",
     "sph_default_params", "sph_query_workspace", "sph_create", "sph_set_state", "sph_build_cells", "sph_step",
     "sph_set_dt", "sph_set_eta", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
-    "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES",
+    "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES", "sph_fma_peak",
     "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint",
     "params_from_case", "Simulation", "Rollout",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TV_BACKGROUND", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_step_adjoint": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
                                         ctypes.POINTER(ctypes.c_double)]),
             "sph_force_pass_adjoint": (_i32, [_vp] + [_vp] * 6 + [ctypes.POINTER(ctypes.c_double)]),
+            "sph_fma_peak": (_i32, [_i32, _i32, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -280,6 +281,23 @@ def sph_profile_end(ctx) -> dict:
 
 def sph_kernel_class_name(k: int) -> str:
     return load().sph_kernel_class_name(int(k)).decode()
+
+
+def sph_fma_peak(precision: int, blocks: int, iters: int, sink, stream=None) -> float:
+    """Enqueue the FMA-throughput launch on ``stream`` (torch's current
+    stream by default) into the device tensor ``sink`` (blocks * 256 float32
+    or float64 elements) and return its floating-point operations; the
+    caller times it with CUDA events on that stream."""
+    import torch
+    dtype = torch.float32 if precision == 32 else torch.float64
+    if not (sink.is_cuda and sink.dtype == dtype and sink.numel() >= blocks * 256):
+        raise ValueError("sink must be a CUDA %s tensor of at least blocks * 256 elements" % dtype)
+    if stream is None:
+        stream = torch.cuda.current_stream(sink.device)
+    flops = ctypes.c_double(0.0)
+    _check(load().sph_fma_peak(int(precision), int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                               ctypes.c_void_p(stream.cuda_stream), ctypes.byref(flops)), "sph_fma_peak")
+    return flops.value
 
 
 NOALLOC_MAX_PARTICLES = 65536

@@ -51,6 +51,7 @@ struct Consts {
     int tv_mode, tv_h_particle, h_pair_max, kahan;
     // uniform resolution (h_min == h_max): every pair has h_ij = h
     int uniform_h;
+    // h_u = h_max (the h of every pair at uniform resolution)
     Real h_u, inv_h_u, four_h2_u, dwr_coef_u;   // dwr_coef_u: W'(r)/r = dwr_coef_u t^3
 };
 

@@ -143,13 +143,18 @@ __device__ __forceinline__ float dwr_of(float r, float inv_h, float coef)
     return coef * (t * t * t);
 }
 
-// The same visit as for_candidates, walked row by row: for each (dy, dz) the
-// cells cx-R .. cx+R are contiguous in the cell order, so the row is one run
-// of particles (two runs across a periodic x boundary) whose x shift and
-// stencil code advance at each cell boundary.  Fewer and more uniform loops
-// than one loop per cell when cells hold only a few particles.
+// The same visit as for_candidates, walked row by row and clipped to the
+// particle's reach.  For each (dy, dz) row the cells are contiguous in the
+// cell order, so the row is one run of particles (two runs across a periodic
+// x boundary) whose x shift and stencil code advance at each cell boundary.
+// A row whose nearest y-z distance to particle i exceeds the reach (the
+// largest support radius of any pair of i) is skipped, and the x extent of a
+// row is cut to the cells within the remaining half-chord; every margin is
+// 1e-3 of a cell edge, far above FP32 rounding, so every candidate that the
+// full stencil would accept is still visited, in the same order.  About 2/3
+// of the 5^3 cells remain in 3-D.
 template <int DIM, typename F>
-__device__ __forceinline__ void for_candidates_rows(const float* oi, int cell_i, const Grid& G,
+__device__ __forceinline__ void for_candidates_rows(const float* oi, float reach, int cell_i, const Grid& G,
                                                     const int32_t* __restrict__ start,
                                                     const float4* __restrict__ pos4, F& f)
 {
@@ -157,30 +162,50 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, int cell_i,
     cell_decode(G, cell_i, c);
     constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
     const int ncx = G.nc[0];
-    // runs along x: first cell (x coordinate), number of cells, x step of the first cell
-    int rc0[2], rn[2], rdx[2], nrun;
-    {
-        int a = c[0] - R, b = c[0] + R;
-        if (!G.periodic[0] || (a >= 0 && b < ncx)) {
-            a = a < 0 ? 0 : a;
-            b = b >= ncx ? ncx - 1 : b;
-            rc0[0] = a; rn[0] = b - a + 1; rdx[0] = a - c[0]; nrun = 1;
-        } else if (a < 0) {
-            rc0[0] = ncx + a; rn[0] = -a; rdx[0] = a - c[0];
-            rc0[1] = 0; rn[1] = b + 1; rdx[1] = -c[0]; nrun = 2;
-        } else {
-            rc0[0] = a; rn[0] = ncx - a; rdx[0] = a - c[0];
-            rc0[1] = 0; rn[1] = b - ncx + 1; rdx[1] = ncx - c[0]; nrun = 2;
-        }
-    }
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    const float inv_ex = 1.f / ex;
+    const float reach2 = reach * reach;
     for (int dz = -zr; dz <= zr; ++dz) {
         int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
         if (cz < 0) continue;
-        const float shz = -(float)dz * G.edgef[2];
+        float rz = 0.f;
+        if (DIM == 3) {
+            rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
+            rz = fmaxf(rz - 1e-3f * ez, 0.f);
+        }
+        const float wz2 = reach2 - rz * rz;
+        if (wz2 <= 0.f) continue;
+        const float shz = -(float)dz * ez;
         for (int dy = -R; dy <= R; ++dy) {
             int cy = cell_step(G, c[1], dy, 1);
             if (cy < 0) continue;
-            const float shy = -(float)dy * G.edgef[1];
+            float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
+            ry = fmaxf(ry - 1e-3f * ey, 0.f);
+            const float w2 = wz2 - ry * ry;
+            if (w2 <= 0.f) continue;
+            const float w = sqrtf(w2) + 1e-3f * ex;
+            const int dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
+            const int dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
+            if (dxlo > dxhi) continue;
+            // runs along x: first cell (x index), number of cells, x step of the
+            // first cell; a periodic window (at most 5 <= ncx cells) wraps once at most
+            int rc0[2], rn[2], rdx[2], nrun;
+            const int a = c[0] + dxlo, b = c[0] + dxhi;
+            if (!G.periodic[0]) {
+                const int a0 = max(a, 0), b0 = min(b, ncx - 1);
+                rc0[0] = a0; rn[0] = b0 - a0 + 1; rdx[0] = a0 - c[0]; nrun = rn[0] > 0 ? 1 : 0;
+            } else if (a >= 0 && b < ncx) {
+                rc0[0] = a; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+            } else if (a < 0) {
+                rc0[0] = ncx + a; rn[0] = min(-a, b - a + 1); rdx[0] = dxlo;
+                rc0[1] = 0; rn[1] = b + 1; rdx[1] = -c[0]; nrun = b >= 0 ? 2 : 1;
+            } else if (a >= ncx) {
+                rc0[0] = a - ncx; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+            } else {
+                rc0[0] = a; rn[0] = ncx - a; rdx[0] = dxlo;
+                rc0[1] = 0; rn[1] = b - ncx + 1; rdx[1] = ncx - c[0]; nrun = 2;
+            }
+            const float shy = -(float)dy * ey;
             const int row = ncx * (cy + G.nc[1] * cz);
             const uint32_t code_row = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
             for (int r = 0; r < nrun; ++r) {
@@ -189,24 +214,24 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, int cell_i,
                 int j = start[cell];
                 const int jend = start[cell + rn[r]];
                 int nb = start[cell + 1];
-                float shx = -(float)dx * G.edgef[0];
+                float shx = -(float)dx * ex;
                 for (; j < jend; ++j) {
                     while (j >= nb) {          // next non-empty cell of the run
                         ++cell;
                         ++dx;
                         nb = start[cell + 1];
-                        shx = -(float)dx * G.edgef[0];
+                        shx = -(float)dx * ex;
                     }
                     const float4 pj = pos4[j];
                     const float rx = (oi[0] - pj.x) + shx;
-                    const float ry = (oi[1] - pj.y) + shy;
-                    float r2 = rx * rx + ry * ry;
-                    float rz = 0.f;
+                    const float ry_ = (oi[1] - pj.y) + shy;
+                    float r2 = rx * rx + ry_ * ry_;
+                    float rz_ = 0.f;
                     if (DIM == 3) {
-                        rz = (oi[2] - pj.z) + shz;
-                        r2 += rz * rz;
+                        rz_ = (oi[2] - pj.z) + shz;
+                        r2 += rz_ * rz_;
                     }
-                    f(j, code_row + (uint32_t)dx, pj, r2, rx, ry, rz);
+                    f(j, code_row + (uint32_t)dx, pj, r2, rx, ry_, rz_);
                 }
             }
         }
@@ -262,7 +287,9 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
             }
         }
     };
-    for_candidates_rows<DIM>(oi, cell_of[i], G, start, pos4, visit);
+    // reach: the largest support radius 2 h_ij of any pair of i (h_j <= h_max)
+    const float reach = UNIFORM ? 2.f * K.h_u : 2.f * pair_h(K, hi, K.h_u);
+    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, pos4, visit);
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
     const float s0 = (float)S.s0[i];

@@ -113,3 +113,13 @@ def test_null_context_and_status_strings(lib):
         assert sph.sph_status_str(s) not in ("", "unknown status")
     assert sph.sph_status_str(99) == "unknown status"
     assert lib.sph_launch_count(None) == -1
+
+
+def test_fma_peak_rejects_bad_arguments_before_launching(lib):
+    flops = ctypes.c_double(-1.0)
+    sink = ctypes.c_void_p(0x100000)     # never dereferenced: every call below fails its host check
+    for prec, blocks, iters in ((16, 1, 1), (32, 0, 1), (64, 1, 0), (32, -4, 10)):
+        assert lib.sph_fma_peak(prec, blocks, iters, sink, None, ctypes.byref(flops)) == 1
+    assert lib.sph_fma_peak(32, 1, 1, None, None, ctypes.byref(flops)) == 1
+    assert lib.sph_fma_peak(32, 1, 1, sink, None, None) == 1
+    assert flops.value == -1.0
