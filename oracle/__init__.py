@@ -19,6 +19,12 @@ Functions and the passages they follow (paper sections / equations):
 * ``forces`` -- Eq. 3 (row 2), 5, 6, 7 and Eq. 14-16.
 * ``time_step`` -- Eq. 9-11.
 * ``step`` -- one kick-drift-kick step (Sec. 1, Sec. 3).
+* ``viscous``, ``pressure``, ``continuity`` -- Eq. 7, Eq. 3 (row 2) with
+  Eq. 5-6, and Eq. 3 (row 1) with U* of Eq. 5 (row 1), each alone.
+* ``advection_step``, ``acoustic_step`` -- Eq. 9-10 and Eq. 11.
+* ``dual_step`` -- one advection step of the dual-criteria scheme (Sec. 2.4,
+  the correction once per advection step as in Sec. 3, Eq. 12-13 for the
+  background-pressure form).
 
 Pins (tests/test_oracle_*.py): kernel normalisation by quadrature and its
 derivative by finite differences; lattice partition of unity and zero
@@ -89,6 +95,7 @@ class Params(ctypes.Structure):
         ("cfl_ac", ctypes.c_double),
         ("u_ref", ctypes.c_double),
         ("dt_tv", ctypes.c_double),
+        ("tv_p0", ctypes.c_double),
     ]
 
 
@@ -155,6 +162,14 @@ def lib():
                                                     ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
                 "orc_force_pass_adjoint": (ctypes.c_int, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp,
                                                           ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
+                "orc_viscous": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
+                "orc_pressure": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
+                "orc_continuity": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
+                "orc_riemann_ustar": (ctypes.c_double, [_pp] + [ctypes.c_double] * 5),
+                "orc_advection_step": (ctypes.c_double, [_pp, _i64, _dp, _bp, _dp]),
+                "orc_acoustic_step": (ctypes.c_double, [_pp, _i64, _dp, _bp]),
+                "orc_dual_step": (_i64, [_pp, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _bp, _dp, _dp, ctypes.c_int,
+                                         _dp, _dp, _dp, _dp, _dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -451,3 +466,77 @@ def sigma0_for(case, dim):
     vals = np.array([lattice_sum(dim, hh / dd) / dd ** dim for hh, dd in pairs])
     out[:] = vals[np.ravel(inv)]
     return out
+
+
+# ----------------------------------------------------- dual-criteria stepping
+
+def _pair_fn(name, P, x, v, h, m, kind, vw, rho, nbrs, width):
+    n = len(x)
+    x, v, vw = _vec(x, n), _vec(v, n), _vec(vw, n)
+    h, m, rho = _sca(h, n), _sca(m, n), _sca(rho, n)
+    kind = _sca(kind, n, np.int8)
+    start, idx = nbrs
+    idx = np.ascontiguousarray(idx, dtype=np.int64) if len(idx) else np.zeros(1, np.int64)
+    out = np.zeros((n, 3)) if width == 3 else np.zeros(n)
+    getattr(lib(), name)(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp), _d(vw), _d(rho),
+                         start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), _d(out))
+    return out
+
+
+def viscous(P, x, v, h, m, kind, vw, rho, nbrs):
+    """Eq. 7 alone: the viscous acceleration (N, 3)."""
+    return _pair_fn("orc_viscous", P, x, v, h, m, kind, vw, rho, nbrs, 3)
+
+
+def pressure(P, x, v, h, m, kind, vw, rho, nbrs):
+    """Eq. 3 (row 2) with Eq. 5-6 alone: the pressure acceleration (N, 3)."""
+    return _pair_fn("orc_pressure", P, x, v, h, m, kind, vw, rho, nbrs, 3)
+
+
+def continuity(P, x, v, h, m, kind, vw, rho, nbrs):
+    """Eq. 3 (row 1) with U* of Eq. 5 (row 1): d rho / dt (N,)."""
+    return _pair_fn("orc_continuity", P, x, v, h, m, kind, vw, rho, nbrs, 1)
+
+
+def riemann_ustar(P, pl, pr, rhobar, ul, ur):
+    return lib().orc_riemann_ustar(ctypes.byref(P), pl, pr, rhobar, ul, ur)
+
+
+def advection_step(P, v, kind):
+    """Eq. 9-10 with h = h_min: returns (Dt_ad, |v|_ad)."""
+    n = len(v)
+    v = _vec(v, n)
+    kind = _sca(kind, n, np.int8)
+    vad = ctypes.c_double(0.0)
+    dt = lib().orc_advection_step(ctypes.byref(P), n, _d(v), kind.ctypes.data_as(_bp), ctypes.byref(vad))
+    return dt, vad.value
+
+
+def acoustic_step(P, v, kind):
+    """Eq. 11 with h = h_min."""
+    n = len(v)
+    v = _vec(v, n)
+    kind = _sca(kind, n, np.int8)
+    return lib().orc_acoustic_step(ctypes.byref(P), n, _d(v), kind.ctypes.data_as(_bp))
+
+
+def dual_step(P, case, state, sigma0, mode="cells"):
+    """One advection step of the dual-criteria scheme.  ``state`` holds x, v
+    ((N, 3) float64) and drho ((N,), zero at the start of a run); returns a
+    new dict with x, v, rho, drho, a (last substep), dr, R, chi, Dt and the
+    number of acoustic substeps (inputs untouched)."""
+    n = len(state["x"])
+    x, v = _vec(state["x"], n).copy(), _vec(state["v"], n).copy()
+    drho = _sca(state.get("drho", 0.0), n).copy()
+    h, m, kind, vw = _case_arrays(case, n)
+    s0 = _sca(sigma0, n)
+    rho, chi = np.zeros(n), np.zeros(n)
+    a, dr, R = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    Dt = ctypes.c_double(0.0)
+    k = lib().orc_dual_step(ctypes.byref(P), n, _d(x), _d(v), _d(rho), _d(drho), _d(h), _d(m),
+                            kind.ctypes.data_as(_bp), _d(vw), _d(s0), {"brute": 0, "cells": 1}[mode], _d(a), _d(dr),
+                            _d(R), _d(chi), ctypes.byref(Dt))
+    if k < 0:
+        raise MemoryError("oracle dual step failed")
+    return {"x": x, "v": v, "rho": rho, "drho": drho, "a": a, "dr": dr, "R": R, "chi": chi, "Dt": Dt.value,
+            "substeps": int(k)}

@@ -26,6 +26,12 @@
  *   limited correction, h = h_min ...................... Eq. 16
  *   kick-drift-kick integration with the correction
  *   applied once per step .............................. Sec. 1, Sec. 3
+ *   dual-criteria time stepping: advection steps with
+ *   density reinitialisation and the correction, acoustic
+ *   substeps with the Riemann pressure force and the
+ *   Riemann continuity equation (U*) ................... Sec. 2.4, Eq. 3 (first row), Eq. 5 (first row),
+ *                                                          Eq. 9-11, Sec. 3 (correction per advection step)
+ *   background pressure p0 = alpha rho0 |v|_ad^2 ....... Eq. 12-13, alpha = 7
  *
  * Readings where the paper is silent or ambiguous (each is also listed in the
  * design notes of the repository):
@@ -50,6 +56,22 @@
  *     checks this branch.
  *   - pair smoothing length for variable resolution: PARITY UNPINNED beyond
  *     the conservation and brute-force checks (the paper does not state it).
+ *   - dual-criteria step (the paper names the scheme and its two criteria;
+ *     the order of operations is read as follows): at the start of an
+ *     advection step the neighbour set is rebuilt and then frozen for the
+ *     whole step (W and W' are evaluated at the current distance, so a pair
+ *     that leaves the support stops contributing and a pair that enters it
+ *     is not seen until the next advection step); the density is
+ *     reinitialised by summation, the viscous acceleration is evaluated once
+ *     and held, and the transport displacement is computed and added to the
+ *     positions once.  Each acoustic substep dt = min(dt_ac, Dt_ad - t) then
+ *     does rho += dt/2 drho; x += dt/2 v; v += dt (a_pressure + a_viscous
+ *     + g); x += dt/2 v; drho from the Riemann continuity equation;
+ *     rho += dt/2 drho; drho is carried to the next substep and across
+ *     advection steps (zero at the start).  The last substep ends exactly at
+ *     Dt_ad.  U* is Eq. 5 (first row) with p_L, p_R read as p_l, p_r and no
+ *     limiter; a wall j stands in with rho_j = rho_i, p_j = p_i and its
+ *     prescribed velocity, as in the force sums.
  */
 #include <math.h>
 #include <stdint.h>
@@ -83,6 +105,7 @@ typedef struct {
     double cfl_ad, cfl_ac;     /* Eq. 9, 11 */
     double u_ref;              /* reference velocity (Eq. 10) */
     double dt_tv;              /* step size in the background-pressure mode (tv_mode 3) */
+    double tv_p0;              /* background pressure of Eq. 12; 0: rho0 c^2 (kick-drift-kick) */
 } orc_params;
 
 static int g_threads = 1;
@@ -433,7 +456,8 @@ void orc_forces(const orc_params* P, int64_t n, const double* x, const double* v
         /* Eq. 12 in kick-drift-kick: the background-pressure acceleration
          * a_bg = -2 sum_j m_j p0 / (rho_i rho_j) grad W_ij = -(2 p0 / rho_i) R_i
          * moves the particle by dt^2/2 a_bg in the drift. */
-        double bg = -(P->dt_tv * P->dt_tv * (P->rho0 * c2) / rho_i);
+        double p0 = P->tv_p0 > 0.0 ? P->tv_p0 : P->rho0 * c2;
+        double bg = -(P->dt_tv * P->dt_tv * p0 / rho_i);
         for (int d = 0; d < 3; ++d) {
             a[3 * i + d] = ai[d];
             R[3 * i + d] = Ri[d];
@@ -777,4 +801,222 @@ int orc_force_pass_adjoint(const orc_params* P, int64_t n, const double* x, cons
     nbr_free(&L);
     free(Rf); free(af); free(drf); free(rho);
     return 0;
+}
+
+
+/* ===================================================================
+ * Dual-criteria time stepping (Sec. 2.4; the correction once per
+ * advection step, Sec. 3).
+ * =================================================================== */
+
+/* Eq. 7 alone: viscous acceleration of every fluid i (walls: zeros). */
+void orc_viscous(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                 const double* m, const int8_t* kind, const double* vw, const double* rho, const int64_t* start,
+                 const int64_t* idx, double* a_nu)
+{
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double ai[3] = {0, 0, 0};
+        if (!kind[i]) {
+            const double rho_i = rho[i];
+            const double* vi = v + 3 * i;
+            for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+                int64_t j = idx[k];
+                if (j == i) continue;
+                double rij[3];
+                orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+                double r = norm3(rij);
+                if (r == 0.0) continue;
+                double dw = orc_kernel_dW(r, orc_pair_h(P, h[i], h[j]), P->dim);
+                int wall = kind[j] != 0;
+                double rho_j = wall ? rho_i : rho[j];
+                const double* vj = wall ? vw + 3 * j : v + 3 * j;
+                double cv = 2.0 * m[j] * P->eta / (rho_i * rho_j) * dw / r;
+                for (int d = 0; d < 3; ++d) ai[d] += cv * (vi[d] - vj[d]);
+            }
+        }
+        for (int d = 0; d < 3; ++d) a_nu[3 * i + d] = ai[d];
+    }
+}
+
+/* Eq. 3 (second row) with the interface pressure of Eq. 5-6 alone: the
+ * pressure acceleration of every fluid i (walls: zeros). */
+void orc_pressure(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                  const double* m, const int8_t* kind, const double* vw, const double* rho, const int64_t* start,
+                  const int64_t* idx, double* a_p)
+{
+    const double c2 = P->c * P->c;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double ai[3] = {0, 0, 0};
+        if (!kind[i]) {
+            const double rho_i = rho[i];
+            const double p_i = c2 * (rho_i - P->rho0);
+            const double* vi = v + 3 * i;
+            for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+                int64_t j = idx[k];
+                if (j == i) continue;
+                double rij[3];
+                orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+                double r = norm3(rij);
+                if (r == 0.0) continue;
+                double dw = orc_kernel_dW(r, orc_pair_h(P, h[i], h[j]), P->dim);
+                double e[3];
+                for (int d = 0; d < 3; ++d) e[d] = -rij[d] / r;
+                int wall = kind[j] != 0;
+                double rho_j = wall ? rho_i : rho[j];
+                double p_j = wall ? p_i : c2 * (rho_j - P->rho0);
+                const double* vj = wall ? vw + 3 * j : v + 3 * j;
+                double pstar = orc_riemann_pstar(P, p_i, p_j, 0.5 * (rho_i + rho_j), dot3(vi, e), dot3(vj, e));
+                double cp = -2.0 * m[j] * pstar / (rho_i * rho_j);
+                for (int d = 0; d < 3; ++d) ai[d] += cp * dw * rij[d] / r;
+            }
+        }
+        for (int d = 0; d < 3; ++d) a_p[3 * i + d] = ai[d];
+    }
+}
+
+/* Eq. 5 (first row) with p_L, p_R read as p_l, p_r: interface velocity. */
+double orc_riemann_ustar(const orc_params* P, double pl, double pr, double rhobar, double ul, double ur)
+{
+    return 0.5 * (ul + ur) + 0.5 * (pl - pr) / (rhobar * P->c);
+}
+
+/* Eq. 3 (first row): drho_i/dt = 2 rho_i sum_j V_j (U*_ij - U_l) dW/dr for
+ * every fluid i (walls: zero). */
+void orc_continuity(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                    const double* m, const int8_t* kind, const double* vw, const double* rho, const int64_t* start,
+                    const int64_t* idx, double* drho)
+{
+    const double c2 = P->c * P->c;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        const double rho_i = rho[i];
+        if (!kind[i]) {
+            const double p_i = c2 * (rho_i - P->rho0);
+            const double* vi = v + 3 * i;
+            for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+                int64_t j = idx[k];
+                if (j == i) continue;
+                double rij[3];
+                orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+                double r = norm3(rij);
+                if (r == 0.0) continue;
+                double dw = orc_kernel_dW(r, orc_pair_h(P, h[i], h[j]), P->dim);
+                double e[3];
+                for (int d = 0; d < 3; ++d) e[d] = -rij[d] / r;
+                int wall = kind[j] != 0;
+                double rho_j = wall ? rho_i : rho[j];
+                double p_j = wall ? p_i : c2 * (rho_j - P->rho0);
+                const double* vj = wall ? vw + 3 * j : v + 3 * j;
+                double ul = dot3(vi, e);
+                double ustar = orc_riemann_ustar(P, p_i, p_j, 0.5 * (rho_i + rho_j), ul, dot3(vj, e));
+                s += m[j] / rho_j * (ustar - ul) * dw;
+            }
+        }
+        drho[i] = kind[i] ? 0.0 : 2.0 * rho_i * s;
+    }
+}
+
+/* Eq. 9-10 with h = h_min: the advection step size; *vad_out (may be NULL)
+ * receives the advection speed |v|_ad. */
+double orc_advection_step(const orc_params* P, int64_t n, const double* v, const int8_t* kind, double* vad_out)
+{
+    double vmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        double sp = sqrt(dot3(v + 3 * i, v + 3 * i));
+        vmax = sp > vmax ? sp : vmax;
+    }
+    double nu = P->eta / P->rho0;
+    double vad = fmax(vmax, fmax(nu / P->h_min, P->u_ref));
+    if (vad_out) *vad_out = vad;
+    return P->cfl_ad * P->h_min / vad;
+}
+
+/* Eq. 11 with h = h_min: the acoustic step size. */
+double orc_acoustic_step(const orc_params* P, int64_t n, const double* v, const int8_t* kind)
+{
+    double vmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        double sp = sqrt(dot3(v + 3 * i, v + 3 * i));
+        vmax = sp > vmax ? sp : vmax;
+    }
+    return P->cfl_ac * P->h_min / (vmax + P->c);
+}
+
+#define ORC_BG_ALPHA 7.0   /* alpha of Eq. 13 */
+
+/* One advection step of the dual-criteria scheme, in place on x, v, rho,
+ * drho (the state); a receives the last substep's acceleration, dr, R, chi
+ * the correction of this step, *Dt_out the advection step size.  Returns the
+ * number of acoustic substeps, or -1 if memory runs out. */
+int64_t orc_dual_step(const orc_params* P, int64_t n, double* x, double* v, double* rho, double* drho,
+                      const double* h, const double* m, const int8_t* kind, const double* vw, const double* sigma0,
+                      int mode, double* a, double* dr, double* R, double* chi, double* Dt_out)
+{
+    nbrlist L;
+    if (nbr_build(P, n, x, h, mode, &L)) return -1;
+    double* a_nu = (double*)malloc((size_t)(3 * n > 0 ? 3 * n : 1) * sizeof(double));
+    double* a_p = (double*)malloc((size_t)(3 * n > 0 ? 3 * n : 1) * sizeof(double));
+    if (!a_nu || !a_p) { free(a_nu); free(a_p); nbr_free(&L); return -1; }
+    /* advection step: density reinitialisation (Eq. 8), step size (Eq. 9-10),
+     * viscous acceleration (Eq. 7), transport correction (Eq. 14-16, or
+     * Eq. 12 with p0 of Eq. 13), applied once */
+    orc_density(P, n, x, h, kind, sigma0, L.start, L.idx, rho, NULL);
+    double vad;
+    const double Dt = orc_advection_step(P, n, v, kind, &vad);
+    orc_params Q = *P;
+    Q.dt_tv = Dt;
+    Q.tv_p0 = ORC_BG_ALPHA * P->rho0 * vad * vad;
+    orc_viscous(&Q, n, x, v, h, m, kind, vw, rho, L.start, L.idx, a_nu);
+    orc_forces(&Q, n, x, v, h, m, kind, vw, rho, L.start, L.idx, a_p, R, chi, dr);
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        for (int d = 0; d < P->dim; ++d) x[3 * i + d] = x[3 * i + d] + dr[3 * i + d];
+    }
+    /* acoustic substeps (Eq. 11) */
+    double t = 0.0;
+    int64_t k = 0;
+    for (;;) {
+        double dt = orc_acoustic_step(P, n, v, kind);
+        const double rem = Dt - t;
+        const int last = dt >= rem;
+        if (last) dt = rem;
+        const double hdt = 0.5 * dt;
+        for (int64_t i = 0; i < n; ++i) {
+            if (kind[i]) continue;
+            rho[i] = rho[i] + hdt * drho[i];
+            for (int d = 0; d < P->dim; ++d) x[3 * i + d] = x[3 * i + d] + hdt * v[3 * i + d];
+        }
+        orc_pressure(P, n, x, v, h, m, kind, vw, rho, L.start, L.idx, a_p);
+        for (int64_t i = 0; i < n; ++i) {
+            for (int d = 0; d < 3; ++d) {
+                double ad = kind[i] || d >= P->dim ? 0.0 : a_p[3 * i + d] + a_nu[3 * i + d] + P->g[d];
+                a[3 * i + d] = ad;
+                if (!kind[i]) v[3 * i + d] = v[3 * i + d] + dt * ad;
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (kind[i]) continue;
+            for (int d = 0; d < P->dim; ++d) x[3 * i + d] = x[3 * i + d] + hdt * v[3 * i + d];
+        }
+        orc_continuity(P, n, x, v, h, m, kind, vw, rho, L.start, L.idx, drho);
+        for (int64_t i = 0; i < n; ++i) {
+            if (kind[i]) continue;
+            rho[i] = rho[i] + hdt * drho[i];
+        }
+        t = t + dt;
+        ++k;
+        if (last) break;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!kind[i]) orc_wrap(P, x + 3 * i);
+    if (Dt_out) *Dt_out = Dt;
+    free(a_nu);
+    free(a_p);
+    nbr_free(&L);
+    return k;
 }
