@@ -20,6 +20,9 @@
  *      dr_i = xi chi_i h^2 R_i (Eq. 14-16);
  *   5. closing half kick, FP64 diagnostics and the next step size
  *      min(dt_ad, dt_ac) (Eq. 9-11, h = h_min).
+ * The dual-criteria integrator of Sec. 2.4 (SPH_INT_DUAL) is the other
+ * choice: one advection step with the density reinitialisation and the
+ * correction, then acoustic substeps with the Riemann continuity equation.
  *
  * Conventions.
  *   - Vectors crossing the ABI are row-major [n][3] doubles (x, y, z per
@@ -64,7 +67,9 @@ typedef enum sph_status {
     SPH_ERR_ARG = 1,        /* invalid argument (host check) */
     SPH_ERR_CUDA = 2,       /* a CUDA call failed */
     SPH_ERR_WORKSPACE = 3,  /* workspace NULL, misaligned or too small */
-    SPH_ERR_OVERFLOW = 4,   /* device: a cell held more particles than supported */
+    SPH_ERR_OVERFLOW = 4,   /* device: a cell held more particles than supported, or (SPH_INT_DUAL)
+                               a particle had more neighbours than its frozen list holds
+                               (128 in 3-D, 96 in 2-D) */
     SPH_ERR_NAN = 5,        /* device: non-finite position or velocity */
     SPH_ERR_DOMAIN = 6,     /* device: particle left a non-periodic box */
     SPH_ERR_STATE = 7,      /* call order: e.g. sph_step before sph_build_cells */
@@ -74,6 +79,21 @@ typedef enum sph_status {
 enum { SPH_TV_OFF = 0, SPH_TV_LIMITED = 1, SPH_TV_UNLIMITED = 2, SPH_TV_BACKGROUND = 3 };
 enum { SPH_TVH_MIN = 0, SPH_TVH_PARTICLE = 1 };
 enum { SPH_HPAIR_MEAN = 0, SPH_HPAIR_MAX = 1 };
+/* Time integrators. */
+enum {
+    SPH_INT_KDK = 0,    /* single-rate kick-drift-kick, dt = min(dt_ad, dt_ac), the
+                           correction applied in every drift (Sec. 1, Sec. 3) */
+    SPH_INT_DUAL = 1    /* dual-criteria time stepping (Sec. 2.4): one sph_step is one
+                           advection step Dt_ad (Eq. 9-10) -- cell list rebuilt and its
+                           neighbour set frozen for the step, density reinitialised by
+                           summation (Eq. 8), viscous force (Eq. 7) held, transport
+                           correction (Eq. 14-16; Eq. 12 with p0 = 7 rho0 |v|_ad^2 of
+                           Eq. 13) added to the positions once -- followed by acoustic
+                           substeps dt = min(dt_ac, Dt_ad - t) (Eq. 11) of drift dt/2,
+                           kick with the Riemann pressure force (Eq. 3 row 2, Eq. 5-6),
+                           drift dt/2, and the Riemann continuity equation (Eq. 3 row 1,
+                           U* of Eq. 5 row 1) integrating the density by halves */
+};
 
 /* Plain-data parameter block.  sph_default_params fills the paper's
  * constants; the caller sets the domain and the fluid. */
@@ -108,7 +128,11 @@ typedef struct sph_params {
     int32_t h_pair;         /* SPH_HPAIR_*: h_ij = (h_i+h_j)/2 (default) or max */
     int32_t kahan;          /* FP32 form: 1 = compensated pair sums (default) */
     int32_t adjoint_steps;  /* longest segment sph_step_adjoint will replay
-                               (0: no adjoint buffers in the workspace) */
+                               (0: no adjoint buffers in the workspace; must be 0
+                               with SPH_INT_DUAL) */
+    int32_t integrator;     /* SPH_INT_*: kick-drift-kick (default) or dual-criteria;
+                               SPH_INT_DUAL requires fixed_dt = 0 */
+    int32_t pad0;
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -124,6 +148,7 @@ typedef struct sph_diag {
     double dt;              /* step size used by the last step */
     double dt_next;         /* step size the next step will use */
     double steps;           /* steps taken since sph_build_cells */
+    double substeps;        /* SPH_INT_DUAL: acoustic substeps of the last advection step */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;
@@ -168,8 +193,21 @@ SPH_API sph_status sph_set_state(sph_ctx* ctx, const double* x, const double* v,
  * the diagnostics and the first dt (Eq. 9-11, or fixed_dt). */
 SPH_API sph_status sph_build_cells(sph_ctx* ctx);
 
-/* Advance nsteps >= 0 kick-drift-kick steps on the context's stream. */
+/* Advance nsteps >= 0 steps on the context's stream: kick-drift-kick steps,
+ * or with SPH_INT_DUAL advection steps, each with its acoustic substeps.  The
+ * dual integrator decides on the device when an advection step is complete;
+ * the host waits for the stream once per advection step to learn it. */
 SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
+
+/* SPH_INT_DUAL: set or read the density rate d rho/dt that the integrator
+ * carries from one acoustic substep to the next and across advection steps
+ * ([n] doubles, caller's particle order, walls 0).  sph_set_state sets it to
+ * zero; call sph_set_density_rate after sph_set_state and before
+ * sph_build_cells.  Reading waits for the copy when drho is host memory.
+ * SPH_ERR_ARG with the kick-drift-kick integrator or a NULL pointer;
+ * SPH_ERR_STATE before sph_set_state. */
+SPH_API sph_status sph_set_density_rate(sph_ctx* ctx, const double* drho);
+SPH_API sph_status sph_get_density_rate(sph_ctx* ctx, double* drho);
 
 /* Override the step size of the next step (> 0). */
 SPH_API sph_status sph_set_dt(sph_ctx* ctx, double dt);
@@ -208,7 +246,9 @@ enum {
     SPH_K_DENSITY = 4,     /* density summation (Eq. 8) */
     SPH_K_FORCES = 5,      /* fused pair pass (Eq. 3, 5-7, 14-16) + closing kick */
     SPH_K_FINALIZE = 6,    /* FP64 reductions and dt (Eq. 9-11) */
-    SPH_K_NCLASS = 7
+    SPH_K_ADVECT = 7,      /* SPH_INT_DUAL: viscous force + transport correction of an advection step */
+    SPH_K_ACOUSTIC = 8,    /* SPH_INT_DUAL: all acoustic substeps of an advection step */
+    SPH_K_NCLASS = 9
 };
 
 /* Per-kernel timing (tracing).  After sph_profile_begin, each of the next

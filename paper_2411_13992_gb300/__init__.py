@@ -33,9 +33,11 @@ __all__ = [
     "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint",
     "params_from_case", "Simulation", "Rollout",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TV_BACKGROUND", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
+    "INT_KDK", "INT_DUAL", "sph_set_density_rate", "sph_get_density_rate",
 ]
 
 TV_OFF, TV_LIMITED, TV_UNLIMITED, TV_BACKGROUND = 0, 1, 2, 3
+INT_KDK, INT_DUAL = 0, 1
 TVH_MIN, TVH_PARTICLE = 0, 1
 HPAIR_MEAN, HPAIR_MAX = 0, 1
 
@@ -58,7 +60,7 @@ class SphParams(ctypes.Structure):
         ("cfl_ad", ctypes.c_double), ("cfl_ac", ctypes.c_double), ("u_ref", ctypes.c_double),
         ("fixed_dt", ctypes.c_double),
         ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32),
-        ("adjoint_steps", ctypes.c_int32),
+        ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("pad0", ctypes.c_int32),
     ]
 
 
@@ -69,13 +71,13 @@ class SphDiag(ctypes.Structure):
         ("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
         ("vmax", ctypes.c_double), ("vt_max", ctypes.c_double), ("dr_max", ctypes.c_double),
         ("n_chi", ctypes.c_double), ("dt", ctypes.c_double), ("dt_next", ctypes.c_double),
-        ("steps", ctypes.c_double),
+        ("steps", ctypes.c_double), ("substeps", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {"mass": self.mass, "momentum": np.array(self.momentum[:]), "ke": self.kinetic, "vmax": self.vmax,
                 "vt_max": self.vt_max, "dr_max": self.dr_max, "n_chi": int(self.n_chi), "dt": self.dt,
-                "dt_next": self.dt_next, "steps": int(self.steps)}
+                "dt_next": self.dt_next, "steps": int(self.steps), "substeps": int(self.substeps)}
 
 
 class SphError(RuntimeError):
@@ -127,6 +129,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_double)]),
             "sph_force_pass_adjoint": (_i32, [_vp] + [_vp] * 6 + [ctypes.POINTER(ctypes.c_double)]),
             "sph_fma_peak": (_i32, [_i32, _i32, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+            "sph_set_density_rate": (_i32, [_vp, _vp]),
+            "sph_get_density_rate": (_i32, [_vp, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -264,7 +268,7 @@ def sph_launch_count(ctx) -> int:
     return int(load().sph_launch_count(ctx))
 
 
-KERNEL_CLASSES = 7
+KERNEL_CLASSES = 9
 
 
 def sph_profile_begin(ctx, max_steps: int) -> None:
@@ -281,6 +285,17 @@ def sph_profile_end(ctx) -> dict:
 
 def sph_kernel_class_name(k: int) -> str:
     return load().sph_kernel_class_name(int(k)).decode()
+
+
+def sph_set_density_rate(ctx, drho) -> None:
+    """Dual-criteria integrator: the carried d rho/dt ([n], caller order)."""
+    keep = []
+    _check(load().sph_set_density_rate(ctx, _ptr(drho, keep, np.float64)), "sph_set_density_rate")
+
+
+def sph_get_density_rate(ctx, out) -> None:
+    keep = []
+    _check(load().sph_get_density_rate(ctx, _ptr(out, keep, np.float64)), "sph_get_density_rate")
 
 
 def sph_fma_peak(precision: int, blocks: int, iters: int, sink, stream=None) -> float:
@@ -401,10 +416,17 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.ctx = sph_create(self.params, self.n, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
-    def set_state(self, x=None, v=None, a=None, dr=None, sigma0=None):
+    def set_state(self, x=None, v=None, a=None, dr=None, sigma0=None, drho=None):
         c = self.case
         sph_set_state(self.ctx, c["x"] if x is None else x, c["v"] if v is None else v, a, dr, c["h"], c["m"],
                       c.get("kind"), c.get("vw"), sigma0)
+        if drho is not None:
+            sph_set_density_rate(self.ctx, drho)
+
+    def density_rate(self):
+        out = np.zeros(self.n)
+        sph_get_density_rate(self.ctx, out)
+        return out
 
     def build_cells(self):
         sph_build_cells(self.ctx)

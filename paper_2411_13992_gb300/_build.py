@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libsphtv.so"
-SOURCES = ["sph_api.cu", "k_cells.cu", "k_pair.cu", "k_pair32.cu", "k_io.cu", "k_adjoint.cu", "k_peak.cu"]
+SOURCES = ["sph_api.cu", "k_cells.cu", "k_pair.cu", "k_pair32.cu", "k_io.cu", "k_adjoint.cu", "k_peak.cu", "k_dual.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-I" + INCLUDE, "-I" + CSRC]

@@ -16,12 +16,26 @@ constexpr double kPi = 3.14159265358979323846;
 // Device error word bits (sticky; read back by sph_sync).
 enum : uint32_t { ERRB_OVERFLOW = 1u, ERRB_NAN = 2u, ERRB_DOMAIN = 4u, ERRB_INPUT = 8u };
 
+// Device state of the dual-criteria integrator (doubles).
+enum {
+    DU_DT_AD = 0,     // advection step size of the current step (Eq. 9-10)
+    DU_VAD = 1,       // advection speed |v|_ad (Eq. 10)
+    DU_T = 2,         // time advanced by the substeps so far
+    DU_DT = 3,        // size of the next (or current) acoustic substep (Eq. 11)
+    DU_HDT_PREV = 4,  // half the previous substep (its density update is completed late)
+    DU_LAST = 5,      // 1: the current substep ends the advection step
+    DU_DONE = 6,      // 1: the advection step is complete (later substep launches are no-ops)
+    DU_K = 7,         // substeps taken in the current advection step
+    DU_FIRST = 8,     // 1: the next substep is the first of its advection step
+    DU_COUNT = 16
+};
+
 // Number of FP64 per-block partial values the fused force kernel writes.
 constexpr int kNPart = 10;
 // Indices into the device diagnostics block (doubles).
 enum {
     DG_MASS = 0, DG_MOM = 1, DG_KE = 4, DG_VMAX = 5, DG_VTMAX = 6, DG_DRMAX = 7, DG_NCHI = 8,
-    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_COUNT = 16
+    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_SUBSTEPS = 12, DG_COUNT = 16
 };
 
 // Cell grid of the cell-linked list: edge >= 2 h_max / R along every axis,
@@ -195,6 +209,24 @@ __device__ __forceinline__ double min_image(const Grid& G, double xi, double xj,
     return dx;
 }
 
+// Neighbour-list entries: (j << kCodeBits) | stencil code of j's cell, the
+// code being (dx + R) + S (dy + R) + S^2 (dz + R) with S = 2R + 1.
+constexpr int kSide = 2 * kStencilR + 1;                 // stencil cells per axis
+constexpr int kCodes = kSide * kSide * kSide;            // 125 for R = 2
+constexpr int kCodeBits = 7;
+static_assert(kCodes <= (1 << kCodeBits), "stencil code does not fit");
+
+// FP32 shift of a neighbour cell from its stencil code: the pair vector is
+// (o_i - o_j) + shift for cell-relative offsets o.
+__device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* sh)
+{
+    const int dx = (int)(code % kSide) - kStencilR, dy = (int)((code / kSide) % kSide) - kStencilR,
+              dz = (int)(code / (kSide * kSide)) - kStencilR;
+    sh[0] = -(float)dx * G.edgef[0];
+    sh[1] = -(float)dy * G.edgef[1];
+    sh[2] = -(float)dz * G.edgef[2];
+}
+
 // ------------------------------------------------------------ buffers
 
 // Particle arrays of one cell-sorted copy of the state.
@@ -204,6 +236,7 @@ struct StateSet {
     Real* v;        // [DIM][n] velocities (walls: prescribed velocity)
     Real* a;        // [DIM][n] accelerations (only carried by the first sort)
     Real* dr;       // [DIM][n] transport displacements (only carried by the first sort)
+    Real* drho;     // [n] density rate of the dual-criteria integrator (carried by every sort), or null
     double* h;      // [n] smoothing lengths
     double* m;      // [n] masses
     double* s0;     // [n] reference sums sigma0 (Eq. 8)

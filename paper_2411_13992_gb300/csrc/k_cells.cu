@@ -8,7 +8,9 @@
 //
 // The kick-drift follows the kick-drift-kick scheme the paper names (Sec. 1,
 // Sec. 3): v += dt/2 a; x += dt v + dr, where dr is the transport-velocity
-// displacement of the previous step (Eq. 16), applied once per step.
+// displacement of the previous step (Eq. 16), applied once per step.  With the
+// dual-criteria integrator (Sec. 2.4) the substeps have moved the particles
+// already and this stage only wraps the periodic axes.
 #include "common.cuh"
 #include "launch.h"
 
@@ -39,7 +41,19 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
 #pragma unroll
     for (int d = 0; d < DIM; ++d) xs[d] = S.x[(size_t)d * n + i];
     uint32_t e = 0;
-    if (drift && S.kind[i] == 0) {
+    if (drift == 2 && S.kind[i] == 0) {
+        // dual-criteria integrator: the substeps moved the particles; only
+        // the periodic wrap is left to do here
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            if (!G.periodic[d]) continue;
+            double xn = xs[d];
+            if (xn < G.lo[d]) xn = __dadd_rn(xn, G.L[d]);
+            else if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
+            if (xn != xs[d]) S.x[(size_t)d * n + i] = xn;
+            xs[d] = xn;
+        }
+    } else if (drift == 1 && S.kind[i] == 0) {
         const double dt = *dt_ptr;
         const double hdt = 0.5 * dt;
 #pragma unroll
@@ -218,6 +232,7 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
             dst.dr[dof] = src.dr[so];
         }
     }
+    if (src.drho) dst.drho[k] = src.drho[i];
     double h = src.h[i];
     double m = src.m[i];
     dst.h[k] = h;

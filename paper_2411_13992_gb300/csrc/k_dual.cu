@@ -1,0 +1,661 @@
+// k_dual.cu -- the dual-criteria time stepping of libsphtv (Sec. 2.4).
+//
+// One advection step (size Dt_ad, Eq. 9-10) follows the cell sort and the
+// density pass; the density pass writes each particle's neighbour list, and
+// that list stays frozen for the whole advection step (W' is evaluated at the
+// current distance, so a pair that leaves the support stops contributing):
+//   k_dual_begin      : Dt_ad, |v|_ad and the first substep size (Eq. 9-11)
+//   k_dual_advect     : viscous acceleration (Eq. 7), held for the step, and
+//                       the transport correction dr (Eq. 14-16, or Eq. 12
+//                       with p0 = 7 rho0 |v|_ad^2 of Eq. 13)
+// then acoustic substeps dt = min(dt_ac, Dt_ad - t) (Eq. 11), each
+//   k_dual_first_half : rho += dt/2 drho (after completing the previous
+//                       substep's second half), x += dr (first substep of the
+//                       advection step only), x += dt/2 v
+//   k_dual_pressure   : Riemann pressure force (Eq. 3 row 2, Eq. 5-6) + the
+//                       held viscous force + g; v += dt a
+//   k_dual_drift      : x += dt/2 v
+//   k_dual_continuity : drho_i = 2 rho_i sum_j V_j (U* - U_l) dW/dr (Eq. 3
+//                       row 1, U* of Eq. 5 row 1), diagnostics partials
+//   k_dual_finalize   : reduction; the next substep size; marks the
+//                       advection step done after its last substep
+// and, once per advection step, k_dual_complete: rho += dt/2 drho of the last
+// substep.  Every substep kernel returns at once when the advection step is
+// done, so the host launches a few substeps more than it expects and waits
+// for the stream once per advection step.
+//
+// Readings (as in the kick-drift-kick passes): e_ij points from i to j;
+// grad W_ij = W'(r) (x_i - x_j)/r; V_j = m_j / rho_j; rho_bar is the mean
+// density, c_bar = c; U* uses p_l, p_r for the p_L, p_R of Eq. 5 and no
+// limiter; a wall j stands in with rho_j = rho_i, p_j = p_i and its
+// prescribed velocity.  The density lives as w = rho - rho0 beside the
+// velocity (vr), so the FP32 form keeps the digits of the deviation.
+#include <type_traits>
+
+#include "common.cuh"
+#include "launch.h"
+#include "pair_physics.cuh"
+
+namespace sphtv {
+
+namespace {
+
+template <typename Real> struct V4;
+template <> struct V4<float> {
+    using T = float4;
+    __device__ static T make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <> struct V4<double> {
+    using T = double4_32a;
+    __device__ static T make(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
+};
+
+template <typename Real>
+struct DualK {
+    int n, cap;
+    StateSet<Real> S;
+    typename V4<Real>::T* vr;
+    float4* pos4;            // FP32 form: cell-relative offsets (updated by the drifts), m or h
+    const int32_t* cell_of;  // FP32 form: home cell of the advection step
+    const float* mf;         // FP32 form: masses
+    const uint32_t* nbl;
+    const int32_t* nbc;
+    Real* anu;               // [DIM][n] viscous acceleration held for the advection step
+    Real* R;                 // [DIM][n] residual
+    Real* chi;               // [n] limiter
+    double* du;              // DU_* state
+    double* partials;
+    uint32_t* err;
+};
+
+constexpr int kTPB64 = 256;
+constexpr int kTPB32 = 128;
+template <typename Real> constexpr int tpb() { return sizeof(Real) == 8 ? kTPB64 : kTPB32; }
+
+__device__ __forceinline__ bool dual_done(const double* du) { return du[DU_DONE] != 0.0; }
+
+// Shared table of the FP32 stencil shifts (FP32 form only).
+template <typename Real>
+__device__ __forceinline__ void fill_shift_table(const Grid& G, float4* tab)
+{
+    if (sizeof(Real) == 4) {
+        for (int t = threadIdx.x; t < kCodes; t += blockDim.x) {
+            float sh[3];
+            code_shift(G, (uint32_t)t, sh);
+            tab[t] = make_float4(sh[0], sh[1], sh[2], 0.f);
+        }
+    }
+    __syncthreads();
+}
+
+// Visit the frozen neighbour list of particle i: f(j, rv, r2) with rv the
+// pair vector x_i - x_j at the current positions.
+template <typename Real, int DIM, typename F>
+__device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, const float4* tab, int i, int cnt, F& f)
+{
+    const int n = A.n;
+    if constexpr (std::is_same<Real, double>::value) {
+        double xi[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) xi[d] = A.S.x[(size_t)d * n + i];
+        for (int k = 0; k < cnt; ++k) {
+            const int j = (int)(A.nbl[(size_t)k * n + i] >> kCodeBits);
+            double rv[3] = {0.0, 0.0, 0.0};
+            double r2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                rv[d] = min_image(G, xi[d], A.S.x[(size_t)d * n + j], d);
+                r2 += rv[d] * rv[d];
+            }
+            f(j, rv, r2);
+        }
+    } else {
+        const float4 pi = A.pos4[i];
+        const float oi[3] = {pi.x, pi.y, pi.z};
+        for (int k = 0; k < cnt; ++k) {
+            const uint32_t e = A.nbl[(size_t)k * n + i];
+            const int j = (int)(e >> kCodeBits);
+            const float4 pj = A.pos4[j];
+            const float4 sh = tab[e & ((1u << kCodeBits) - 1u)];
+            float rv[3] = {0.f, 0.f, 0.f};
+            rv[0] = (oi[0] - pj.x) + sh.x;
+            rv[1] = (oi[1] - pj.y) + sh.y;
+            float r2 = rv[0] * rv[0] + rv[1] * rv[1];
+            if (DIM == 3) {
+                rv[2] = (oi[2] - pj.z) + sh.z;
+                r2 += rv[2] * rv[2];
+            }
+            f(j, rv, r2);
+        }
+    }
+}
+
+// Smoothing length of particle j and its mass, from the layout of the form.
+template <typename Real, bool UNIFORM>
+__device__ __forceinline__ void h_m_of(const DualK<Real>& A, const Consts<Real>& K, int j, Real& h, Real& m)
+{
+    if constexpr (std::is_same<Real, double>::value) {
+        h = A.S.h[j];
+        m = A.S.m[j];
+    } else {
+        const float w = A.pos4[j].w;
+        h = UNIFORM ? K.h_u : w;
+        m = UNIFORM ? w : A.mf[j];
+    }
+}
+
+// W'(r, h), zero at and beyond the support 2h (the list is frozen while the
+// particles move).
+template <typename Real, int DIM>
+__device__ __forceinline__ Real dw_clamped(Real r, Real h)
+{
+    if (!(r < Real(2) * h)) return Real(0);
+    return wendland_dW<DIM, Real>(r, Real(1) / h);
+}
+
+// FP32 x offsets of particle i from its home cell's origin (as the permute forms them).
+template <int DIM>
+__device__ __forceinline__ void store_offsets(float4* pos4, const int32_t* cell_of, const Grid& G, int i,
+                                             const double* xs)
+{
+    int c[3];
+    cell_decode(G, cell_of[i], c);
+    float4 p = pos4[i];
+    float o[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d] = (float)(xs[d] - (G.lo[d] + (double)c[d] * G.edge[d]));
+    pos4[i] = make_float4(o[0], o[1], o[2], p.w);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real fma_free_add(Real a, Real b);
+template <> __device__ __forceinline__ double fma_free_add<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float fma_free_add<float>(float a, float b) { return __fadd_rn(a, b); }
+template <typename Real>
+__device__ __forceinline__ Real fma_free_mul(Real a, Real b);
+template <> __device__ __forceinline__ double fma_free_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float fma_free_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ begin
+
+struct DualConsts {
+    double eta, rho0, h_min, u_ref, cfl_ad, cfl_ac, c;
+};
+
+// Eq. 9-11 with h = h_min from max |v| of the fluid (the diagnostics of the
+// previous step or of sph_build_cells; the sort does not change v).
+__global__ void k_dual_begin(DualConsts D, const double* __restrict__ diag, double* __restrict__ du)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double vmax = diag[DG_VMAX];
+    const double nu = D.eta / D.rho0;
+    const double vad = fmax(vmax, fmax(nu / D.h_min, D.u_ref));
+    const double Dt = D.cfl_ad * D.h_min / vad;
+    double dt = D.cfl_ac * D.h_min / (vmax + D.c);
+    const double rem = Dt - 0.0;
+    const int last = !(dt < rem);      // also ends the step on a non-finite size
+    if (last) dt = rem;
+    du[DU_DT_AD] = Dt;
+    du[DU_VAD] = vad;
+    du[DU_T] = 0.0;
+    du[DU_DT] = dt;
+    du[DU_HDT_PREV] = 0.0;
+    du[DU_LAST] = last;
+    du[DU_DONE] = 0.0;
+    du[DU_K] = 0.0;
+    du[DU_FIRST] = 1.0;
+}
+
+// ----------------------------------------------------------------- advect
+
+template <typename Real, int DIM, typename Acc, bool UNIFORM>
+__global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_advect(DualK<Real> A, Grid G, Consts<Real> K)
+{
+    __shared__ float4 tab[kCodes];
+    fill_shift_table<Real>(G, tab);
+    const int n = A.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (A.S.kind[i]) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            A.anu[(size_t)d * n + i] = Real(0);
+            A.R[(size_t)d * n + i] = Real(0);
+            A.S.dr[(size_t)d * n + i] = Real(0);
+        }
+        A.chi[i] = Real(0);
+        return;
+    }
+    int cnt = A.nbc[i];
+    if (cnt > A.cap) {
+        atomicOr(A.err, ERRB_OVERFLOW);
+        cnt = A.cap;
+    }
+    const auto me = A.vr[i];
+    const Real vi[3] = {me.x, me.y, me.z};
+    const Real rho_i = K.rho0 + me.w;
+    Real hi, mi;
+    h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+    Acc acc_nu[DIM], acc_R[DIM];
+    auto pair = [&](int j, const Real* rv, Real r2) {
+        if (!(r2 > Real(0))) return;
+        const Real r = sqrt(r2);
+        const Real inv_r = Real(1) / r;
+        Real hj, mj;
+        h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
+        const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
+        const auto oj = A.vr[j];
+        const bool wall = isinf(oj.w);
+        const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+        const Real vj[3] = {oj.x, oj.y, oj.z};
+        const Real cv = K.two_eta * mj / (rho_i * rho_j) * dw * inv_r;
+        const Real Vj = mj / rho_j;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            acc_nu[d].add(cv * (vi[d] - vj[d]));
+            acc_R[d].add(Vj * (dw * rv[d] * inv_r));
+        }
+    };
+    for_list<Real, DIM>(A, G, tab, i, cnt, pair);
+    Real R[3] = {0, 0, 0}, R2 = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        R[d] = acc_R[d].value();
+        R2 += R[d] * R[d];
+        A.anu[(size_t)d * n + i] = acc_nu[d].value();
+        A.R[(size_t)d * n + i] = R[d];
+    }
+    const Real htv = K.tv_h_particle ? hi : K.h_min;
+    const Real chi = tv_limiter(K, htv * htv * R2);
+    A.chi[i] = chi;
+    // Eq. 12 with p0 = 7 rho0 |v|_ad^2 (Eq. 13): dr = -(Dt^2 p0 / rho_i) R_i
+    const double Dt = A.du[DU_DT_AD], vad = A.du[DU_VAD];
+    const double p0 = 7.0 * (double)K.rho0 * vad * vad;
+    const double bg = -(Dt * Dt * p0 / (double)rho_i);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const Real dr = K.tv_mode == SPH_TV_BACKGROUND ? (Real)(bg * (double)R[d])
+                                                       : K.tv_xi * chi * htv * htv * R[d];
+        A.S.dr[(size_t)d * n + i] = dr;
+    }
+}
+
+// ------------------------------------------------------------- substeps
+
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(256) k_dual_first_half(DualK<Real> A, Grid G)
+{
+    if (dual_done(A.du)) return;
+    const int n = A.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || A.S.kind[i]) return;
+    const double dt = A.du[DU_DT];
+    const double hdt = 0.5 * dt;
+    const bool first = A.du[DU_FIRST] != 0.0;
+    auto me = A.vr[i];
+    Real w = me.w;
+    const Real dr = A.S.drho[i];
+    if (!first) w = fma_free_add<Real>(w, fma_free_mul<Real>((Real)A.du[DU_HDT_PREV], dr));
+    w = fma_free_add<Real>(w, fma_free_mul<Real>((Real)hdt, dr));
+    me.w = w;
+    A.vr[i] = me;
+    double xs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const size_t o = (size_t)d * n + i;
+        double x = A.S.x[o];
+        if (first) x = __dadd_rn(x, (double)A.S.dr[o]);
+        x = __dadd_rn(x, __dmul_rn(hdt, (double)A.S.v[o]));
+        A.S.x[o] = x;
+        xs[d] = x;
+    }
+    if (sizeof(Real) == 4) store_offsets<DIM>(A.pos4, A.cell_of, G, i, xs);
+}
+
+template <typename Real, int DIM, typename Acc, bool UNIFORM>
+__global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_pressure(DualK<Real> A, Grid G, Consts<Real> K)
+{
+    __shared__ float4 tab[kCodes];
+    if (dual_done(A.du)) return;
+    fill_shift_table<Real>(G, tab);
+    const int n = A.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || A.S.kind[i]) return;
+    const int cnt = min(A.nbc[i], A.cap);
+    const double dt = A.du[DU_DT];
+    const auto me = A.vr[i];
+    const Real vi[3] = {me.x, me.y, me.z};
+    const Real rho_i = K.rho0 + me.w;
+    const Real p_i = K.c2 * me.w;
+    Real hi, mi;
+    h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+    Acc acc[DIM];
+    auto pair = [&](int j, const Real* rv, Real r2) {
+        if (!(r2 > Real(0))) return;
+        const Real r = sqrt(r2);
+        const Real inv_r = Real(1) / r;
+        Real hj, mj;
+        h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
+        const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
+        const auto oj = A.vr[j];
+        const bool wall = isinf(oj.w);
+        const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+        const Real p_j = wall ? p_i : K.c2 * oj.w;
+        Real ul = 0, ur = 0;
+        const Real vj[3] = {oj.x, oj.y, oj.z};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const Real e = -rv[d] * inv_r;
+            ul += vi[d] * e;
+            ur += vj[d] * e;
+        }
+        const Real du = ul - ur;
+        Real beta = K.beta_slope * (du * K.inv_c);
+        beta = beta > Real(0) ? beta : Real(0);
+        beta = beta < Real(1) ? beta : Real(1);
+        const Real rhobar = Real(0.5) * (rho_i + rho_j);
+        const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
+        const Real cp = Real(-2) * mj * pstar / (rho_i * rho_j);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) acc[d].add(cp * (dw * rv[d] * inv_r));
+    };
+    for_list<Real, DIM>(A, G, tab, i, cnt, pair);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const size_t o = (size_t)d * n + i;
+        const Real a = (acc[d].value() + A.anu[o]) + K.g[d];
+        A.S.a[o] = a;
+        A.S.v[o] = fma_free_add<Real>(A.S.v[o], fma_free_mul<Real>((Real)dt, a));
+    }
+}
+
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(256) k_dual_drift(DualK<Real> A, Grid G)
+{
+    if (dual_done(A.du)) return;
+    const int n = A.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || A.S.kind[i]) return;
+    const double hdt = 0.5 * A.du[DU_DT];
+    double xs[3] = {0.0, 0.0, 0.0};
+    Real v[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const size_t o = (size_t)d * n + i;
+        v[d] = A.S.v[o];
+        xs[d] = __dadd_rn(A.S.x[o], __dmul_rn(hdt, (double)v[d]));
+        A.S.x[o] = xs[d];
+    }
+    const Real w = A.vr[i].w;
+    A.vr[i] = V4<Real>::make(v[0], v[1], v[2], w);
+    if (sizeof(Real) == 4) store_offsets<DIM>(A.pos4, A.cell_of, G, i, xs);
+}
+
+template <typename Real, int DIM, typename Acc, bool UNIFORM>
+__global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continuity(DualK<Real> A, Grid G, Consts<Real> K)
+{
+    __shared__ float4 tab[kCodes];
+    if (dual_done(A.du)) return;
+    fill_shift_table<Real>(G, tab);
+    const int n = A.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part[kNPart];
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) part[k] = 0.0;
+    if (i < n && A.S.kind[i] == 0) {
+        const int cnt = min(A.nbc[i], A.cap);
+        const auto me = A.vr[i];
+        const Real vi[3] = {me.x, me.y, me.z};
+        const Real rho_i = K.rho0 + me.w;
+        const Real p_i = K.c2 * me.w;
+        Real hi, mi;
+        h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+        Acc s;
+        auto pair = [&](int j, const Real* rv, Real r2) {
+            if (!(r2 > Real(0))) return;
+            const Real r = sqrt(r2);
+            const Real inv_r = Real(1) / r;
+            Real hj, mj;
+            h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
+            const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
+            const auto oj = A.vr[j];
+            const bool wall = isinf(oj.w);
+            const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+            const Real p_j = wall ? p_i : K.c2 * oj.w;
+            Real ul = 0, ur = 0;
+            const Real vj[3] = {oj.x, oj.y, oj.z};
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const Real e = -rv[d] * inv_r;
+                ul += vi[d] * e;
+                ur += vj[d] * e;
+            }
+            const Real rhobar = Real(0.5) * (rho_i + rho_j);
+            const Real ustar = Real(0.5) * (ul + ur) + Real(0.5) * (p_i - p_j) / (rhobar * K.c);
+            s.add(mj / rho_j * (ustar - ul) * dw);
+        };
+        for_list<Real, DIM>(A, G, tab, i, cnt, pair);
+        A.S.drho[i] = Real(2) * rho_i * s.value();
+        // diagnostics of the current state (used after the last substep)
+        const double Dt = A.du[DU_DT_AD];
+        const double m_i = A.S.m[i];
+        double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const size_t o = (size_t)d * n + i;
+            const double v = (double)A.S.v[o];
+            const double dr = (double)A.S.dr[o];
+            part[1 + d] = m_i * v;
+            v2 += v * v;
+            dr2 += dr * dr;
+            const double vt = v + dr / Dt;
+            vt2 += vt * vt;
+        }
+        part[0] = m_i;
+        part[4] = 0.5 * m_i * v2;
+        part[5] = A.chi[i] > Real(0) ? 1.0 : 0.0;
+        part[6] = sqrt(v2);
+        part[7] = sqrt(vt2);
+        part[8] = sqrt(dr2);
+    } else if (i < n) {
+        A.S.drho[i] = Real(0);
+    }
+    block_partials(part, A.partials + (size_t)blockIdx.x * kNPart);
+}
+
+// Reduce the substep's partials (in a fixed order); advance t; pick the next
+// substep size, or finish the advection step and write the diagnostics.
+__global__ void __launch_bounds__(256) k_dual_finalize(int nblocks, const double* __restrict__ partials, DualConsts D,
+                                                       double* __restrict__ du, double* __restrict__ diag,
+                                                       double* __restrict__ dt_ptr)
+{
+    if (dual_done(du)) return;
+    double acc[kNPart];
+#pragma unroll
+    for (int k = 0; k < kNPart; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double* p = partials + (size_t)b * kNPart;
+#pragma unroll
+        for (int k = 0; k < kNPart; ++k) acc[k] = (k >= 6 && k <= 8) ? fmax(acc[k], p[k]) : acc[k] + p[k];
+    }
+    __shared__ double out[kNPart];
+    block_partials(acc, out);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double vmax = out[6];
+    const double dt = du[DU_DT];
+    const double t = du[DU_T] + dt;
+    const double k = du[DU_K] + 1.0;
+    du[DU_T] = t;
+    du[DU_K] = k;
+    du[DU_HDT_PREV] = 0.5 * dt;
+    du[DU_FIRST] = 0.0;
+    if (du[DU_LAST] != 0.0) {
+        const double Dt = du[DU_DT_AD];
+        const double nu = D.eta / D.rho0;
+        const double vad = fmax(vmax, fmax(nu / D.h_min, D.u_ref));
+        diag[DG_MASS] = out[0];
+        diag[DG_MOM + 0] = out[1];
+        diag[DG_MOM + 1] = out[2];
+        diag[DG_MOM + 2] = out[3];
+        diag[DG_KE] = out[4];
+        diag[DG_NCHI] = out[5];
+        diag[DG_VMAX] = vmax;
+        diag[DG_VTMAX] = out[7];
+        diag[DG_DRMAX] = out[8];
+        diag[DG_DT] = Dt;
+        diag[DG_DTNEXT] = D.cfl_ad * D.h_min / vad;
+        diag[DG_STEPS] = diag[DG_STEPS] + 1.0;
+        diag[DG_SUBSTEPS] = k;
+        *dt_ptr = Dt;
+        du[DU_DONE] = 1.0;
+        return;
+    }
+    double dtn = D.cfl_ac * D.h_min / (vmax + D.c);
+    const double rem = du[DU_DT_AD] - t;
+    const int last = !(dtn < rem);     // also ends the step on a non-finite size
+    if (last) dtn = rem;
+    du[DU_DT] = dtn;
+    du[DU_LAST] = last;
+}
+
+// Second half of the last substep's density update: rho += dt/2 drho.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_dual_complete(DualK<Real> A)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n || A.S.kind[i]) return;
+    auto me = A.vr[i];
+    me.w = fma_free_add<Real>(me.w, fma_free_mul<Real>((Real)A.du[DU_HDT_PREV], A.S.drho[i]));
+    A.vr[i] = me;
+}
+
+// ============================================================ launchers
+
+namespace {
+
+inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+template <typename Real>
+DualK<Real> dual_k(const DualArgs& a)
+{
+    DualK<Real> k;
+    k.n = a.n;
+    k.cap = a.cap;
+    k.S = *(const StateSet<Real>*)a.S;
+    k.vr = (typename V4<Real>::T*)a.vr;
+    k.pos4 = a.pos4;
+    k.cell_of = a.cell_of;
+    k.mf = a.mf;
+    k.nbl = a.nbl;
+    k.nbc = a.nbc;
+    k.anu = (Real*)a.anu;
+    k.R = (Real*)a.R;
+    k.chi = (Real*)a.chi;
+    k.du = a.du;
+    k.partials = a.partials;
+    k.err = a.err;
+    return k;
+}
+
+DualConsts dual_consts(const sph_params& P)
+{
+    return DualConsts{P.eta, P.rho0, P.h_min, P.u_ref, P.cfl_ad, P.cfl_ac, P.c0};
+}
+
+// Pair kernel dispatch: precision, dimension, compensated sums (FP32) and
+// uniform resolution (FP32) are template arguments.
+template <template <typename, int, typename, bool> class Kern> struct Dispatch;
+
+#define SPH_DUAL_PAIR_KERNEL(name)                                                                         \
+    template <typename Real, int DIM, typename Acc, bool U>                                                \
+    struct name##_t {                                                                                      \
+        static void run(const DualK<Real>& A, const Grid& G, const Consts<Real>& K, cudaStream_t st)     \
+        {                                                                                                  \
+            name<Real, DIM, Acc, U><<<nblk(A.n, tpb<Real>()), tpb<Real>(), 0, st>>>(A, G, K);              \
+        }                                                                                                  \
+    };
+SPH_DUAL_PAIR_KERNEL(k_dual_advect)
+SPH_DUAL_PAIR_KERNEL(k_dual_pressure)
+SPH_DUAL_PAIR_KERNEL(k_dual_continuity)
+#undef SPH_DUAL_PAIR_KERNEL
+
+template <template <typename, int, typename, bool> class KT>
+void run_pair(int prec, int dim, const DualArgs& a, const Grid& G, const void* Kp, cudaStream_t st)
+{
+    if (prec == 64) {
+        const auto A = dual_k<double>(a);
+        const auto& K = *(const Consts<double>*)Kp;
+        if (dim == 2) KT<double, 2, PlainD, false>::run(A, G, K, st);
+        else KT<double, 3, PlainD, false>::run(A, G, K, st);
+        return;
+    }
+    const auto A = dual_k<float>(a);
+    const auto& K = *(const Consts<float>*)Kp;
+    const bool u = K.uniform_h != 0, ks = K.kahan != 0;
+    if (dim == 2) {
+        if (ks) u ? KT<float, 2, KSum, true>::run(A, G, K, st) : KT<float, 2, KSum, false>::run(A, G, K, st);
+        else u ? KT<float, 2, PlainF, true>::run(A, G, K, st) : KT<float, 2, PlainF, false>::run(A, G, K, st);
+    } else {
+        if (ks) u ? KT<float, 3, KSum, true>::run(A, G, K, st) : KT<float, 3, KSum, false>::run(A, G, K, st);
+        else u ? KT<float, 3, PlainF, true>::run(A, G, K, st) : KT<float, 3, PlainF, false>::run(A, G, K, st);
+    }
+}
+
+template <typename Real>
+void run_elem(int dim, const DualArgs& a, const Grid& G, int which, cudaStream_t st)
+{
+    const auto A = dual_k<Real>(a);
+    const int T = 256, B = nblk(A.n, T);
+    if (which == 0) {
+        if (dim == 2) k_dual_first_half<Real, 2><<<B, T, 0, st>>>(A, G);
+        else k_dual_first_half<Real, 3><<<B, T, 0, st>>>(A, G);
+    } else if (which == 1) {
+        if (dim == 2) k_dual_drift<Real, 2><<<B, T, 0, st>>>(A, G);
+        else k_dual_drift<Real, 3><<<B, T, 0, st>>>(A, G);
+    } else {
+        k_dual_complete<Real><<<B, T, 0, st>>>(A);
+    }
+}
+
+}  // namespace
+
+int dual_pair_blocks(int prec, int n) { return prec == 64 ? nblk(n, kTPB64) : nblk(n, kTPB32); }
+
+cudaError_t launch_dual_begin(const sph_params& P, const double* diag, double* du, cudaStream_t st)
+{
+    k_dual_begin<<<1, 32, 0, st>>>(dual_consts(P), diag, du);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual_advect(int prec, int dim, const DualArgs& a, const Grid& G, const void* K, cudaStream_t st)
+{
+    run_pair<k_dual_advect_t>(prec, dim, a, G, K, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual_substep(int prec, int dim, const DualArgs& a, const Grid& G, const void* K,
+                                const sph_params& P, double* diag, double* dt_ptr, cudaStream_t st,
+                                int64_t* launches)
+{
+    if (prec == 64) run_elem<double>(dim, a, G, 0, st);
+    else run_elem<float>(dim, a, G, 0, st);
+    run_pair<k_dual_pressure_t>(prec, dim, a, G, K, st);
+    if (prec == 64) run_elem<double>(dim, a, G, 1, st);
+    else run_elem<float>(dim, a, G, 1, st);
+    run_pair<k_dual_continuity_t>(prec, dim, a, G, K, st);
+    k_dual_finalize<<<1, 256, 0, st>>>(dual_pair_blocks(prec, a.n), a.partials, dual_consts(P), a.du, diag, dt_ptr);
+    *launches += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual_complete(int prec, const DualArgs& a, cudaStream_t st)
+{
+    if (prec == 64) run_elem<double>(2, a, Grid{}, 2, st);
+    else run_elem<float>(2, a, Grid{}, 2, st);
+    return cudaGetLastError();
+}
+
+}  // namespace sphtv

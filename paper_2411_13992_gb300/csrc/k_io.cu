@@ -99,6 +99,16 @@ __global__ void k_scalar_out(int n, const Real* __restrict__ src, const int32_t*
     if (k < n) dst[id[k]] = (double)src[k];
 }
 
+// Caller-order scalar in (walls get 0); used before the first sort, when the
+// internal order is the caller's.
+template <typename Real>
+__global__ void k_scalar_in(int n, const double* __restrict__ src, const int8_t* __restrict__ kind,
+                            Real* __restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = kind[i] ? Real(0) : (Real)src[i];
+}
+
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 cudaError_t launch_vec_in(int prec, int dim, int n, const double* src3, void* dst, cudaStream_t st)
@@ -168,6 +178,13 @@ cudaError_t launch_check_input(int n, const double* h, const double* m, double h
                                cudaStream_t st)
 {
     k_check_input<<<nblk(n, 256), 256, 0, st>>>(n, h, m, h_min, h_max, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_in(int prec, int n, const double* src, const int8_t* kind, void* dst, cudaStream_t st)
+{
+    if (prec == 64) k_scalar_in<double><<<nblk(n, 256), 256, 0, st>>>(n, src, kind, (double*)dst);
+    else k_scalar_in<float><<<nblk(n, 256), 256, 0, st>>>(n, src, kind, (float*)dst);
     return cudaGetLastError();
 }
 

@@ -30,9 +30,13 @@ namespace sphtv {
 
 // ============================================================== FP64 form
 
+// With nbl non-null it also writes the particle's neighbour list (j != i,
+// 0 < r < 2 h_ij), transposed (entry k at nbl[k * n + i] = j << kCodeBits),
+// and the count (which may exceed cap) for the dual-criteria integrator.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, const int32_t* __restrict__ start,
-                                                     Grid G, Consts<double> K, double4_32a* __restrict__ vr)
+                                                     Grid G, Consts<double> K, double4_32a* __restrict__ vr,
+                                                     uint32_t* __restrict__ nbl, int32_t* __restrict__ nbc, int cap)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -44,11 +48,13 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     }
     if (S.kind[i]) {
         vr[i] = make_double4_32a(vi[0], vi[1], vi[2], __longlong_as_double(0x7ff0000000000000ll));
+        if (nbc) nbc[i] = 0;
         return;
     }
     const double hi = S.h[i];
     int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
     double sigma = 0.0;
+    int cnt = 0;
     const int SR = G.R, zr = DIM == 3 ? SR : 0;
     for (int dz = -zr; dz <= zr; ++dz) {
         int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
@@ -69,11 +75,18 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
                     }
                     double r = sqrt(r2);
                     double hij = pair_h(K, hi, S.h[j]);
-                    if (r < 2.0 * hij) sigma += wendland_W<DIM, double>(r, 1.0 / hij);
+                    if (r < 2.0 * hij) {
+                        sigma += wendland_W<DIM, double>(r, 1.0 / hij);
+                        if (nbl && j != i && r2 > 0.0) {
+                            if (cnt < cap) nbl[(size_t)cnt * n + i] = (uint32_t)j << kCodeBits;
+                            ++cnt;
+                        }
+                    }
                 }
             }
         }
     }
+    if (nbc) nbc[i] = cnt;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     vr[i] = make_double4_32a(vi[0], vi[1], vi[2], __dsub_rn(rho, K.rho0));
 }
@@ -296,8 +309,9 @@ cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* sta
     if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st);
     auto s = *(StateSet<double>*)S;
     auto k = *(const Consts<double>*)K;
-    if (dim == 2) k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
-    else k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr);
+    const int cap = nbl_capacity(dim);
+    if (dim == 2) k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, nbl, nbc, cap);
+    else k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, nbl, nbc, cap);
     return cudaGetLastError();
 }
 

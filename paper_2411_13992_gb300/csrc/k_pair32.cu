@@ -34,12 +34,6 @@ __device__ __forceinline__ float support2(const Consts<float>& K, float hi, floa
     return 4.f * h * h;
 }
 
-// List entries: (j << kCodeBits) | stencil code of j's cell.
-constexpr int kSide = 2 * kStencilR + 1;                 // stencil cells per axis
-constexpr int kCodes = kSide * kSide * kSide;            // 125 for R = 2
-constexpr int kCodeBits = 7;
-static_assert(kCodes <= (1 << kCodeBits), "stencil code does not fit");
-
 // Visit every candidate of the (2R+1)^D cells around cell_i (cell-relative
 // FP32 positions plus the exact shift of the neighbour cell): f(j, code, pj,
 // r2, rx, ry, rz) with code = stencil index of the neighbour cell.  Lanes of
@@ -236,16 +230,6 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
             }
         }
     }
-}
-
-// Shift of a neighbour cell from its stencil code (as for_candidates forms it).
-__device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* sh)
-{
-    const int dx = (int)(code % kSide) - kStencilR, dy = (int)((code / kSide) % kSide) - kStencilR,
-              dz = (int)(code / (kSide * kSide)) - kStencilR;
-    sh[0] = -(float)dx * G.edgef[0];
-    sh[1] = -(float)dy * G.edgef[1];
-    sh[2] = -(float)dz * G.edgef[2];
 }
 
 // ---------------------------------------------------------------- density

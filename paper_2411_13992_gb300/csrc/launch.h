@@ -50,6 +50,8 @@ cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* 
 
 // k_pair.cu (FP64 form; FP32 calls are forwarded to k_pair32.cu)
 int pair_blocks(int prec, int n);
+// FP64 form: nbl / nbc may be null (no list); with them the density pass
+// writes the neighbour list the dual-criteria integrator uses.
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
                            cudaStream_t st);
@@ -87,6 +89,33 @@ cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, 
 cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,
                                cudaStream_t st);
 cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st);
+cudaError_t launch_scalar_in(int prec, int n, const double* src, const int8_t* kind, void* dst, cudaStream_t st);
+
+// k_dual.cu (dual-criteria time stepping).  Device pointers of one context;
+// S points at the StateSet<Real> of the current (sorted) copy.
+struct DualArgs {
+    int n, cap;
+    const void* S;
+    void* vr;
+    float4* pos4;
+    const int32_t* cell_of;
+    const float* mf;
+    const uint32_t* nbl;
+    const int32_t* nbc;
+    void* anu;
+    void* R;
+    void* chi;
+    double* du;
+    double* partials;
+    uint32_t* err;
+};
+int dual_pair_blocks(int prec, int n);
+cudaError_t launch_dual_begin(const sph_params& P, const double* diag, double* du, cudaStream_t st);
+cudaError_t launch_dual_advect(int prec, int dim, const DualArgs& a, const Grid& G, const void* K, cudaStream_t st);
+cudaError_t launch_dual_substep(int prec, int dim, const DualArgs& a, const Grid& G, const void* K,
+                                const sph_params& P, double* diag, double* dt_ptr, cudaStream_t st,
+                                int64_t* launches);
+cudaError_t launch_dual_complete(int prec, const DualArgs& a, cudaStream_t st);
 
 // k_adjoint.cu
 int adj_pair_blocks(int n);

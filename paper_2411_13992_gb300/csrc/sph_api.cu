@@ -4,6 +4,7 @@
 // the caller's workspace; nothing here allocates device memory.  All work is
 // enqueued on the context's stream; the only host waits are in sph_sync,
 // sph_get_diag and sph_get_state (host destinations).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,8 +52,11 @@ struct sph_ctx {
     float4* pos4;
     int32_t* cell;
     float* mf;
-    uint32_t* nbl;      // FP32 form: force neighbour lists [cap][n], transposed
-    int32_t* nbc;       // FP32 form: neighbour count per particle
+    uint32_t* nbl;      // FP32 form or dual integrator: neighbour lists [cap][n], transposed
+    int32_t* nbc;       // neighbour count per particle (with nbl)
+    void* anu;          // dual integrator: viscous acceleration held for an advection step
+    double* du;         // dual integrator: device state (DU_*)
+    int dual_est;       // dual integrator: substeps to launch before the first check
     void* R;
     void* chi;
     double* partials;
@@ -105,6 +109,8 @@ sph_status check_params(const sph_params* p, int64_t n)
         return SPH_ERR_ARG;
     if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
     if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
+    if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
+    if (p->integrator == SPH_INT_DUAL && (p->fixed_dt != 0.0 || p->adjoint_steps != 0)) return SPH_ERR_ARG;
     for (int d = 0; d < p->dim; ++d) {
         if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
         double nc = std::floor(p->L[d] * kStencilR / (2.0 * p->h_max));
@@ -190,18 +196,20 @@ size_t carve(sph_ctx* c, char* base)
     const int D = c->dim;
     const size_t rs = c->prec == 64 ? 8 : 4;
     const size_t nc1 = (size_t)c->G.ncell + 1;
+    const bool dual = c->P.integrator == SPH_INT_DUAL;
     for (int s = 0; s < 2; ++s) {
         double* x = W.take<double>(D * n);
         char* v = W.take<char>(D * n * rs);
         char* a = W.take<char>(D * n * rs);
         char* dr = W.take<char>(D * n * rs);
+        char* drho = dual ? W.take<char>(n * rs) : nullptr;
         double* h = W.take<double>(n);
         double* m = W.take<double>(n);
         double* s0 = W.take<double>(n);
         int32_t* id = W.take<int32_t>(n);
         int8_t* kind = W.take<int8_t>(n);
-        c->set[s].d = StateSet<double>{x, (double*)v, (double*)a, (double*)dr, h, m, s0, id, kind};
-        c->set[s].f = StateSet<float>{x, (float*)v, (float*)a, (float*)dr, h, m, s0, id, kind};
+        c->set[s].d = StateSet<double>{x, (double*)v, (double*)a, (double*)dr, (double*)drho, h, m, s0, id, kind};
+        c->set[s].f = StateSet<float>{x, (float*)v, (float*)a, (float*)dr, (float*)drho, h, m, s0, id, kind};
     }
     c->key = W.take<int32_t>(n);
     c->perm_tmp = W.take<int32_t>(n);
@@ -214,11 +222,15 @@ size_t carve(sph_ctx* c, char* base)
     c->pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
     c->cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
     c->mf = c->prec == 32 ? W.take<float>(n) : nullptr;
-    c->nbl = c->prec == 32 ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
-    c->nbc = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
+    const bool lists = c->prec == 32 || dual;
+    c->nbl = lists ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
+    c->nbc = lists ? W.take<int32_t>(n) : nullptr;
+    c->anu = dual ? W.take<char>(D * n * rs) : nullptr;
+    c->du = dual ? W.take<double>(DU_COUNT) : nullptr;
     c->R = W.take<char>(D * n * rs);
     c->chi = W.take<char>(n * rs);
-    c->partials = W.take<double>((size_t)pair_blocks(c->prec, (int)n) * kNPart);
+    const int pblocks = std::max(pair_blocks(c->prec, (int)n), dual_pair_blocks(c->prec, (int)n));
+    c->partials = W.take<double>((size_t)pblocks * kNPart);
     c->rows = W.take<double>((size_t)reduce_rows_blocks() * kNPart);
     c->diag = W.take<double>(DG_COUNT);
     c->dt = W.take<double>(1);
@@ -284,6 +296,12 @@ inline cudaError_t prof_mark(sph_ctx* c, int cls, int end)
 
 #define SPH_MARK(cls, end) SPH_CU(prof_mark(c, cls, end))
 
+#define SPH_TRY(call)                    \
+    do {                                 \
+        sph_status s_ = (call);          \
+        if (s_ != SPH_OK) return s_;     \
+    } while (0)
+
 // Kick-drift (optional), cell keys, counting sort, permute.
 sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
 {
@@ -339,6 +357,75 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->rows, c->P, c->diag, c->dt, count_step, c->st));
     SPH_MARK(SPH_K_FINALIZE, 1);
     c->launches += 3;
+    return SPH_OK;
+}
+
+DualArgs dual_args(sph_ctx* c)
+{
+    DualArgs a;
+    a.n = (int)c->n;
+    a.cap = nbl_capacity(c->dim);
+    a.S = cur_set(c);
+    a.vr = c->vr;
+    a.pos4 = c->pos4;
+    a.cell_of = c->cell;
+    a.mf = c->mf;
+    a.nbl = c->nbl;
+    a.nbc = c->nbc;
+    a.anu = c->anu;
+    a.R = c->R;
+    a.chi = c->chi;
+    a.du = c->du;
+    a.partials = c->partials;
+    a.err = c->err;
+    return a;
+}
+
+// One advection step of the dual-criteria integrator (Sec. 2.4): sort (wrap
+// only), density pass with the frozen neighbour list, Dt_ad, the viscous
+// force and the correction; then acoustic substeps until the device marks the
+// advection step done.  Substeps are launched in batches; a batch may run
+// past the end (the extra launches return at once) and the host reads the
+// device state once per batch.
+sph_status run_dual_step(sph_ctx* c)
+{
+    const int n = (int)c->n;
+    SPH_TRY(run_sort(c, 2, 0));
+    SPH_MARK(SPH_K_DENSITY, 0);
+    SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
+                          c->nbl, c->nbc, c->st));
+    SPH_MARK(SPH_K_DENSITY, 1);
+    SPH_MARK(SPH_K_ADVECT, 0);
+    SPH_CU(launch_dual_begin(c->P, c->diag, c->du, c->st));
+    const DualArgs a = dual_args(c);
+    SPH_CU(launch_dual_advect(c->prec, c->dim, a, c->G, consts(c), c->st));
+    SPH_MARK(SPH_K_ADVECT, 1);
+    c->launches += 3;
+    double hb[DU_COUNT];
+    if (c->dual_est <= 0) {
+        SPH_CU(cudaMemcpyAsync(hb, c->du, sizeof(hb), cudaMemcpyDeviceToHost, c->st));
+        SPH_CU(cudaStreamSynchronize(c->st));
+        const double ratio = hb[DU_DT_AD] / hb[DU_DT];
+        c->dual_est = std::isfinite(ratio) && ratio < 1.0e6 ? (int)std::ceil(ratio) + 1 : 2;
+    }
+    SPH_MARK(SPH_K_ACOUSTIC, 0);
+    int batch = c->dual_est, taken = 0;
+    constexpr int kMaxSubsteps = 1 << 20;
+    for (;;) {
+        for (int b = 0; b < batch; ++b)
+            SPH_CU(launch_dual_substep(c->prec, c->dim, a, c->G, consts(c), c->P, c->diag, c->dt, c->st,
+                                       &c->launches));
+        taken += batch;
+        SPH_CU(cudaMemcpyAsync(hb, c->du, sizeof(hb), cudaMemcpyDeviceToHost, c->st));
+        SPH_CU(cudaStreamSynchronize(c->st));
+        if (hb[DU_DONE] != 0.0) break;
+        if (taken >= kMaxSubsteps) return SPH_ERR_NAN;   // the step sizes are not finite or vanish
+        batch = 2;
+    }
+    SPH_CU(launch_dual_complete(c->prec, a, c->st));
+    ++c->launches;
+    SPH_MARK(SPH_K_ACOUSTIC, 1);
+    c->dual_est = (int)hb[DU_K] + 1;
     return SPH_OK;
 }
 
@@ -443,12 +530,6 @@ sph_status cot_out(sph_ctx* c, const double* src, double* dst)
     ++c->launches;
     return SPH_OK;
 }
-
-#define SPH_TRY(call)                    \
-    do {                                 \
-        sph_status s_ = (call);          \
-        if (s_ != SPH_OK) return s_;     \
-    } while (0)
 
 }  // namespace
 
@@ -583,6 +664,7 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     }
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
+    if (Sd.drho) SPH_CU(cudaMemsetAsync(Sd.drho, 0, n * rs, c->st));
     c->launches += 5;
     if (c->P.adjoint_steps > 0) {
         SPH_CU(cudaMemcpyAsync(c->orig_h, Sd.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -600,6 +682,15 @@ sph_status sph_build_cells(sph_ctx* c)
 {
     if (!c) return SPH_ERR_ARG;
     if (!c->have_state) return SPH_ERR_STATE;
+    if (c->P.integrator == SPH_INT_DUAL) {
+        // density and diagnostics of the loaded state; the first advection
+        // step takes Dt_ad and dt_ac from its max |v|
+        SPH_TRY(run_sort(c, 2, 0));
+        SPH_TRY(run_forces(c, 0, 0, 0));
+        c->dual_est = 0;
+        c->have_cells = 1;
+        return SPH_OK;
+    }
     sph_status s = run_sort(c, 0, c->ad_given);
     if (s != SPH_OK) return s;
     s = run_forces(c, 0, !c->ad_given, 0);
@@ -613,12 +704,40 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps)
     if (!c || nsteps < 0) return SPH_ERR_ARG;
     if (!c->have_cells) return SPH_ERR_STATE;
     for (int32_t k = 0; k < nsteps; ++k) {
-        sph_status s = run_sort(c, 1, 0);
-        if (s != SPH_OK) return s;
-        s = run_forces(c, 1, 1, 1);
-        if (s != SPH_OK) return s;
+        if (c->P.integrator == SPH_INT_DUAL) {
+            SPH_TRY(run_dual_step(c));
+        } else {
+            SPH_TRY(run_sort(c, 1, 0));
+            SPH_TRY(run_forces(c, 1, 1, 1));
+        }
         if (c->prof_ev) ++c->prof_step;
     }
+    return SPH_OK;
+}
+
+sph_status sph_set_density_rate(sph_ctx* c, const double* drho)
+{
+    if (!c || !drho || c->P.integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
+    if (!c->have_state || c->have_cells) return SPH_ERR_STATE;
+    const size_t n = (size_t)c->n;
+    void* dst = c->prec == 64 ? (void*)c->set[c->cur].d.drho : (void*)c->set[c->cur].f.drho;
+    SPH_CU(cudaMemcpyAsync(c->stage, drho, n * sizeof(double), cudaMemcpyDefault, c->st));
+    SPH_CU(launch_scalar_in(c->prec, (int)n, c->stage, c->set[c->cur].d.kind, dst, c->st));
+    ++c->launches;
+    return SPH_OK;
+}
+
+sph_status sph_get_density_rate(sph_ctx* c, double* drho)
+{
+    if (!c || !drho || c->P.integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
+    if (!c->have_state) return SPH_ERR_STATE;
+    const int n = (int)c->n;
+    const StateSet<double>& Sd = c->set[c->cur].d;
+    const void* src = c->prec == 64 ? (void*)Sd.drho : (void*)c->set[c->cur].f.drho;
+    SPH_CU(launch_scalar_out(c->prec, n, src, Sd.id, c->stage, c->st));
+    SPH_CU(cudaMemcpyAsync(drho, c->stage, (size_t)n * sizeof(double), cudaMemcpyDefault, c->st));
+    ++c->launches;
+    if (is_host_ptr(drho)) SPH_CU(cudaStreamSynchronize(c->st));
     return SPH_OK;
 }
 
@@ -687,6 +806,7 @@ sph_status sph_get_diag(sph_ctx* c, sph_diag* out)
     out->dt = buf[DG_DT];
     out->dt_next = buf[DG_DTNEXT];
     out->steps = buf[DG_STEPS];
+    out->substeps = buf[DG_SUBSTEPS];
     return SPH_OK;
 }
 
@@ -769,7 +889,7 @@ sph_status sph_profile_end(sph_ctx* c, double* ms, int64_t* count)
 const char* sph_kernel_class_name(int32_t k)
 {
     static const char* names[SPH_K_NCLASS] = {"kick_drift_key", "scan", "scatter_order", "permute", "density",
-                                              "forces", "finalize"};
+                                              "forces", "finalize", "advect", "acoustic"};
     return (k >= 0 && k < SPH_K_NCLASS) ? names[k] : "?";
 }
 

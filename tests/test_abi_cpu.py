@@ -81,6 +81,7 @@ def test_workspace_query_and_argument_checks(lib):
         dict(dim=4), dict(precision=16), dict(rho0=0.0), dict(c0=-1.0), dict(eta=-1.0), dict(h_min=0.0),
         dict(h_max=0.5 * c["h_min"]), dict(tv_mode=4), dict(fixed_dt=-1.0), dict(adjoint_steps=-1),
         dict(h_max=0.3),          # fewer than 5 cells along a periodic axis
+        dict(integrator=2), dict(integrator=1, fixed_dt=1e-3), dict(integrator=1, adjoint_steps=4),
     ]
     for kw in bad:
         q = sph.params_from_case(c, 64)
@@ -123,3 +124,16 @@ def test_fma_peak_rejects_bad_arguments_before_launching(lib):
     assert lib.sph_fma_peak(32, 1, 1, None, None, ctypes.byref(flops)) == 1
     assert lib.sph_fma_peak(32, 1, 1, sink, None, None) == 1
     assert flops.value == -1.0
+
+
+def test_dual_integrator_workspace_and_host_checks(lib):
+    c = cases.tgv2d(20)
+    for prec in (64, 32):
+        kdk = sph.sph_query_workspace(sph.params_from_case(c, prec), c["n"])
+        dual = sph.sph_query_workspace(sph.params_from_case(c, prec, integrator=sph.INT_DUAL), c["n"])
+        assert dual > kdk                  # density rate, held viscous force, neighbour lists
+    buf = (ctypes.c_double * 4)()
+    assert lib.sph_set_density_rate(None, buf) == 1
+    assert lib.sph_get_density_rate(None, buf) == 1
+    assert sph.sph_kernel_class_name(7) == "advect" and sph.sph_kernel_class_name(8) == "acoustic"
+    assert sph.sph_kernel_class_name(9) == "?"
