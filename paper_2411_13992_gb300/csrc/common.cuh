@@ -209,6 +209,22 @@ __device__ __forceinline__ double min_image(const Grid& G, double xi, double xj,
     return dx;
 }
 
+// 1/x and sqrt(x) to ~1 ulp on the special-function unit (x > 0, normal):
+// the FP32 form needs neither the IEEE-rounded division nor square root.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Neighbour-list entries: (j << kCodeBits) | stencil code of j's cell, the
 // code being (dx + R) + S (dy + R) + S^2 (dz + R) with S = 2R + 1.
 constexpr int kSide = 2 * kStencilR + 1;                 // stencil cells per axis

@@ -88,8 +88,10 @@ __device__ __forceinline__ void fill_shift_table(const Grid& G, float4* tab)
     __syncthreads();
 }
 
-// Visit the frozen neighbour list of particle i: f(j, rv, r2) with rv the
-// pair vector x_i - x_j at the current positions.
+// Visit the frozen neighbour list of particle i: f(j, rv, r2, wj, oj) with
+// rv the pair vector x_i - x_j at the current positions, wj = pos4[j].w (FP32
+// form: m or h) and oj = vr[j].  The FP32 walk keeps the list entry two ahead
+// and the neighbour's data one ahead in flight.
 template <typename Real, int DIM, typename F>
 __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, const float4* tab, int i, int cnt, F& f)
 {
@@ -107,16 +109,27 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
                 rv[d] = min_image(G, xi[d], A.S.x[(size_t)d * n + j], d);
                 r2 += rv[d] * rv[d];
             }
-            f(j, rv, r2);
+            f(j, rv, r2, 0.f, A.vr[j]);
         }
     } else {
         const float4 pi = A.pos4[i];
         const float oi[3] = {pi.x, pi.y, pi.z};
+        const uint32_t* lp = A.nbl + i;
+        uint32_t e_cur = cnt > 0 ? lp[0] : 0u;
+        uint32_t e_nxt = cnt > 1 ? lp[(size_t)n] : 0u;
+        float4 pj_n = A.pos4[e_cur >> kCodeBits];
+        float4 oj_n = A.vr[e_cur >> kCodeBits];
         for (int k = 0; k < cnt; ++k) {
-            const uint32_t e = A.nbl[(size_t)k * n + i];
-            const int j = (int)(e >> kCodeBits);
-            const float4 pj = A.pos4[j];
-            const float4 sh = tab[e & ((1u << kCodeBits) - 1u)];
+            const uint32_t ec = e_cur;
+            const float4 pj = pj_n;
+            const float4 oj = oj_n;
+            if (k + 1 < cnt) {
+                pj_n = A.pos4[e_nxt >> kCodeBits];
+                oj_n = A.vr[e_nxt >> kCodeBits];
+            }
+            e_cur = e_nxt;
+            e_nxt = (k + 2 < cnt) ? lp[(size_t)(k + 2) * n] : 0u;
+            const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
             float rv[3] = {0.f, 0.f, 0.f};
             rv[0] = (oi[0] - pj.x) + sh.x;
             rv[1] = (oi[1] - pj.y) + sh.y;
@@ -125,32 +138,63 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
                 rv[2] = (oi[2] - pj.z) + sh.z;
                 r2 += rv[2] * rv[2];
             }
-            f(j, rv, r2);
+            f((int)(ec >> kCodeBits), rv, r2, pj.w, oj);
         }
     }
 }
 
-// Smoothing length of particle j and its mass, from the layout of the form.
+// Smoothing length and mass of particle j (wj = pos4[j].w in the FP32 form).
 template <typename Real, bool UNIFORM>
-__device__ __forceinline__ void h_m_of(const DualK<Real>& A, const Consts<Real>& K, int j, Real& h, Real& m)
+__device__ __forceinline__ void h_m_of(const DualK<Real>& A, const Consts<Real>& K, int j, float wj, Real& h, Real& m)
 {
     if constexpr (std::is_same<Real, double>::value) {
         h = A.S.h[j];
         m = A.S.m[j];
     } else {
-        const float w = A.pos4[j].w;
-        h = UNIFORM ? K.h_u : w;
-        m = UNIFORM ? w : A.mf[j];
+        h = UNIFORM ? K.h_u : wj;
+        m = UNIFORM ? wj : A.mf[j];
     }
 }
 
-// W'(r, h), zero at and beyond the support 2h (the list is frozen while the
-// particles move).
-template <typename Real, int DIM>
-__device__ __forceinline__ Real dw_clamped(Real r, Real h)
+// 1/r, r and W'(r, h_ij)/r of a pair, zero at and beyond the support 2 h_ij
+// (the list is frozen while the particles move).  FP64: IEEE operations;
+// FP32: rsqrt and W'/r = coef t^3, t = max(1 - r/(2h), 0).
+template <typename Real>
+struct PairGeo {
+    Real inv_r, r, dwr;
+};
+
+template <typename Real, int DIM, bool UNIFORM>
+__device__ __forceinline__ PairGeo<Real> pair_geo(const Consts<Real>& K, Real r2, Real hi, Real hj)
 {
-    if (!(r < Real(2) * h)) return Real(0);
-    return wendland_dW<DIM, Real>(r, Real(1) / h);
+    PairGeo<Real> g;
+    if constexpr (std::is_same<Real, double>::value) {
+        g.r = sqrt(r2);
+        g.inv_r = 1.0 / g.r;
+        const double h = pair_h(K, hi, hj);
+        g.dwr = g.r < 2.0 * h ? wendland_dW<DIM, double>(g.r, 1.0 / h) * g.inv_r : 0.0;
+    } else {
+        g.inv_r = rsqrtf(r2);
+        g.r = r2 * g.inv_r;
+        float inv_h, coef;
+        if (UNIFORM) {
+            inv_h = K.inv_h_u;
+            coef = K.dwr_coef_u;
+        } else {
+            inv_h = __frcp_rn(pair_h(K, hi, hj));
+            coef = -5.f * kernel_norm<DIM, float>() * pow_dim<DIM, float>(inv_h) * inv_h * inv_h;
+        }
+        const float t = fmaxf(fmaf(-0.5f * inv_h, g.r, 1.f), 0.f);
+        g.dwr = coef * (t * t * t);
+    }
+    return g;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real recip(Real x)
+{
+    if constexpr (std::is_same<Real, double>::value) return 1.0 / x;
+    else return rcp_approx(x);
 }
 
 // FP32 x offsets of particle i from its home cell's origin (as the permute forms them).
@@ -236,26 +280,28 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_advect(D
     const auto me = A.vr[i];
     const Real vi[3] = {me.x, me.y, me.z};
     const Real rho_i = K.rho0 + me.w;
+    const Real inv_rho_i = recip(rho_i);
     Real hi, mi;
-    h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+    {
+        float wi = 0.f;
+        if constexpr (!std::is_same<Real, double>::value) wi = A.pos4[i].w;
+        h_m_of<Real, UNIFORM>(A, K, i, wi, hi, mi);
+    }
     Acc acc_nu[DIM], acc_R[DIM];
-    auto pair = [&](int j, const Real* rv, Real r2) {
+    auto pair = [&](int j, const Real* rv, Real r2, float wj, const typename V4<Real>::T& oj) {
         if (!(r2 > Real(0))) return;
-        const Real r = sqrt(r2);
-        const Real inv_r = Real(1) / r;
         Real hj, mj;
-        h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
-        const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
-        const auto oj = A.vr[j];
+        h_m_of<Real, UNIFORM>(A, K, j, wj, hj, mj);
+        const PairGeo<Real> g = pair_geo<Real, DIM, UNIFORM>(K, r2, hi, hj);
         const bool wall = isinf(oj.w);
-        const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+        const Real inv_rho_j = wall ? inv_rho_i : recip(K.rho0 + oj.w);
+        const Real cv = K.two_eta * mj * inv_rho_i * inv_rho_j * g.dwr;   // Eq. 7
+        const Real vw = mj * inv_rho_j * g.dwr;                           // V_j W'/r
         const Real vj[3] = {oj.x, oj.y, oj.z};
-        const Real cv = K.two_eta * mj / (rho_i * rho_j) * dw * inv_r;
-        const Real Vj = mj / rho_j;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             acc_nu[d].add(cv * (vi[d] - vj[d]));
-            acc_R[d].add(Vj * (dw * rv[d] * inv_r));
+            acc_R[d].add(vw * rv[d]);
         }
     };
     for_list<Real, DIM>(A, G, tab, i, cnt, pair);
@@ -328,38 +374,35 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_pressure
     const auto me = A.vr[i];
     const Real vi[3] = {me.x, me.y, me.z};
     const Real rho_i = K.rho0 + me.w;
+    const Real inv_rho_i = recip(rho_i);
     const Real p_i = K.c2 * me.w;
     Real hi, mi;
-    h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+    {
+        float wi = 0.f;
+        if constexpr (!std::is_same<Real, double>::value) wi = A.pos4[i].w;
+        h_m_of<Real, UNIFORM>(A, K, i, wi, hi, mi);
+    }
     Acc acc[DIM];
-    auto pair = [&](int j, const Real* rv, Real r2) {
+    auto pair = [&](int j, const Real* rv, Real r2, float wj, const typename V4<Real>::T& oj) {
         if (!(r2 > Real(0))) return;
-        const Real r = sqrt(r2);
-        const Real inv_r = Real(1) / r;
         Real hj, mj;
-        h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
-        const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
-        const auto oj = A.vr[j];
+        h_m_of<Real, UNIFORM>(A, K, j, wj, hj, mj);
+        const PairGeo<Real> g = pair_geo<Real, DIM, UNIFORM>(K, r2, hi, hj);
         const bool wall = isinf(oj.w);
         const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+        const Real inv_rho_j = wall ? inv_rho_i : recip(rho_j);
         const Real p_j = wall ? p_i : K.c2 * oj.w;
-        Real ul = 0, ur = 0;
-        const Real vj[3] = {oj.x, oj.y, oj.z};
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const Real e = -rv[d] * inv_r;
-            ul += vi[d] * e;
-            ur += vj[d] * e;
-        }
-        const Real du = ul - ur;
-        Real beta = K.beta_slope * (du * K.inv_c);
+        Real dvr = (vi[0] - oj.x) * rv[0] + (vi[1] - oj.y) * rv[1];
+        if (DIM == 3) dvr += (vi[2] - oj.z) * rv[2];
+        const Real du = -dvr * g.inv_r;                        // U_l - U_r, e_ij from i to j
+        Real beta = K.beta_slope * (du * K.inv_c);             // Eq. 6
         beta = beta > Real(0) ? beta : Real(0);
         beta = beta < Real(1) ? beta : Real(1);
         const Real rhobar = Real(0.5) * (rho_i + rho_j);
-        const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
-        const Real cp = Real(-2) * mj * pstar / (rho_i * rho_j);
+        const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;   // Eq. 5
+        const Real cpw = Real(-2) * mj * inv_rho_i * inv_rho_j * pstar * g.dwr;           // Eq. 3
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) acc[d].add(cp * (dw * rv[d] * inv_r));
+        for (int d = 0; d < DIM; ++d) acc[d].add(cpw * rv[d]);
     };
     for_list<Real, DIM>(A, G, tab, i, cnt, pair);
 #pragma unroll
@@ -409,32 +452,31 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
         const auto me = A.vr[i];
         const Real vi[3] = {me.x, me.y, me.z};
         const Real rho_i = K.rho0 + me.w;
+        const Real inv_rho_i = recip(rho_i);
         const Real p_i = K.c2 * me.w;
         Real hi, mi;
-        h_m_of<Real, UNIFORM>(A, K, i, hi, mi);
+        {
+            float wi = 0.f;
+            if constexpr (!std::is_same<Real, double>::value) wi = A.pos4[i].w;
+            h_m_of<Real, UNIFORM>(A, K, i, wi, hi, mi);
+        }
         Acc s;
-        auto pair = [&](int j, const Real* rv, Real r2) {
+        auto pair = [&](int j, const Real* rv, Real r2, float wj, const typename V4<Real>::T& oj) {
             if (!(r2 > Real(0))) return;
-            const Real r = sqrt(r2);
-            const Real inv_r = Real(1) / r;
             Real hj, mj;
-            h_m_of<Real, UNIFORM>(A, K, j, hj, mj);
-            const Real dw = dw_clamped<Real, DIM>(r, pair_h(K, hi, hj));
-            const auto oj = A.vr[j];
+            h_m_of<Real, UNIFORM>(A, K, j, wj, hj, mj);
+            const PairGeo<Real> g = pair_geo<Real, DIM, UNIFORM>(K, r2, hi, hj);
             const bool wall = isinf(oj.w);
             const Real rho_j = wall ? rho_i : K.rho0 + oj.w;
+            const Real inv_rho_j = wall ? inv_rho_i : recip(rho_j);
             const Real p_j = wall ? p_i : K.c2 * oj.w;
-            Real ul = 0, ur = 0;
-            const Real vj[3] = {oj.x, oj.y, oj.z};
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const Real e = -rv[d] * inv_r;
-                ul += vi[d] * e;
-                ur += vj[d] * e;
-            }
+            Real dvr = (vi[0] - oj.x) * rv[0] + (vi[1] - oj.y) * rv[1];
+            if (DIM == 3) dvr += (vi[2] - oj.z) * rv[2];
+            // U* - U_l = (U_r - U_l)/2 + (p_l - p_r) / (2 rho_bar c)   (Eq. 5, first row)
             const Real rhobar = Real(0.5) * (rho_i + rho_j);
-            const Real ustar = Real(0.5) * (ul + ur) + Real(0.5) * (p_i - p_j) / (rhobar * K.c);
-            s.add(mj / rho_j * (ustar - ul) * dw);
+            const Real dus = Real(0.5) * dvr * g.inv_r + Real(0.5) * (p_i - p_j) * recip(rhobar) * K.inv_c;
+            // V_j (U* - U_l) dW/dr, dW/dr = (W'/r) r
+            s.add(mj * inv_rho_j * dus * (g.dwr * g.r));
         };
         for_list<Real, DIM>(A, G, tab, i, cnt, pair);
         A.S.drho[i] = Real(2) * rho_i * s.value();
@@ -646,8 +688,11 @@ cudaError_t launch_dual_substep(int prec, int dim, const DualArgs& a, const Grid
     if (prec == 64) run_elem<double>(dim, a, G, 1, st);
     else run_elem<float>(dim, a, G, 1, st);
     run_pair<k_dual_continuity_t>(prec, dim, a, G, K, st);
-    k_dual_finalize<<<1, 256, 0, st>>>(dual_pair_blocks(prec, a.n), a.partials, dual_consts(P), a.du, diag, dt_ptr);
-    *launches += 5;
+    const int nb = dual_pair_blocks(prec, a.n);
+    const int rows = launch_reduce_rows(nb, a.partials, a.rows, st);
+    k_dual_finalize<<<1, 256, 0, st>>>(rows ? rows : nb, rows ? a.rows : a.partials, dual_consts(P), a.du, diag,
+                                       dt_ptr);
+    *launches += rows ? 6 : 5;
     return cudaGetLastError();
 }
 

@@ -352,6 +352,15 @@ cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials
 
 int reduce_rows_blocks() { return 256; }
 
+int launch_reduce_rows(int nblocks, const double* partials, double* rows, cudaStream_t st)
+{
+    const int G = reduce_rows_blocks();
+    if (nblocks <= 4 * G) return 0;
+    const int chunk = (nblocks + G - 1) / G;
+    k_reduce_rows<<<G, 256, 0, st>>>(nblocks, chunk, partials, rows);
+    return G;
+}
+
 cudaError_t launch_finalize(int nblocks, const double* partials, double* rows, const sph_params& P, double* diag,
                             double* dt, int count_step, cudaStream_t st)
 {

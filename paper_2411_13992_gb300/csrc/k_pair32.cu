@@ -80,22 +80,6 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
     }
 }
 
-// 1/x and sqrt(x) to ~1 ulp on the special-function unit (x > 0, normal):
-// the FP32 form needs neither the IEEE-rounded division nor square root.
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // One neighbour's contribution to a_i and R_i in the FP32 form, given
 // rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force
 // (Eq. 3, 5-7, 14) arranged for FP32 throughput -- W' only enters through

@@ -72,6 +72,9 @@ cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const
                             void* Rout, void* chi, double* partials, cudaStream_t st);
 cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st);
 int reduce_rows_blocks();
+// First level of the fixed-order reduction of per-block partials: returns the
+// number of rows written (0: too few partials, reduce them directly).
+int launch_reduce_rows(int nblocks, const double* partials, double* rows, cudaStream_t st);
 cudaError_t launch_finalize(int nblocks, const double* partials, double* rows, const sph_params& P, double* diag,
                             double* dt, int count_step, cudaStream_t st);
 
@@ -107,6 +110,7 @@ struct DualArgs {
     void* chi;
     double* du;
     double* partials;
+    double* rows;
     uint32_t* err;
 };
 int dual_pair_blocks(int prec, int n);

@@ -377,6 +377,7 @@ DualArgs dual_args(sph_ctx* c)
     a.chi = c->chi;
     a.du = c->du;
     a.partials = c->partials;
+    a.rows = c->rows;
     a.err = c->err;
     return a;
 }
