@@ -45,14 +45,11 @@ __global__ void k_init_ids(int n, int32_t* id)
 }
 
 template <int DIM>
-__global__ void k_sigma0(int n, const double* __restrict__ h, const double* __restrict__ m, double rho0,
-                         double* __restrict__ s0)
+__device__ double sigma0_of(double h, double m, double rho0)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double vol = m[i] / rho0;
+    const double vol = m / rho0;
     const double dp = DIM == 2 ? sqrt(vol) : cbrt(vol);
-    const double ratio = h[i] / dp;            // smoothing length in units of dp
+    const double ratio = h / dp;               // smoothing length in units of dp
     const double reach2 = 4.0 * ratio * ratio;
     const int K = (int)ceil(2.0 * ratio);
     const double inv = 1.0 / ratio;
@@ -68,7 +65,27 @@ __global__ void k_sigma0(int n, const double* __restrict__ h, const double* __re
                 double mult = (kx ? 2.0 : 1.0) * (ky ? 2.0 : 1.0) * (kz ? 2.0 : 1.0);
                 s += mult * wendland_W<DIM, double>(sqrt(r2), inv);
             }
-    s0[i] = s / (DIM == 2 ? dp * dp : dp * dp * dp);
+    return s / (DIM == 2 ? dp * dp : dp * dp * dp);
+}
+
+// The reference sum depends on (h, m) only: particle 0's value is computed
+// once (k_sigma0_first) and copied to every particle with the same h and m;
+// the others compute their own (the lattice sum is FP64 work, and FP64 runs
+// at 1/74 of the FP32 rate).
+template <int DIM>
+__global__ void k_sigma0_first(const double* __restrict__ h, const double* __restrict__ m, double rho0,
+                               double* __restrict__ s0)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) s0[0] = sigma0_of<DIM>(h[0], m[0], rho0);
+}
+
+template <int DIM>
+__global__ void k_sigma0(int n, const double* __restrict__ h, const double* __restrict__ m, double rho0,
+                         double* __restrict__ s0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 1 || i >= n) return;
+    s0[i] = (h[i] == h[0] && m[i] == m[0]) ? s0[0] : sigma0_of<DIM>(h[i], m[i], rho0);
 }
 
 template <typename V4>
@@ -161,8 +178,13 @@ cudaError_t launch_init_ids(int n, int32_t* id, cudaStream_t st)
 cudaError_t launch_sigma0(int dim, int n, const double* h, const double* m, double rho0, double* s0,
                           cudaStream_t st)
 {
-    if (dim == 2) k_sigma0<2><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
-    else k_sigma0<3><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
+    if (dim == 2) {
+        k_sigma0_first<2><<<1, 32, 0, st>>>(h, m, rho0, s0);
+        k_sigma0<2><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
+    } else {
+        k_sigma0_first<3><<<1, 32, 0, st>>>(h, m, rho0, s0);
+        k_sigma0<3><<<nblk(n, 128), 128, 0, st>>>(n, h, m, rho0, s0);
+    }
     return cudaGetLastError();
 }
 

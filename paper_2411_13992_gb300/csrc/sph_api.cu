@@ -661,7 +661,7 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     if (sigma0) SPH_CU(cudaMemcpyAsync(Sd.s0, sigma0, n * sizeof(double), cudaMemcpyDefault, c->st));
     else {
         SPH_CU(launch_sigma0(c->dim, (int)n, Sd.h, Sd.m, c->P.rho0, Sd.s0, c->st));
-        ++c->launches;
+        c->launches += 2;
     }
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
