@@ -291,7 +291,7 @@ static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst,
     const int T = 256;
     auto s = *(StateSet<Real>*)src;
     auto d = *(StateSet<Real>*)dst;
-    constexpr bool F32 = sizeof(Real) == 4;
+    constexpr bool F32 = true;   // both forms: the density passes walk the FP32 cell-relative positions
     if (dim == 2) {
         if (carry_ad) k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
         else k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);

@@ -25,18 +25,26 @@
 #include "common.cuh"
 #include "launch.h"
 #include "pair_physics.cuh"
+#include "pair_walk.cuh"
 
 namespace sphtv {
 
 // ============================================================== FP64 form
 
-// With nbl non-null it also writes the particle's neighbour list (j != i,
+// Candidates come from the clipped FP32 row walk over the cell-relative
+// positions (pos4); a loose FP32 test drops the far ones and the exact FP64
+// test (minimum image, sqrt(r2) < 2 h_ij) decides the rest.  The walk visits
+// candidates in the order of the cell scan (cells by dz, dy, dx, then index),
+// so sigma is summed in the same order as a plain scan would.  With nbl
+// non-null it also writes the particle's neighbour list (j != i,
 // 0 < r < 2 h_ij), transposed (entry k at nbl[k * n + i] = j << kCodeBits),
-// and the count (which may exceed cap) for the dual-criteria integrator.
+// and the count (which may exceed cap); the FP64 force pass walks it.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, const int32_t* __restrict__ start,
                                                      Grid G, Consts<double> K, double4_32a* __restrict__ vr,
-                                                     uint32_t* __restrict__ nbl, int32_t* __restrict__ nbc, int cap)
+                                                     const float4* __restrict__ pos4,
+                                                     const int32_t* __restrict__ cell_of, uint32_t* __restrict__ nbl,
+                                                     int32_t* __restrict__ nbc, int cap)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -52,40 +60,32 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
         return;
     }
     const double hi = S.h[i];
-    int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
+    const float4 pi = pos4[i];
+    const float oi[3] = {pi.x, pi.y, pi.z};
+    // reach of the walk: the largest support radius 2 h_ij of i (h_j <= h_max)
+    const float reach = (float)(2.0 * pair_h(K, hi, K.h_u));
     double sigma = 0.0;
     int cnt = 0;
-    const int SR = G.R, zr = DIM == 3 ? SR : 0;
-    for (int dz = -zr; dz <= zr; ++dz) {
-        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
-        if (cz < 0) continue;
-        for (int dy = -SR; dy <= SR; ++dy) {
-            int cy = cell_step(G, c[1], dy, 1);
-            if (cy < 0) continue;
-            for (int dx = -SR; dx <= SR; ++dx) {
-                int cx = cell_step(G, c[0], dx, 0);
-                if (cx < 0) continue;
-                int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                for (int j = start[cell]; j < start[cell + 1]; ++j) {
-                    double r2 = 0.0;
+    auto visit = [&](int j, uint32_t code, const float4&, float r2f, float, float, float) {
+        const double hij = pair_h(K, hi, S.h[j]);
+        const float lim = (float)(2.0 * hij);
+        if (!(r2f <= lim * lim * 1.0001f)) return;       // FP32 prefilter, 1e-4 margin
+        double r2 = 0.0;
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        double t = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
-                        r2 += t * t;
-                    }
-                    double r = sqrt(r2);
-                    double hij = pair_h(K, hi, S.h[j]);
-                    if (r < 2.0 * hij) {
-                        sigma += wendland_W<DIM, double>(r, 1.0 / hij);
-                        if (nbl && j != i && r2 > 0.0) {
-                            if (cnt < cap) nbl[(size_t)cnt * n + i] = (uint32_t)j << kCodeBits;
-                            ++cnt;
-                        }
-                    }
-                }
+        for (int d = 0; d < DIM; ++d) {
+            double t = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+            r2 += t * t;
+        }
+        const double r = sqrt(r2);
+        if (r < 2.0 * hij) {
+            sigma += wendland_W<DIM, double>(r, 1.0 / hij);
+            if (nbl && j != i && r2 > 0.0) {
+                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
+                ++cnt;
             }
         }
-    }
+    };
+    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, pos4, visit);
     if (nbc) nbc[i] = cnt;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     vr[i] = make_double4_32a(vi[0], vi[1], vi[2], __dsub_rn(rho, K.rho0));
@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, const int32_t* __restrict__ start,
                                                     Grid G, Consts<double> K, const double4_32a* __restrict__ vr,
-                                                    const double* __restrict__ dt_ptr, int kick_on, int write_ad,
-                                                    double* __restrict__ Rout, double* __restrict__ chi_out,
-                                                    double* __restrict__ partials)
+                                                    const uint32_t* __restrict__ nbl, const int32_t* __restrict__ nbc,
+                                                    int cap, const double* __restrict__ dt_ptr, int kick_on,
+                                                    int write_ad, double* __restrict__ Rout,
+                                                    double* __restrict__ chi_out, double* __restrict__ partials)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part[kNPart];
@@ -114,34 +115,44 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double rho_i = K.rho0 + me.w;
         const double p_i = K.c2 * me.w;
         PlainD acc_a[DIM], acc_R[DIM];
-        int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
-        const int SR = G.R, zr = DIM == 3 ? SR : 0;
-        for (int dz = -zr; dz <= zr; ++dz) {
-            int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
-            if (cz < 0) continue;
-            for (int dy = -SR; dy <= SR; ++dy) {
-                int cy = cell_step(G, c[1], dy, 1);
-                if (cy < 0) continue;
-                for (int dx = -SR; dx <= SR; ++dx) {
-                    int cx = cell_step(G, c[0], dx, 0);
-                    if (cx < 0) continue;
-                    int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                    for (int j = start[cell]; j < start[cell + 1]; ++j) {
-                        if (j == i) continue;
-                        double rv[3] = {0, 0, 0};
-                        double r2 = 0.0;
+        // one neighbour j (j != i); returns without work outside the support
+        auto visit = [&](int j) {
+            double rv[3] = {0, 0, 0};
+            double r2 = 0.0;
 #pragma unroll
-                        for (int d = 0; d < DIM; ++d) {
-                            rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
-                            r2 += rv[d] * rv[d];
-                        }
-                        double r = sqrt(r2);
-                        double hij = pair_h(K, hi, S.h[j]);
-                        if (!(r < 2.0 * hij) || r == 0.0) continue;
-                        double dw = wendland_dW<DIM, double>(r, 1.0 / hij);
-                        double4_32a oj = vr[j];
-                        double vj[3] = {oj.x, oj.y, oj.z};
-                        pair_force<double, DIM, PlainD>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, S.m[j], acc_a, acc_R);
+            for (int d = 0; d < DIM; ++d) {
+                rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+                r2 += rv[d] * rv[d];
+            }
+            const double hij = pair_h(K, hi, S.h[j]);
+            if (r2 > 4.0 * hij * hij * (1.0 + 1e-12)) return;   // far: no FP64 square root
+            double r = sqrt(r2);
+            if (!(r < 2.0 * hij) || r == 0.0) return;
+            double dw = wendland_dW<DIM, double>(r, 1.0 / hij);
+            double4_32a oj = vr[j];
+            double vj[3] = {oj.x, oj.y, oj.z};
+            pair_force<double, DIM, PlainD>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, S.m[j], acc_a, acc_R);
+        };
+        const int cnt = nbl ? nbc[i] : cap + 1;
+        if (cnt <= cap) {
+            // the density pass's list: the same neighbours in the same order as
+            // the cell scan below, so the sums are bit-identical
+            for (int k = 0; k < cnt; ++k) visit((int)(nbl[(size_t)k * n + i] >> kCodeBits));
+        } else {
+            int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
+            const int SR = G.R, zr = DIM == 3 ? SR : 0;
+            for (int dz = -zr; dz <= zr; ++dz) {
+                int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+                if (cz < 0) continue;
+                for (int dy = -SR; dy <= SR; ++dy) {
+                    int cy = cell_step(G, c[1], dy, 1);
+                    if (cy < 0) continue;
+                    for (int dx = -SR; dx <= SR; ++dx) {
+                        int cx = cell_step(G, c[0], dx, 0);
+                        if (cx < 0) continue;
+                        int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
+                        for (int j = start[cell]; j < start[cell + 1]; ++j)
+                            if (j != i) visit(j);
                     }
                 }
             }
@@ -159,8 +170,8 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double chi = tv_limiter(K, htv2 * R2);
         const double m_i = S.m[i];
         // Eq. 12 (background pressure p0 = rho0 c^2): dr = dt^2/2 a_bg = -(dt^2 p0 / rho_i) R_i
-        const double bg = -(dt * dt * (K.rho0 * K.c2) / rho_i);
         const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
+        const double bg = bgmode ? -(dt * dt * (K.rho0 * K.c2) / rho_i) : 0.0;
         double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -310,8 +321,10 @@ cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* sta
     auto s = *(StateSet<double>*)S;
     auto k = *(const Consts<double>*)K;
     const int cap = nbl_capacity(dim);
-    if (dim == 2) k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, nbl, nbc, cap);
-    else k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, nbl, nbc, cap);
+    if (dim == 2)
+        k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap);
+    else
+        k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap);
     return cudaGetLastError();
 }
 
@@ -326,12 +339,13 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
                                chi, partials, st);
     auto s = *(StateSet<double>*)S;
     auto k = *(const Consts<double>*)K;
+    const int cap = nbl_capacity(dim);
     if (dim == 2)
-        k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
-                                                  (double*)Rout, (double*)chi, partials);
+        k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials);
     else
-        k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, dt, kick_on, write_ad,
-                                                  (double*)Rout, (double*)chi, partials);
+        k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,154 @@
+// pair_walk.cuh -- candidate walks over the 5^D cells around a particle's
+// cell, on cell-relative FP32 positions (pos4 = {offset from the cell
+// origin, m or h}).  Both visit the candidates in the same order: cells by
+// (dz, dy, dx) ascending (periodic images in the order of the stencil step),
+// particles by index within a cell.  Used by the FP32 pair passes and, as a
+// prefilter in front of the exact FP64 test, by the FP64 density pass.
+#pragma once
+
+#include "common.cuh"
+
+namespace sphtv {
+
+// Visit every candidate of the (2R+1)^D cells around cell_i (cell-relative
+// FP32 positions plus the exact shift of the neighbour cell): f(j, code, pj,
+// r2, rx, ry, rz) with code = stencil index of the neighbour cell.  Lanes of
+// a warp whose particles share a cell read the same j at the same time, so
+// the loads of pos4 are warp broadcasts.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_candidates(const float* oi, int cell_i, const Grid& G,
+                                               const int32_t* __restrict__ start,
+                                               const float4* __restrict__ pos4, F& f)
+{
+    int c[3];
+    cell_decode(G, cell_i, c);
+    constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
+    for (int dz = -zr; dz <= zr; ++dz) {
+        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+        if (cz < 0) continue;
+        const float shz = -(float)dz * G.edgef[2];
+        for (int dy = -R; dy <= R; ++dy) {
+            int cy = cell_step(G, c[1], dy, 1);
+            if (cy < 0) continue;
+            const float shy = -(float)dy * G.edgef[1];
+            const int row = G.nc[0] * (cy + G.nc[1] * cz);
+            for (int dx = -R; dx <= R; ++dx) {
+                int cx = cell_step(G, c[0], dx, 0);
+                if (cx < 0) continue;
+                const float shx = -(float)dx * G.edgef[0];
+                const uint32_t code = (uint32_t)((dx + R) + kSide * (dy + R) + kSide * kSide * (dz + R));
+                const int cell = cx + row;
+                const int j1 = start[cell + 1];
+                for (int j = start[cell]; j < j1; ++j) {
+                    const float4 pj = pos4[j];
+                    const float rx = (oi[0] - pj.x) + shx;
+                    const float ry = (oi[1] - pj.y) + shy;
+                    float r2 = rx * rx + ry * ry;
+                    float rz = 0.f;
+                    if (DIM == 3) {
+                        rz = (oi[2] - pj.z) + shz;
+                        r2 += rz * rz;
+                    }
+                    f(j, code, pj, r2, rx, ry, rz);
+                }
+            }
+        }
+    }
+}
+
+// The same visit as for_candidates, walked row by row and clipped to the
+// particle's reach.  For each (dy, dz) row the cells are contiguous in the
+// cell order, so the row is one run of particles (two runs across a periodic
+// x boundary) whose x shift and stencil code advance at each cell boundary.
+// A row whose nearest y-z distance to particle i exceeds the reach (the
+// largest support radius of any pair of i) is skipped, and the x extent of a
+// row is cut to the cells within the remaining half-chord; every margin is
+// 1e-3 of a cell edge, far above FP32 rounding, so every candidate that the
+// full stencil would accept is still visited, in the same order.  About 2/3
+// of the 5^3 cells remain in 3-D.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_candidates_rows(const float* oi, float reach, int cell_i, const Grid& G,
+                                                    const int32_t* __restrict__ start,
+                                                    const float4* __restrict__ pos4, F& f)
+{
+    int c[3];
+    cell_decode(G, cell_i, c);
+    constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
+    const int ncx = G.nc[0];
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    const float inv_ex = 1.f / ex;
+    const float reach2 = reach * reach;
+    for (int dz = -zr; dz <= zr; ++dz) {
+        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+        if (cz < 0) continue;
+        float rz = 0.f;
+        if (DIM == 3) {
+            rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
+            rz = fmaxf(rz - 1e-3f * ez, 0.f);
+        }
+        const float wz2 = reach2 - rz * rz;
+        if (wz2 <= 0.f) continue;
+        const float shz = -(float)dz * ez;
+        for (int dy = -R; dy <= R; ++dy) {
+            int cy = cell_step(G, c[1], dy, 1);
+            if (cy < 0) continue;
+            float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
+            ry = fmaxf(ry - 1e-3f * ey, 0.f);
+            const float w2 = wz2 - ry * ry;
+            if (w2 <= 0.f) continue;
+            const float w = sqrtf(w2) + 1e-3f * ex;
+            const int dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
+            const int dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
+            if (dxlo > dxhi) continue;
+            // runs along x: first cell (x index), number of cells, x step of the
+            // first cell; a periodic window (at most 5 <= ncx cells) wraps once at most
+            int rc0[2], rn[2], rdx[2], nrun;
+            const int a = c[0] + dxlo, b = c[0] + dxhi;
+            if (!G.periodic[0]) {
+                const int a0 = max(a, 0), b0 = min(b, ncx - 1);
+                rc0[0] = a0; rn[0] = b0 - a0 + 1; rdx[0] = a0 - c[0]; nrun = rn[0] > 0 ? 1 : 0;
+            } else if (a >= 0 && b < ncx) {
+                rc0[0] = a; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+            } else if (a < 0) {
+                rc0[0] = ncx + a; rn[0] = min(-a, b - a + 1); rdx[0] = dxlo;
+                rc0[1] = 0; rn[1] = b + 1; rdx[1] = -c[0]; nrun = b >= 0 ? 2 : 1;
+            } else if (a >= ncx) {
+                rc0[0] = a - ncx; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+            } else {
+                rc0[0] = a; rn[0] = ncx - a; rdx[0] = dxlo;
+                rc0[1] = 0; rn[1] = b - ncx + 1; rdx[1] = ncx - c[0]; nrun = 2;
+            }
+            const float shy = -(float)dy * ey;
+            const int row = ncx * (cy + G.nc[1] * cz);
+            const uint32_t code_row = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
+            for (int r = 0; r < nrun; ++r) {
+                int cell = row + rc0[r];
+                int dx = rdx[r];
+                int j = start[cell];
+                const int jend = start[cell + rn[r]];
+                int nb = start[cell + 1];
+                float shx = -(float)dx * ex;
+                for (; j < jend; ++j) {
+                    while (j >= nb) {          // next non-empty cell of the run
+                        ++cell;
+                        ++dx;
+                        nb = start[cell + 1];
+                        shx = -(float)dx * ex;
+                    }
+                    const float4 pj = pos4[j];
+                    const float rx = (oi[0] - pj.x) + shx;
+                    const float ry_ = (oi[1] - pj.y) + shy;
+                    float r2 = rx * rx + ry_ * ry_;
+                    float rz_ = 0.f;
+                    if (DIM == 3) {
+                        rz_ = (oi[2] - pj.z) + shz;
+                        r2 += rz_ * rz_;
+                    }
+                    f(j, code_row + (uint32_t)dx, pj, r2, rx, ry_, rz_);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace sphtv

@@ -57,6 +57,7 @@ struct sph_ctx {
     void* anu;          // dual integrator: viscous acceleration held for an advection step
     double* du;         // dual integrator: device state (DU_*)
     int dual_est;       // dual integrator: substeps to launch before the first check
+    int density_only;   // sph_density_noalloc's view: no neighbour lists
     void* R;
     void* chi;
     double* partials;
@@ -200,8 +201,9 @@ size_t carve(sph_ctx* c, char* base)
     for (int s = 0; s < 2; ++s) {
         double* x = W.take<double>(D * n);
         char* v = W.take<char>(D * n * rs);
-        char* a = W.take<char>(D * n * rs);
-        char* dr = W.take<char>(D * n * rs);
+        // (the density-only view of sph_density_noalloc needs no a, dr, R, chi)
+        char* a = c->density_only ? nullptr : W.take<char>(D * n * rs);
+        char* dr = c->density_only ? nullptr : W.take<char>(D * n * rs);
         char* drho = dual ? W.take<char>(n * rs) : nullptr;
         double* h = W.take<double>(n);
         double* m = W.take<double>(n);
@@ -219,16 +221,16 @@ size_t carve(sph_ctx* c, char* base)
     c->start = W.take<int32_t>(nc1);
     c->scan_tmp = W.take<int32_t>(scan_temp_elems((int)nc1));
     c->vr = W.take<char>(n * 4 * rs);
-    c->pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
-    c->cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
-    c->mf = c->prec == 32 ? W.take<float>(n) : nullptr;
-    const bool lists = c->prec == 32 || dual;
+    c->pos4 = W.take<float4>(n);     // both forms: FP32 cell-relative positions for the candidate walks
+    c->cell = W.take<int32_t>(n);
+    c->mf = W.take<float>(n);
+    const bool lists = !c->density_only;   // both forms: the force pass walks the density pass's list
     c->nbl = lists ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
     c->nbc = lists ? W.take<int32_t>(n) : nullptr;
     c->anu = dual ? W.take<char>(D * n * rs) : nullptr;
     c->du = dual ? W.take<double>(DU_COUNT) : nullptr;
-    c->R = W.take<char>(D * n * rs);
-    c->chi = W.take<char>(n * rs);
+    c->R = c->density_only ? nullptr : W.take<char>(D * n * rs);
+    c->chi = c->density_only ? nullptr : W.take<char>(n * rs);
     const int pblocks = std::max(pair_blocks(c->prec, (int)n), dual_pair_blocks(c->prec, (int)n));
     c->partials = W.take<double>((size_t)pblocks * kNPart);
     c->rows = W.take<double>((size_t)reduce_rows_blocks() * kNPart);
@@ -1050,6 +1052,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     c.st = (cudaStream_t)stream;
     c.G = G;
     c.K64 = make_consts<double>(p);
+    c.density_only = 1;
     if (carve(&c, nullptr) > kNoAllocScratchBytes) return SPH_ERR_WORKSPACE;
     carve(&c, (char*)base);
 
@@ -1073,7 +1076,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     s = run_sort(&c, 0, 0);
     if (s != SPH_OK) return s;
     const StateSet<double>& S1 = c.set[c.cur].d;
-    SPH_CU(launch_density(64, c.dim, ni, cur_set(&c), c.start, c.G, consts(&c), c.vr, nullptr, nullptr, nullptr,
+    SPH_CU(launch_density(64, c.dim, ni, cur_set(&c), c.start, c.G, consts(&c), c.vr, c.pos4, c.cell, nullptr,
                           nullptr, c.st));
     SPH_CU(launch_rho_out(64, ni, c.vr, S1.kind, S1.id, p->rho0, rho, c.st));
     return SPH_OK;
