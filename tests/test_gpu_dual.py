@@ -33,6 +33,10 @@ def _case(kind):
         return cases.tgv2d(24, jitter_dp=0.1, seed=3)
     if kind == "cavity":
         return cases.cavity2d(24, U=1.0, jitter_dp=0.1, seed=3)
+    if kind == "cavity_g":
+        c = cases.cavity2d(24, U=1.0, jitter_dp=0.1, seed=4)
+        c["g"] = (0.0, -1.0, 0.0)
+        return c
     if kind == "3d":
         return cases.tgv3d(10, jitter_dp=0.1, seed=3)
     return cases.cylinder2d(D=1.0, res=10, box=(3.0, 2.0), center=(1.0, 1.0), refine=(0.6, 2.4, 0.4, 1.6),
@@ -89,10 +93,10 @@ MODES = {"limited": {}, "unlimited": {"tv_mode": oracle.TV_UNLIMITED},
          "background": {"tv_mode": oracle.TV_BACKGROUND}, "none": {"tv_mode": oracle.TV_NONE}}
 
 
-@pytest.mark.parametrize("kind", ["tgv", "cavity", "3d", "cylinder"])
+@pytest.mark.parametrize("kind", ["tgv", "cavity", "cavity_g", "3d", "cylinder"])
 @pytest.mark.parametrize("mode", list(MODES))
 def test_fp64_advection_step_parity(kind, mode):
-    if kind in ("3d", "cylinder") and mode in ("none", "background"):
+    if kind in ("3d", "cylinder", "cavity_g") and mode in ("none", "background"):
         pytest.skip("covered on the 2-D cases")
     c = _case(kind)
     P = oracle_params(c, **MODES[mode])
@@ -113,7 +117,7 @@ def test_fp64_advection_step_parity(kind, mode):
         assert err[k] <= 1e-11, (k, err)
 
 
-@pytest.mark.parametrize("kind", ["tgv", "cavity", "3d"])
+@pytest.mark.parametrize("kind", ["tgv", "cavity", "cavity_g", "3d", "cylinder"])
 def test_fp32_advection_step_parity(kind):
     c = _case(kind)
     P = oracle_params(c)
