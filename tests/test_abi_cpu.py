@@ -137,3 +137,13 @@ def test_dual_integrator_workspace_and_host_checks(lib):
     assert lib.sph_get_density_rate(None, buf) == 1
     assert sph.sph_kernel_class_name(7) == "advect" and sph.sph_kernel_class_name(8) == "acoustic"
     assert sph.sph_kernel_class_name(9) == "?"
+
+
+def test_particle_count_limit_is_two_to_the_25(lib):
+    """A list entry holds j in 25 bits: n = 2^25 is accepted, one more is refused."""
+    c = cases.tgv2d(20)
+    p = sph.params_from_case(c, 32)
+    assert sph.sph_query_workspace(p, 2 ** 25) > 0
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_query_workspace(p, 2 ** 25 + 1)
+    assert e.value.status == 1
