@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
         }
         const double r = sqrt(r2);
         if (r < 2.0 * hij) {
-            sigma += wendland_W<DIM, double>(r, 1.0 / hij);
+            sigma += wendland_W<DIM, double>(r, K.uniform_h ? K.inv_h_u : 1.0 / hij);
             if (nbl && j != i && r2 > 0.0) {
                 if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
                 ++cnt;
@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         for (int d = 0; d < DIM; ++d) xi[d] = S.x[(size_t)d * n + i];
         const double hi = S.h[i];
         const double rho_i = K.rho0 + me.w;
+        const double inv_rho_i = 1.0 / rho_i;
         const double p_i = K.c2 * me.w;
         PlainD acc_a[DIM], acc_R[DIM];
         // one neighbour j (j != i); returns without work outside the support
@@ -126,12 +127,15 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
             }
             const double hij = pair_h(K, hi, S.h[j]);
             if (r2 > 4.0 * hij * hij * (1.0 + 1e-12)) return;   // far: no FP64 square root
-            double r = sqrt(r2);
-            if (!(r < 2.0 * hij) || r == 0.0) return;
-            double dw = wendland_dW<DIM, double>(r, 1.0 / hij);
+            if (!(r2 > 0.0)) return;
+            const double inv_r = rsqrt(r2);
+            const double r = r2 * inv_r;
+            if (!(r < 2.0 * hij)) return;
+            const double dw = wendland_dW<DIM, double>(r, K.uniform_h ? K.inv_h_u : 1.0 / hij);
             double4_32a oj = vr[j];
             double vj[3] = {oj.x, oj.y, oj.z};
-            pair_force<double, DIM, PlainD>(K, rv, r, dw, vi, rho_i, p_i, vj, oj.w, S.m[j], acc_a, acc_R);
+            pair_force<double, DIM, PlainD>(K, rv, r, inv_r, dw, vi, rho_i, inv_rho_i, p_i, vj, oj.w, S.m[j], acc_a,
+                                            acc_R);
         };
         const int cnt = nbl ? nbc[i] : cap + 1;
         if (cnt <= cap) {

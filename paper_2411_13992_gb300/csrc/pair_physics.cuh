@@ -33,16 +33,18 @@ __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
 }
 
 // Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, r = |rv|,
-// dw = W'(r, h_ij)).  Adds into the caller's accumulators.
+// inv_r = 1/r, dw = W'(r, h_ij), inv_rho_i = 1/rho_i).  Adds into the
+// caller's accumulators.  One reciprocal per neighbour density serves both
+// V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU).
 template <typename Real, int DIM, typename Acc>
-__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real dw, const Real* vi,
-                                           Real rho_i, Real p_i, const Real* vj, Real w_j, Real m_j, Acc* acc_a,
-                                           Acc* acc_R)
+__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real inv_r, Real dw,
+                                           const Real* vi, Real rho_i, Real inv_rho_i, Real p_i, const Real* vj,
+                                           Real w_j, Real m_j, Acc* acc_a, Acc* acc_R)
 {
     const bool wall = isinf(w_j);
     const Real rho_j = wall ? rho_i : K.rho0 + w_j;
+    const Real inv_rho_j = wall ? inv_rho_i : Real(1) / rho_j;
     const Real p_j = wall ? p_i : K.c2 * w_j;
-    const Real inv_r = Real(1) / r;
     Real ul = Real(0), ur = Real(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -56,10 +58,10 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
     beta = beta < Real(1) ? beta : Real(1);
     const Real rhobar = Real(0.5) * (rho_i + rho_j);
     const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
-    const Real inv_rr = Real(1) / (rho_i * rho_j);
+    const Real inv_rr = inv_rho_i * inv_rho_j;
     const Real cp = Real(-2) * m_j * pstar * inv_rr;
     const Real cv = K.two_eta * m_j * inv_rr * dw * inv_r;
-    const Real V_j = m_j / rho_j;
+    const Real V_j = m_j * inv_rho_j;
     const Real dwr = dw * inv_r;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
