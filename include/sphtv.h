@@ -132,7 +132,10 @@ typedef struct sph_params {
                                with SPH_INT_DUAL) */
     int32_t integrator;     /* SPH_INT_*: kick-drift-kick (default) or dual-criteria;
                                SPH_INT_DUAL requires fixed_dt = 0 */
-    int32_t pad0;
+    int32_t graphs;         /* 1 (default): sph_step replays kick-drift-kick steps two at a
+                               time from a captured CUDA graph on a library-owned stream,
+                               ordered after and before the context's stream by events
+                               (same results, fewer launches); 0: always launch directly */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -155,8 +158,8 @@ typedef struct sph_ctx sph_ctx;
 
 /* Fill *p with the paper's constants: riemann_eta 3, tv_xi -0.2, tv_C 1e3,
  * tv_thresh 5e-4, cfl_ad 0.25, cfl_ac 0.6, tv_mode limited, tv_h h_min,
- * h_pair mean, kahan on, precision 64, dim 2, rho0 1.  Returns SPH_ERR_ARG
- * on NULL. */
+ * h_pair mean, kahan on, graphs on, precision 64, dim 2, rho0 1.  Returns
+ * SPH_ERR_ARG on NULL. */
 SPH_API sph_status sph_default_params(sph_params* p);
 
 /* Bytes of device workspace a context for n particles needs, 1 <= n <= 2^25.

@@ -60,7 +60,7 @@ class SphParams(ctypes.Structure):
         ("cfl_ad", ctypes.c_double), ("cfl_ac", ctypes.c_double), ("u_ref", ctypes.c_double),
         ("fixed_dt", ctypes.c_double),
         ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32),
-        ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("graphs", ctypes.c_int32),
     ]
 
 

@@ -54,6 +54,7 @@ struct Grid {
     double inv_edge[3];
     float edgef[3];
     int ncell;
+    int sms;            // streaming multiprocessors of the device (grid sizing of the pair passes)
 };
 
 // Constants of the method for one precision.

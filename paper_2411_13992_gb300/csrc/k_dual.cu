@@ -624,7 +624,8 @@ template <template <typename, int, typename, bool> class Kern> struct Dispatch;
     struct name##_t {                                                                                      \
         static void run(const DualK<Real>& A, const Grid& G, const Consts<Real>& K, cudaStream_t st)     \
         {                                                                                                  \
-            name<Real, DIM, Acc, U><<<nblk(A.n, tpb<Real>()), tpb<Real>(), 0, st>>>(A, G, K);              \
+            const int T = pair_threads(sizeof(Real) == 8 ? 64 : 32, A.n, G.sms);                            \
+            name<Real, DIM, Acc, U><<<nblk(A.n, T), T, 0, st>>>(A, G, K);                                    \
         }                                                                                                  \
     };
 SPH_DUAL_PAIR_KERNEL(k_dual_advect)
@@ -672,7 +673,7 @@ void run_elem(int dim, const DualArgs& a, const Grid& G, int which, cudaStream_t
 
 }  // namespace
 
-int dual_pair_blocks(int prec, int n) { return prec == 64 ? nblk(n, kTPB64) : nblk(n, kTPB32); }
+int dual_pair_blocks(int prec, int n, int sms) { return pair_blocks(prec, n, sms); }
 
 cudaError_t launch_dual_begin(const sph_params& P, const double* diag, double* du, cudaStream_t st)
 {
@@ -696,7 +697,7 @@ cudaError_t launch_dual_substep(int prec, int dim, const DualArgs& a, const Grid
     if (prec == 64) run_elem<double>(dim, a, G, 1, st);
     else run_elem<float>(dim, a, G, 1, st);
     run_pair<k_dual_continuity_t>(prec, dim, a, G, K, st);
-    const int nb = dual_pair_blocks(prec, a.n);
+    const int nb = dual_pair_blocks(prec, a.n, G.sms);
     const int rows = launch_reduce_rows(nb, a.partials, a.rows, st);
     k_dual_finalize<<<1, 256, 0, st>>>(rows ? rows : nb, rows ? a.rows : a.partials, dual_consts(P), a.du, diag,
                                        dt_ptr);

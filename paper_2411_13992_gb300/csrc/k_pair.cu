@@ -314,13 +314,26 @@ __global__ void __launch_bounds__(256) k_finalize(int nblocks, const double* __r
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-int pair_blocks(int prec, int n) { return prec == 32 ? pair_blocks32(n) : nblk(n, 256); }
+// Threads per block of the pair passes: 256 (FP64) or 128 (FP32) when the
+// particles fill every SM at that size; smaller blocks (down to one warp)
+// when they do not, so that a small problem still spreads over all SMs
+// instead of queueing its FP64 work on a few.
+int pair_threads(int prec, int n, int sms)
+{
+    const int full = prec == 64 ? 256 : 128;
+    if (sms <= 0) sms = 152;
+    if ((int64_t)n >= (int64_t)sms * full) return full;
+    int t = ((n + sms - 1) / sms + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > full ? full : t);
+}
+
+int pair_blocks(int prec, int n, int sms) { return nblk(n, pair_threads(prec, n, sms)); }
 
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
                            cudaStream_t st)
 {
-    const int T = 256;
+    const int T = pair_threads(prec, n, G.sms);
     if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st);
     auto s = *(StateSet<double>*)S;
     auto k = *(const Consts<double>*)K;
@@ -337,7 +350,7 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
                           void* Rout, void* chi, double* partials, cudaStream_t st)
 {
-    const int T = 256;
+    const int T = pair_threads(prec, n, G.sms);
     if (prec == 32)
         return launch_forces32(dim, n, S, start, G, K, mf, vr, pos4, cell_of, nbl, nbc, dt, kick_on, write_ad, Rout,
                                chi, partials, st);
@@ -353,9 +366,9 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st)
+cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, int sms, cudaStream_t st)
 {
-    const int T = prec == 32 ? 128 : 256;   // one partials row per block of the forces kernel of that form
+    const int T = pair_threads(prec, n, sms);   // one partials row per block of the force pass
     if (prec == 64) {
         auto s = *(StateSet<double>*)S;
         if (dim == 2) k_diag_only<double, 2><<<nblk(n, T), T, 0, st>>>(n, s, partials);

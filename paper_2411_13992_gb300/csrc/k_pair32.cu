@@ -279,8 +279,6 @@ __global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-int pair_blocks32(int n) { return nblk(n, kTPB32); }
-
 int nbl_capacity(int dim) { return dim == 3 ? 128 : 96; }
 
 template <int DIM, typename Acc, bool U>
@@ -288,8 +286,9 @@ static void density_t(int n, const float4* pos4, const int32_t* cell_of, const i
                       const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl, int32_t* nbc,
                       cudaStream_t st)
 {
-    k_density32<DIM, Acc, U><<<nblk(n, kTPB32), kTPB32, 0, st>>>(n, pos4, cell_of, start, G, K, S, vr, nbl, nbc,
-                                                                 nbl_capacity(DIM));
+    const int T = pair_threads(32, n, G.sms);
+    k_density32<DIM, Acc, U><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, K, S, vr, nbl, nbc,
+                                                       nbl_capacity(DIM));
 }
 
 template <int DIM, typename Acc, bool U>
@@ -298,9 +297,9 @@ static void forces_t(int n, const float4* pos4, const int32_t* cell_of, const in
                      const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
                      float* Rout, float* chi, double* partials, cudaStream_t st)
 {
-    k_forces32<DIM, Acc, U><<<nblk(n, kTPB32), kTPB32, 0, st>>>(n, pos4, cell_of, start, G, K, S, mf, vr, nbl, nbc,
-                                                                nbl_capacity(DIM), dt, kick_on, write_ad, Rout, chi,
-                                                                partials);
+    const int T = pair_threads(32, n, G.sms);
+    k_forces32<DIM, Acc, U><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, K, S, mf, vr, nbl, nbc,
+                                                      nbl_capacity(DIM), dt, kick_on, write_ad, Rout, chi, partials);
 }
 
 #define SPH_DISPATCH32(FN, ...)                                                   \

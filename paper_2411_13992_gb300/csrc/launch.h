@@ -49,7 +49,8 @@ cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* 
                            cudaStream_t st);
 
 // k_pair.cu (FP64 form; FP32 calls are forwarded to k_pair32.cu)
-int pair_blocks(int prec, int n);
+int pair_threads(int prec, int n, int sms);
+int pair_blocks(int prec, int n, int sms);
 // FP64 form: nbl / nbc may be null (no list); with them the density pass
 // writes the neighbour list the dual-criteria integrator uses.
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
@@ -61,7 +62,6 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
                           void* Rout, void* chi, double* partials, cudaStream_t st);
 
 // k_pair32.cu
-int pair_blocks32(int n);
 int nbl_capacity(int dim);
 cudaError_t launch_density32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K, void* vr,
                              const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
@@ -70,7 +70,7 @@ cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const
                             const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                             const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
                             void* Rout, void* chi, double* partials, cudaStream_t st);
-cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, cudaStream_t st);
+cudaError_t launch_diag_only(int prec, int dim, int n, void* S, double* partials, int sms, cudaStream_t st);
 int reduce_rows_blocks();
 // First level of the fixed-order reduction of per-block partials: returns the
 // number of rows written (0: too few partials, reduce them directly).
@@ -113,7 +113,7 @@ struct DualArgs {
     double* rows;
     uint32_t* err;
 };
-int dual_pair_blocks(int prec, int n);
+int dual_pair_blocks(int prec, int n, int sms);
 cudaError_t launch_dual_begin(const sph_params& P, const double* diag, double* du, cudaStream_t st);
 cudaError_t launch_dual_advect(int prec, int dim, const DualArgs& a, const Grid& G, const void* K, cudaStream_t st);
 cudaError_t launch_dual_substep(int prec, int dim, const DualArgs& a, const Grid& G, const void* K,

@@ -58,6 +58,13 @@ struct sph_ctx {
     double* du;         // dual integrator: device state (DU_*)
     int dual_est;       // dual integrator: substeps to launch before the first check
     int density_only;   // sph_density_noalloc's view: no neighbour lists
+    // CUDA graph replay of kick-drift-kick steps (params.graphs): two steps
+    // per graph, one graph per parity of the ping-pong state sets
+    cudaStream_t gst;           // library-owned stream of the replays
+    cudaEvent_t gev[2];         // context stream -> gst, gst -> context stream
+    cudaGraphExec_t gexec[2];
+    int gstate[2];              // 0 not captured, 1 ready, -1 capture failed (launch directly)
+    int64_t glaunches[2];       // kernels in one replay
     void* R;
     void* chi;
     double* partials;
@@ -111,6 +118,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (!(p->fixed_dt >= 0) || !(p->cfl_ad > 0) || !(p->cfl_ac > 0)) return SPH_ERR_ARG;
     if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
+    if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
     if (p->integrator == SPH_INT_DUAL && (p->fixed_dt != 0.0 || p->adjoint_steps != 0)) return SPH_ERR_ARG;
     for (int d = 0; d < p->dim; ++d) {
         if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
@@ -119,6 +127,20 @@ sph_status check_params(const sph_params* p, int64_t n)
         if (nc > 1 << 20) return SPH_ERR_ARG;
     }
     return SPH_OK;
+}
+
+// Streaming multiprocessors of the current device (152 on GB300 if the
+// query fails or there is no device, as in a workspace query on a host
+// without one; the count only sizes grids).
+int device_sms()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return v;
 }
 
 Grid make_grid(const sph_params* p)
@@ -152,6 +174,7 @@ Grid make_grid(const sph_params* p)
         ncell *= G.nc[d];
     }
     G.ncell = (int)ncell;
+    G.sms = device_sms();
     return G;
 }
 
@@ -231,8 +254,8 @@ size_t carve(sph_ctx* c, char* base)
     c->du = dual ? W.take<double>(DU_COUNT) : nullptr;
     c->R = c->density_only ? nullptr : W.take<char>(D * n * rs);
     c->chi = c->density_only ? nullptr : W.take<char>(n * rs);
-    const int pblocks = std::max(pair_blocks(c->prec, (int)n), dual_pair_blocks(c->prec, (int)n));
-    c->partials = W.take<double>((size_t)pblocks * kNPart);
+    // one partials row per block of a pair pass; blocks are never smaller than a warp
+    c->partials = W.take<double>(((size_t)n + 31) / 32 * kNPart);
     c->rows = W.take<double>((size_t)reduce_rows_blocks() * kNPart);
     c->diag = W.take<double>(DG_COUNT);
     c->dt = W.take<double>(1);
@@ -341,8 +364,9 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     if (!pairs) {
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
                               c->nbl, c->nbc, c->st));
-        SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->st));
-        SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->rows, c->P, c->diag, c->dt, count_step, c->st));
+        SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->G.sms, c->st));
+        SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
+                               count_step, c->st));
         c->launches += 3;
         return SPH_OK;
     }
@@ -356,7 +380,8 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
                          c->nbl, c->nbc, c->dt, kick_on, write_ad, c->R, c->chi, c->partials, c->st));
     SPH_MARK(SPH_K_FORCES, 1);
     SPH_MARK(SPH_K_FINALIZE, 0);
-    SPH_CU(launch_finalize(pair_blocks(c->prec, n), c->partials, c->rows, c->P, c->diag, c->dt, count_step, c->st));
+    SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
+                           count_step, c->st));
     SPH_MARK(SPH_K_FINALIZE, 1);
     c->launches += 3;
     return SPH_OK;
@@ -430,6 +455,52 @@ sph_status run_dual_step(sph_ctx* c)
     SPH_MARK(SPH_K_ACOUSTIC, 1);
     c->dual_est = (int)hb[DU_K] + 1;
     return SPH_OK;
+}
+
+// Capture two kick-drift-kick steps starting from state-set parity par into
+// a graph on the library stream.  Nothing runs during the capture (the sets
+// and counters are left as they were); on any failure the context falls
+// back to direct launches for that parity.
+void graph_capture(sph_ctx* c, int par)
+{
+    c->gstate[par] = -1;
+    if (!c->gst) {
+        if (cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
+            c->gst = nullptr;
+            cudaGetLastError();
+            return;
+        }
+        if (cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    cudaStream_t user = c->st;
+    const int cur0 = c->cur;
+    const int64_t l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        c->st = c->gst;
+        for (int k = 0; k < 2 && ok; ++k) ok = run_sort(c, 1, 0) == SPH_OK && run_forces(c, 1, 1, 1) == SPH_OK;
+        c->st = user;
+        ok = cudaStreamEndCapture(c->gst, &g) == cudaSuccess && ok && g;
+    }
+    c->cur = cur0;
+    c->glaunches[par] = c->launches - l0;
+    c->launches = l0;
+    if (ok && cudaGraphInstantiate(&c->gexec[par], g, 0) == cudaSuccess) c->gstate[par] = 1;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
+void graph_release(sph_ctx* c)
+{
+    for (int par = 0; par < 2; ++par) {
+        if (c->gstate[par] == 1) cudaGraphExecDestroy(c->gexec[par]);
+        c->gstate[par] = 0;
+    }
 }
 
 bool is_host_ptr(const void* p)
@@ -557,6 +628,7 @@ sph_status sph_default_params(sph_params* p)
     p->tv_h = SPH_TVH_MIN;
     p->h_pair = SPH_HPAIR_MEAN;
     p->kahan = 1;
+    p->graphs = 1;
     return SPH_OK;
 }
 
@@ -706,6 +778,21 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps)
 {
     if (!c || nsteps < 0) return SPH_ERR_ARG;
     if (!c->have_cells) return SPH_ERR_STATE;
+    if (c->P.integrator == SPH_INT_KDK && c->P.graphs && !c->prof_ev && nsteps >= 2) {
+        const int par = c->cur;
+        if (c->gstate[par] == 0) graph_capture(c, par);
+        if (c->gstate[par] == 1) {
+            SPH_CU(cudaEventRecord(c->gev[0], c->st));
+            SPH_CU(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+            for (int32_t k = 0; k + 1 < nsteps; k += 2) {
+                SPH_CU(cudaGraphLaunch(c->gexec[par], c->gst));
+                c->launches += c->glaunches[par];
+            }
+            SPH_CU(cudaEventRecord(c->gev[1], c->gst));
+            SPH_CU(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+            nsteps &= 1;     // two steps per replay bring the sets back to this parity
+        }
+    }
     for (int32_t k = 0; k < nsteps; ++k) {
         if (c->P.integrator == SPH_INT_DUAL) {
             SPH_TRY(run_dual_step(c));
@@ -759,6 +846,7 @@ sph_status sph_set_eta(sph_ctx* c, double eta)
     c->P.eta = eta;
     c->K64 = make_consts<double>(&c->P);
     c->K32 = make_consts<float>(&c->P);
+    graph_release(c);       // the captured launches hold the old constants
     return SPH_OK;
 }
 
@@ -899,6 +987,13 @@ const char* sph_kernel_class_name(int32_t k)
 void sph_destroy(sph_ctx* c)
 {
     if (!c) return;
+    graph_release(c);
+    if (c->gst) {
+        cudaStreamSynchronize(c->gst);
+        cudaEventDestroy(c->gev[0]);
+        cudaEventDestroy(c->gev[1]);
+        cudaStreamDestroy(c->gst);
+    }
     prof_free(c);
     delete[] c->tape;
     delete c;
