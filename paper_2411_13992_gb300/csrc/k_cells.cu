@@ -3,7 +3,7 @@
 // Per step:  kick + drift + cell key + histogram  ->  exclusive scan of the
 // cell counts  ->  atomic scatter into cell ranges  ->  per-cell ordering by
 // particle id (so the sorted order never depends on atomic timing)  ->
-// permute the particle arrays into the new order (and, in the FP32 form,
+// permute the particle arrays into the new order (and, in both forms,
 // emit FP32 positions relative to each particle's cell origin).
 //
 // The kick-drift follows the kick-drift-kick scheme the paper names (Sec. 1,
@@ -210,7 +210,7 @@ __global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, cons
 
 // --------------------------------------------------------------- permute
 
-// FP32 form: pos4 = {offset from the cell origin, h} (uniform resolution:
+// pos4 = {offset from the cell origin, h} (uniform resolution:
 // {offset, m}, since h is then a constant), mf = m in FP32, cell_out = key.
 template <typename Real, int DIM, bool CARRY_AD, bool F32POS>
 __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real> src, StateSet<Real> dst,

@@ -55,7 +55,7 @@ struct DualK {
     int n, cap;
     StateSet<Real> S;
     typename V4<Real>::T* vr;
-    float4* pos4;            // FP32 form: cell-relative offsets (updated by the drifts), m or h
+    float4* pos4;            // cell-relative offsets (the FP32 form's drifts keep them current), m or h
     const int32_t* cell_of;  // FP32 form: home cell of the advection step
     const float* mf;         // FP32 form: masses
     const uint32_t* nbl;

@@ -1,9 +1,13 @@
 // sph_api.cu -- host implementation of the libsphtv C ABI (include/sphtv.h).
 //
 // The context is a small host object.  Every device buffer is carved out of
-// the caller's workspace; nothing here allocates device memory.  All work is
-// enqueued on the context's stream; the only host waits are in sph_sync,
-// sph_get_diag and sph_get_state (host destinations).
+// the caller's workspace; nothing here allocates device memory (the CUDA
+// graph replay of sph_step adds a library-owned stream, two events and the
+// graphs, which are driver objects).  Work is enqueued on the context's
+// stream (graph replays on the library stream, ordered by events); the host
+// waits in sph_sync, sph_get_diag, sph_get_state / sph_get_density_rate with
+// host destinations, sph_set_dt, and once per advection step of the
+// dual-criteria integrator.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -52,7 +56,7 @@ struct sph_ctx {
     float4* pos4;
     int32_t* cell;
     float* mf;
-    uint32_t* nbl;      // FP32 form or dual integrator: neighbour lists [cap][n], transposed
+    uint32_t* nbl;      // neighbour lists of the density pass [cap][n], transposed
     int32_t* nbc;       // neighbour count per particle (with nbl)
     void* anu;          // dual integrator: viscous acceleration held for an advection step
     double* du;         // dual integrator: device state (DU_*)
