@@ -59,8 +59,9 @@ def test_moving_lid_pulls_the_adjacent_fluid_linearly(orc):
     assert (a1[near, 0] > 0.0).all()                     # dragged along the lid's motion
     assert np.abs(a1[near, 1]).max() < 1e-12 * a1[near, 0].max()
     assert np.abs(a1[far]).max() < 1e-11                 # beyond the support: rounding noise only
-    np.testing.assert_allclose(a2[near, 0], 2.0 * a1[near, 0], rtol=1e-12)
-    np.testing.assert_allclose(a3[near, 0], 3.0 * a1[near, 0], rtol=1e-12)
+    # (the rest state carries pressure rounding noise of ~1e-12 absolute)
+    np.testing.assert_allclose(a2[near, 0], 2.0 * a1[near, 0], rtol=1e-10)
+    np.testing.assert_allclose(a3[near, 0], 3.0 * a1[near, 0], rtol=1e-10)
 
 
 def test_uniform_pressure_exerts_no_force_next_to_walls(orc):
