@@ -125,27 +125,35 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index: int):
         self.gpu_index = gpu_index
         self.proc = None
         self.path = None
+        self.window = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                          "--format=csv,noheader,nounits", "-lms", "20", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        time.sleep(0.3)          # let the sampler run before the timed region opens
+
+    def mark(self, begin: bool):
+        """Host time at the start / end of the timed region (the rows kept are those inside it)."""
+        import datetime
+        now = datetime.datetime.now()
+        self.window = (now, None) if begin else (self.window[0] if self.window else now, now)
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        time.sleep(0.25)
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -155,9 +163,23 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
+        inside = rows
+        if self.window and self.window[1] is not None:
+            import datetime
+
+            def stamp(r):
+                try:
+                    return datetime.datetime.strptime(r[9], "%Y/%m/%d %H:%M:%S.%f")
+                except (ValueError, IndexError):
+                    return None
+            t0, t1 = self.window
+            inside = [r for r in rows if stamp(r) is not None and t0 <= stamp(r) <= t1]
+            if not inside:       # a region shorter than one sampling interval: the nearest rows
+                inside = rows
+        rows = inside
         sm = [float(r[1]) for r in rows if _isnum(r[1])]
         smax = [float(r[2]) for r in rows if _isnum(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -320,7 +342,9 @@ def run_native(args):
     sampler = ClockSampler(_gpu_index(torch, dev))
     sampler.start()
     barrier()
+    sampler.mark(True)
     ms, prof = _timed_steps(torch, sim, args.steps)
+    sampler.mark(False)
     barrier()
     clocks = sampler.stop()
     launches = sim.launches() - launches0
@@ -570,7 +594,7 @@ def _adjoint_ratio(torch, sph, cases):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--n", type=int, default=128, help="particles per side of the 3-D Taylor-Green lattice")
