@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     };
     // reach: the largest support radius 2 h_ij of any pair of i (h_j <= h_max)
     const float reach = UNIFORM ? 2.f * K.h_u : 2.f * pair_h(K, hi, K.h_u);
-    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, pos4, visit);
+    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, cell_of, pos4, visit);
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
     const float s0 = (float)S.s0[i];

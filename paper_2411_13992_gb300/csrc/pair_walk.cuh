@@ -59,7 +59,9 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 // The same visit as for_candidates, walked row by row and clipped to the
 // particle's reach.  For each (dy, dz) row the cells are contiguous in the
 // cell order, so the row is one run of particles (two runs across a periodic
-// x boundary) whose x shift and stencil code advance at each cell boundary.
+// x boundary).  The x shift and stencil code of a candidate come from its own
+// cell index (cell_of[j] - k_r = dx for every j of run r), so the walk has no
+// inner loop over the cell boundaries of a run.
 // A row whose nearest y-z distance to particle i exceeds the reach (the
 // largest support radius of any pair of i) is skipped, and the x extent of a
 // row is cut to the cells within the remaining half-chord; every margin is
@@ -69,6 +71,7 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 template <int DIM, typename F>
 __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach, int cell_i, const Grid& G,
                                                     const int32_t* __restrict__ start,
+                                                    const int32_t* __restrict__ cell_of,
                                                     const float4* __restrict__ pos4, F& f)
 {
     int c[3];
@@ -122,20 +125,13 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
             const int row = ncx * (cy + G.nc[1] * cz);
             const uint32_t code_row = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
             for (int r = 0; r < nrun; ++r) {
-                int cell = row + rc0[r];
-                int dx = rdx[r];
-                int j = start[cell];
+                const int cell = row + rc0[r];
+                const int kr = cell - rdx[r];      // dx of candidate j = cell_of[j] - kr
                 const int jend = start[cell + rn[r]];
-                int nb = start[cell + 1];
-                float shx = -(float)dx * ex;
-                for (; j < jend; ++j) {
-                    while (j >= nb) {          // next non-empty cell of the run
-                        ++cell;
-                        ++dx;
-                        nb = start[cell + 1];
-                        shx = -(float)dx * ex;
-                    }
+                for (int j = start[cell]; j < jend; ++j) {
                     const float4 pj = pos4[j];
+                    const int dx = cell_of[j] - kr;
+                    const float shx = -(float)dx * ex;
                     const float rx = (oi[0] - pj.x) + shx;
                     const float ry_ = (oi[1] - pj.y) + shy;
                     float r2 = rx * rx + ry_ * ry_;
