@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
         for (int d = 0; d < DIM; ++d) xbp[(size_t)d * n + k] = vbp[(size_t)d * n + k] = Real(0);
         sigb[k] = Real(0);
     }
-    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
 // ------------------------------------------------- density + drift / kick
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256) k_adj_sum(int nblocks, const double* __re
     for (int q = 0; q < kNPart; ++q) v[q] = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += partials[(size_t)b * kNPart];
     __shared__ double out[kNPart];
-    block_partials(v, out);
+    block_partials<false>(v, out);
     __syncthreads();
     if (threadIdx.x == 0) *acc += out[0];
 }

@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
             const double v = (double)A.S.v[(size_t)d * n + i];
             v2 += v * v;
         }
-        part[6] = sqrt(v2);
+        part[6] = v2;                 // squares: block_partials takes the roots
         if (A.du[DU_LAST] != 0.0) {
             const double inv_Dt = 1.0 / A.du[DU_DT_AD];
             const double m_i = A.S.m[i];
@@ -506,13 +506,13 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
             part[0] = m_i;
             part[4] = 0.5 * m_i * v2;
             part[5] = A.chi[i] > Real(0) ? 1.0 : 0.0;
-            part[7] = sqrt(vt2);
-            part[8] = sqrt(dr2);
+            part[7] = vt2;
+            part[8] = dr2;
         }
     } else if (i < n) {
         A.S.drho[i] = Real(0);
     }
-    block_partials(part, A.partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, A.partials + (size_t)blockIdx.x * kNPart);
 }
 
 // Reduce the substep's partials (in a fixed order); advance t; pick the next
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256) k_dual_finalize(int nblocks, const double
         for (int k = 0; k < kNPart; ++k) acc[k] = (k >= 6 && k <= 8) ? fmax(acc[k], p[k]) : acc[k] + p[k];
     }
     __shared__ double out[kNPart];
-    block_partials(acc, out);
+    block_partials<false>(acc, out);
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double vmax = out[6];

@@ -198,9 +198,9 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         part[0] = m_i;
         part[4] = 0.5 * m_i * v2;
         part[5] = chi > 0.0 ? 1.0 : 0.0;
-        part[6] = sqrt(v2);
-        part[7] = sqrt(vt2);
-        part[8] = sqrt(dr2);
+        part[6] = v2;                 // squares: block_partials takes the roots
+        part[7] = vt2;
+        part[8] = dr2;
     } else if (i < n) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         }
         chi_out[i] = 0.0;
     }
-    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
 // ================================================ diagnostics only
@@ -239,11 +239,11 @@ __global__ void __launch_bounds__(256) k_diag_only(int n, StateSet<Real> S, doub
         }
         part[0] = m_i;
         part[4] = 0.5 * m_i * v2;
-        part[6] = sqrt(v2);
-        part[7] = sqrt(v2);
-        part[8] = sqrt(dr2);
+        part[6] = v2;                 // squares: block_partials takes the roots
+        part[7] = v2;
+        part[8] = dr2;
     }
-    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
 // =========================================================== finalize
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_reduce_rows(int nrows, int chunk, const
 #pragma unroll
         for (int k = 0; k < kNPart; ++k) acc[k] = (k >= 6 && k <= 8) ? fmax(acc[k], p[k]) : acc[k] + p[k];
     }
-    block_partials(acc, out + (size_t)blockIdx.x * kNPart);
+    block_partials<false>(acc, out + (size_t)blockIdx.x * kNPart);
 }
 
 struct DtConsts {
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_finalize(int nblocks, const double* __r
         for (int k = 0; k < kNPart; ++k) acc[k] = (k >= 6 && k <= 8) ? fmax(acc[k], p[k]) : acc[k] + p[k];
     }
     __shared__ double out[kNPart];
-    block_partials(acc, out);
+    block_partials<false>(acc, out);
     __syncthreads();
     if (threadIdx.x == 0) {
         const double vmax = out[6];

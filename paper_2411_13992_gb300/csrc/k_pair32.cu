@@ -105,12 +105,16 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     const float hi = UNIFORM ? K.h_u : pi.w;
     Acc sigma;
     int cnt = 0;
+    uint32_t* lp = nbl + i;
     auto visit = [&](int j, uint32_t code, const float4& pj, float r2, float, float, float) {
         if (r2 < support2<UNIFORM>(K, hi, pj.w)) {
             const float inv_h = UNIFORM ? K.inv_h_u : 1.f / pair_h(K, hi, pj.w);
             sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), inv_h));
             if (r2 > 0.f) {
-                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
+                if (cnt < cap) {
+                    *lp = ((uint32_t)j << kCodeBits) | code;
+                    lp += n;
+                }
                 ++cnt;
             }
         }
@@ -236,12 +240,18 @@ __global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __
         // (its FP64 division only in that mode: FP64 is 1/74 of the FP32 rate)
         const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
         const float bg = bgmode ? (float)(-(dt * dt * (double)(K.rho0 * K.c2)) / (double)rho_i) : 0.f;
-        double v2 = 0.0, vt2 = 0.0, dr2 = 0.0;
+        // momentum and kinetic energy in FP64; the maxima of the transport
+        // speed |v + dr/dt| and of |dr| (diagnostics of the correction) from
+        // FP32 squares, to keep this epilogue off the FP64 pipe
+        const float inv_dt = dt > 0.0 ? 1.f / (float)dt : 0.f;
+        const float hdtf = (float)hdt;
+        double v2 = 0.0;
+        float vt2 = 0.f, dr2 = 0.f;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const size_t o = (size_t)d * n + i;
             const float dr = bgmode ? bg * R[d] : K.tv_xi * chi * htv2 * R[d];
-            const float vn = __fadd_rn(vi[d], __fmul_rn((float)hdt, a[d]));
+            const float vn = __fadd_rn(vi[d], __fmul_rn(hdtf, a[d]));
             if (write_ad) {
                 S.a[o] = a[d];
                 S.dr[o] = dr;
@@ -250,17 +260,17 @@ __global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __
             Rout[o] = R[d];
             part[1 + d] = m_i * (double)vn;
             v2 += (double)vn * vn;
-            dr2 += (double)dr * dr;
-            const double vt = dt > 0.0 ? (double)vn + (double)dr / dt : (double)vn;
+            dr2 += dr * dr;
+            const float vt = fmaf(dr, inv_dt, vn);
             vt2 += vt * vt;
         }
         chi_out[i] = chi;
         part[0] = m_i;
         part[4] = 0.5 * m_i * v2;
         part[5] = chi > 0.f ? 1.0 : 0.0;
-        part[6] = sqrt(v2);
-        part[7] = sqrt(vt2);
-        part[8] = sqrt(dr2);
+        part[6] = v2;                 // squares: block_partials takes the roots
+        part[7] = (double)vt2;
+        part[8] = (double)dr2;
     } else if (i < n) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -272,7 +282,7 @@ __global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __
         }
         chi_out[i] = 0.f;
     }
-    block_partials(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
 }
 
 // --------------------------------------------------------------- launchers

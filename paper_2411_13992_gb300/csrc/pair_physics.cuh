@@ -71,13 +71,25 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
     }
 }
 
-// Block reduction of the FP64 partials: 6 sums then 3 maxima.
+// Block reduction of the diagnostics partials into out_block (layout: 0
+// mass, 1-3 momentum, 4 KE, 5 n_chi, 6 max|v|, 7 max|v + dr/dt|, 8 max|dr|,
+// 9 unused, written 0).  FIRST: per-particle values of a pair pass, with
+// slot 5 a 0/1 flag and slots 6-8 the SQUARES of the magnitudes: the square
+// root of the largest square is the largest magnitude (both correctly
+// rounded), so one root per block replaces one per particle.  Otherwise:
+// rows of partials to fold.  The sums are FP64 shuffle trees in a fixed
+// order.  With FIRST the flags are counted with a ballot and the maxima of
+// the non-negative squares are integer maxima of their bit patterns (a NaN
+// counts as 0, as fmax ignores it), which keeps both off the FP64 pipe
+// (1/64 of the FP32 rate on this part).
+template <bool FIRST>
 __device__ __forceinline__ void block_partials(double* vals, double* out_block)
 {
     __shared__ double sh[32][kNPart];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    constexpr int kSums = FIRST ? 5 : 9;
 #pragma unroll
-    for (int k = 0; k < kNPart; ++k) {
+    for (int k = 0; k < kSums; ++k) {
         double x = vals[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -86,14 +98,29 @@ __device__ __forceinline__ void block_partials(double* vals, double* out_block)
         }
         if (lane == 0) sh[w][k] = x;
     }
+    if (FIRST) {
+        const unsigned flags = __ballot_sync(0xffffffffu, __double_as_longlong(vals[5]) != 0);
+        if (lane == 0) sh[w][5] = (double)__popc(flags);
+#pragma unroll
+        for (int k = 6; k <= 8; ++k) {
+            long long b = __double_as_longlong(vals[k]);
+            if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) b = 0;      // NaN
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, off));
+            if (lane == 0) sh[w][k] = __longlong_as_double(b);
+        }
+    }
     __syncthreads();
-    if (threadIdx.x < kNPart) {
-        int k = threadIdx.x;
+    if (threadIdx.x < 9) {
+        const int k = threadIdx.x;
         double x = sh[0][k];
         for (int t = 1; t < nw; ++t) x = (k >= 6 && k <= 8) ? fmax(x, sh[t][k]) : x + sh[t][k];
+        if (FIRST && k >= 6) x = sqrt(x);
         out_block[k] = x;
+    } else if (threadIdx.x == 9) {
+        out_block[9] = 0.0;
     }
 }
-// partial layout: 0 mass, 1-3 momentum, 4 KE, 5 n_chi, 6 vmax, 7 vt_max, 8 dr_max, 9 unused
+
 
 }  // namespace sphtv

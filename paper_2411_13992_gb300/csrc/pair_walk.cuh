@@ -128,9 +128,7 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                 const int cell = row + rc0[r];
                 const int kr = cell - rdx[r];      // dx of candidate j = cell_of[j] - kr
                 const int jend = start[cell + rn[r]];
-                for (int j = start[cell]; j < jend; ++j) {
-                    const float4 pj = pos4[j];
-                    const int dx = cell_of[j] - kr;
+                auto one = [&](int j, const float4& pj, int dx) {
                     const float shx = -(float)dx * ex;
                     const float rx = (oi[0] - pj.x) + shx;
                     const float ry_ = (oi[1] - pj.y) + shy;
@@ -141,7 +139,15 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                         r2 += rz_ * rz_;
                     }
                     f(j, code_row + (uint32_t)dx, pj, r2, rx, ry_, rz_);
+                };
+                int j = start[cell];
+                for (; j + 1 < jend; j += 2) {
+                    const float4 p0 = pos4[j], p1 = pos4[j + 1];
+                    const int d0 = cell_of[j] - kr, d1 = cell_of[j + 1] - kr;
+                    one(j, p0, d0);
+                    one(j + 1, p1, d1);
                 }
+                if (j < jend) one(j, pos4[j], cell_of[j] - kr);
             }
         }
     }
