@@ -92,15 +92,19 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // every load of the particle's own data first: they are independent
+    const int8_t kind = S.kind[i];
+    const float4 pi = pos4[i];
+    const int cell_i = cell_of[i];
+    const float s0 = (float)S.s0[i];
     float vi[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
-    if (S.kind[i]) {
+    if (kind) {
         vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
         nbc[i] = 0;
         return;
     }
-    const float4 pi = pos4[i];
     const float oi[3] = {pi.x, pi.y, pi.z};
     const float hi = UNIFORM ? K.h_u : pi.w;
     Acc sigma;
@@ -121,10 +125,9 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     };
     // reach: the largest support radius 2 h_ij of any pair of i (h_j <= h_max)
     const float reach = UNIFORM ? 2.f * K.h_u : 2.f * pair_h(K, hi, K.h_u);
-    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, cell_of, pos4, visit);
+    for_candidates_rows<DIM>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
-    const float s0 = (float)S.s0[i];
     const float w = K.rho0 * (sigma.value() - s0) / s0;
     vr[i] = make_float4(vi[0], vi[1], vi[2], w);
 }

@@ -69,6 +69,12 @@ struct sph_ctx {
     cudaGraphExec_t gexec[2];
     int gstate[2];              // 0 not captured, 1 ready, -1 capture failed (launch directly)
     int64_t glaunches[2];       // kernels in one replay
+    // the adjoint's segment (forward replay recording the tape, then the
+    // reverse sweep) for one segment length, captured on first use
+    cudaGraphExec_t aexec;
+    int astate;                 // as gstate
+    int asteps, acur0, acur1;   // segment length; state-set parity at its start and end
+    int64_t alaunches;
     void* R;
     void* chi;
     double* partials;
@@ -465,21 +471,30 @@ sph_status run_dual_step(sph_ctx* c)
 // a graph on the library stream.  Nothing runs during the capture (the sets
 // and counters are left as they were); on any failure the context falls
 // back to direct launches for that parity.
+// The library stream of the replays and the two events that fence it
+// against the context's stream; false if they cannot be created.
+bool graph_stream(sph_ctx* c)
+{
+    if (c->gst) return true;
+    if (cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
+        c->gst = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(c->gst);
+        c->gst = nullptr;
+        return false;
+    }
+    return true;
+}
+
 void graph_capture(sph_ctx* c, int par)
 {
     c->gstate[par] = -1;
-    if (!c->gst) {
-        if (cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
-            c->gst = nullptr;
-            cudaGetLastError();
-            return;
-        }
-        if (cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-    }
+    if (!graph_stream(c)) return;
     cudaStream_t user = c->st;
     const int cur0 = c->cur;
     const int64_t l0 = c->launches;
@@ -505,6 +520,21 @@ void graph_release(sph_ctx* c)
         if (c->gstate[par] == 1) cudaGraphExecDestroy(c->gexec[par]);
         c->gstate[par] = 0;
     }
+    if (c->astate == 1) cudaGraphExecDestroy(c->aexec);
+    c->astate = 0;
+    c->asteps = 0;
+}
+
+// Launch a captured graph on the library stream, fenced against the
+// context's stream on both sides.
+sph_status graph_launch(sph_ctx* c, cudaGraphExec_t g, int times)
+{
+    SPH_CU(cudaEventRecord(c->gev[0], c->st));
+    SPH_CU(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+    for (int k = 0; k < times; ++k) SPH_CU(cudaGraphLaunch(g, c->gst));
+    SPH_CU(cudaEventRecord(c->gev[1], c->gst));
+    SPH_CU(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+    return SPH_OK;
 }
 
 bool is_host_ptr(const void* p)
@@ -607,6 +637,55 @@ sph_status cot_out(sph_ctx* c, const double* src, double* dst)
     SPH_CU(cudaMemcpyAsync(dst, c->stage, 3 * n * sizeof(double), cudaMemcpyDefault, c->st));
     ++c->launches;
     return SPH_OK;
+}
+
+// One segment of the adjoint after the cotangents are in: nsteps forward
+// steps from the reloaded state that record the tape (with the step sizes
+// taken), then the reverse sweep over them.  No host work between the
+// launches, so the whole segment can be captured in one graph.
+sph_status adjoint_segment(sph_ctx* c, int nsteps)
+{
+    for (int t = 0; t < nsteps; ++t) {
+        SPH_CU(cudaMemcpyAsync(c->tape[t].dt, c->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        SPH_TRY(run_sort(c, 1, 0));
+        SPH_TRY(run_forces(c, 1, 1, 1));
+        SPH_TRY(save_tape(c, t));
+    }
+    AdjView& A = c->adj;
+    SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
+    for (int t = nsteps - 1; t >= 0; --t) {
+        SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), c->G, consts(c), A, 1, c->st));
+        c->launches += 4;
+    }
+    return SPH_OK;
+}
+
+// Capture adjoint_segment(nsteps) from the current state-set parity into a
+// graph on the library stream (same rules as graph_capture).
+void adjoint_capture(sph_ctx* c, int nsteps)
+{
+    if (c->astate == 1) cudaGraphExecDestroy(c->aexec);
+    c->astate = -1;
+    c->asteps = nsteps;
+    c->acur0 = c->cur;
+    if (!graph_stream(c)) return;
+    cudaStream_t user = c->st;
+    const int64_t l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        c->st = c->gst;
+        ok = adjoint_segment(c, nsteps) == SPH_OK;
+        c->st = user;
+        ok = cudaStreamEndCapture(c->gst, &g) == cudaSuccess && ok && g;
+    }
+    c->acur1 = c->cur;
+    c->cur = c->acur0;
+    c->alaunches = c->launches - l0;
+    c->launches = l0;
+    if (ok && cudaGraphInstantiate(&c->aexec, g, 0) == cudaSuccess) c->astate = 1;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
 }
 
 }  // namespace
@@ -786,14 +865,8 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps)
         const int par = c->cur;
         if (c->gstate[par] == 0) graph_capture(c, par);
         if (c->gstate[par] == 1) {
-            SPH_CU(cudaEventRecord(c->gev[0], c->st));
-            SPH_CU(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
-            for (int32_t k = 0; k + 1 < nsteps; k += 2) {
-                SPH_CU(cudaGraphLaunch(c->gexec[par], c->gst));
-                c->launches += c->glaunches[par];
-            }
-            SPH_CU(cudaEventRecord(c->gev[1], c->gst));
-            SPH_CU(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+            SPH_TRY(graph_launch(c, c->gexec[par], nsteps / 2));
+            c->launches += (int64_t)(nsteps / 2) * c->glaunches[par];
             nsteps &= 1;     // two steps per replay bring the sets back to this parity
         }
     }
@@ -1028,22 +1101,22 @@ sph_status sph_step_adjoint(sph_ctx* c, const double* x0, const double* v0, cons
     if (!c->have_state) return SPH_ERR_STATE;
     SPH_TRY(reload_state(c, x0, v0, a0, dr0));
     SPH_TRY(sph_build_cells(c));
-    for (int t = 0; t < nsteps; ++t) {
-        SPH_CU(cudaMemcpyAsync(c->tape[t].dt, c->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-        SPH_TRY(run_sort(c, 1, 0));
-        SPH_TRY(run_forces(c, 1, 1, 1));
-        SPH_TRY(save_tape(c, t));
-    }
     AdjView& A = c->adj;
-    SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
-    SPH_TRY(cot_in(c, xbar, A.xc));
+    SPH_TRY(cot_in(c, xbar, A.xc));      // the forward replay leaves the cotangents alone
     SPH_TRY(cot_in(c, vbar, A.vc));
     SPH_TRY(cot_in(c, abar, A.ac));
     SPH_TRY(cot_in(c, drbar, A.drc));
-    for (int t = nsteps - 1; t >= 0; --t) {
-        SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), c->G, consts(c), A, 1, c->st));
-        c->launches += 4;
+    bool replayed = false;
+    if (c->P.graphs && !c->prof_ev) {
+        if (c->astate == 0 || c->asteps != nsteps || c->acur0 != c->cur) adjoint_capture(c, nsteps);
+        if (c->astate == 1 && c->asteps == nsteps && c->acur0 == c->cur) {
+            SPH_TRY(graph_launch(c, c->aexec, 1));
+            c->launches += c->alaunches;
+            c->cur = c->acur1;
+            replayed = true;
+        }
     }
+    if (!replayed) SPH_TRY(adjoint_segment(c, nsteps));
     SPH_TRY(cot_out(c, A.xc, xbar));
     SPH_TRY(cot_out(c, A.vc, vbar));
     SPH_TRY(cot_out(c, A.ac, abar));
