@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
             }
         }
     };
-    for_candidates_rows<DIM>(oi, reach, cell_of[i], G, start, cell_of, pos4, visit);
+    for_candidates_rows<DIM, false>(oi, reach, cell_of[i], G, start, cell_of, pos4, visit);
     if (nbc) nbc[i] = cnt;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     vr[i] = make_double4_32a(vi[0], vi[1], vi[2], __dsub_rn(rho, K.rho0));

@@ -61,14 +61,17 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 // cell order, so the row is one run of particles (two runs across a periodic
 // x boundary).  The x shift and stencil code of a candidate come from its own
 // cell index (cell_of[j] - k_r = dx for every j of run r), so the walk has no
-// inner loop over the cell boundaries of a run.
+// inner loop over the cell boundaries of a run.  TWO: two candidates per
+// iteration, their loads issued together (the FP32 density pass; the FP64
+// pass, whose visit is larger, runs one at a time to stay within its
+// registers).
 // A row whose nearest y-z distance to particle i exceeds the reach (the
 // largest support radius of any pair of i) is skipped, and the x extent of a
 // row is cut to the cells within the remaining half-chord; every margin is
 // 1e-3 of a cell edge, far above FP32 rounding, so every candidate that the
 // full stencil would accept is still visited, in the same order.  About 2/3
 // of the 5^3 cells remain in 3-D.
-template <int DIM, typename F>
+template <int DIM, bool TWO = true, typename F>
 __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach, int cell_i, const Grid& G,
                                                     const int32_t* __restrict__ start,
                                                     const int32_t* __restrict__ cell_of,
@@ -141,13 +144,13 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                     f(j, code_row + (uint32_t)dx, pj, r2, rx, ry_, rz_);
                 };
                 int j = start[cell];
-                for (; j + 1 < jend; j += 2) {
+                for (; TWO && j + 1 < jend; j += 2) {
                     const float4 p0 = pos4[j], p1 = pos4[j + 1];
                     const int d0 = cell_of[j] - kr, d1 = cell_of[j + 1] - kr;
                     one(j, p0, d0);
                     one(j + 1, p1, d1);
                 }
-                if (j < jend) one(j, pos4[j], cell_of[j] - kr);
+                for (; j < jend; ++j) one(j, pos4[j], cell_of[j] - kr);
             }
         }
     }
