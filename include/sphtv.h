@@ -193,7 +193,11 @@ SPH_API sph_status sph_set_state(sph_ctx* ctx, const double* x, const double* v,
 
 /* Sort the loaded state into cells and run the density pass; when a/dr
  * were not given, also the force pass (a, dr from x and v).  Then compute
- * the diagnostics and the first dt (Eq. 9-11, or fixed_dt). */
+ * the diagnostics and the first dt (Eq. 9-11, or fixed_dt).  Kick-drift-kick
+ * with a and dr given: only the diagnostics and the first dt, which need
+ * neither cells nor densities; the first sph_step sorts the particles and
+ * runs the density pass as every step does, and sph_get_state with rho
+ * before any step sorts them and runs the density pass first. */
 SPH_API sph_status sph_build_cells(sph_ctx* ctx);
 
 /* Advance nsteps >= 0 steps on the context's stream: kick-drift-kick steps,

@@ -133,15 +133,18 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                 const int jend = start[cell + rn[r]];
                 auto one = [&](int j, const float4& pj, int dx) {
                     const float shx = -(float)dx * ex;
-                    const float rx = (oi[0] - pj.x) + shx;
-                    const float ry_ = (oi[1] - pj.y) + shy;
-                    float r2 = rx * rx + ry_ * ry_;
+                    // x and y in packed FP32x2 arithmetic (o_i - o_j as fma(o_j, -1, o_i): one rounding)
+                    const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
+                                                             make_float2(oi[0], oi[1])),
+                                                  make_float2(shx, shy));
+                    const float2 q = __fmul2_rn(rxy, rxy);
+                    float r2 = q.x + q.y;
                     float rz_ = 0.f;
                     if (DIM == 3) {
                         rz_ = (oi[2] - pj.z) + shz;
-                        r2 += rz_ * rz_;
+                        r2 = fmaf(rz_, rz_, r2);
                     }
-                    f(j, code_row + (uint32_t)dx, pj, r2, rx, ry_, rz_);
+                    f(j, code_row + (uint32_t)dx, pj, r2, rxy.x, rxy.y, rz_);
                 };
                 int j = start[cell];
                 for (; TWO && j + 1 < jend; j += 2) {

@@ -84,6 +84,11 @@ struct sph_ctx {
     uint32_t* err;
     double* stage;
     int have_state, have_cells, ad_given;
+    // kick-drift-kick, built with a and dr given: the state is still in the
+    // caller's order, with no cell list and no densities; the next step
+    // sorts it (its kick and drift need neither), sph_get_state(rho) sorts
+    // it and runs the density pass first
+    int cells_pending;
     int64_t launches;
     double host_dt;
     // adjoint (params.adjoint_steps > 0): tape slots, the per-particle
@@ -849,10 +854,24 @@ sph_status sph_build_cells(sph_ctx* c)
         c->have_cells = 1;
         return SPH_OK;
     }
-    sph_status s = run_sort(c, 0, c->ad_given);
+    if (c->ad_given) {
+        // a and dr given: only the diagnostics and dt_0 (from v and dr); the
+        // sort and the density pass are left to the first step, which does
+        // both itself
+        const int n = (int)c->n;
+        SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->G.sms, c->st));
+        SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt, 0,
+                               c->st));
+        c->launches += 2;
+        c->cells_pending = 1;
+        c->have_cells = 1;
+        return SPH_OK;
+    }
+    sph_status s = run_sort(c, 0, 0);
     if (s != SPH_OK) return s;
-    s = run_forces(c, 0, !c->ad_given, 0);
+    s = run_forces(c, 0, 1, 0);
     if (s != SPH_OK) return s;
+    c->cells_pending = 0;
     c->have_cells = 1;
     return SPH_OK;
 }
@@ -860,6 +879,7 @@ sph_status sph_build_cells(sph_ctx* c)
 sph_status sph_step(sph_ctx* c, int32_t nsteps)
 {
     if (!c || nsteps < 0) return SPH_ERR_ARG;
+    const int32_t nsteps_in = nsteps;
     if (!c->have_cells) return SPH_ERR_STATE;
     if (c->P.integrator == SPH_INT_KDK && c->P.graphs && !c->prof_ev && nsteps >= 2) {
         const int par = c->cur;
@@ -879,6 +899,7 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps)
         }
         if (c->prof_ev) ++c->prof_step;
     }
+    if (c->P.integrator == SPH_INT_KDK && nsteps_in > 0) c->cells_pending = 0;
     return SPH_OK;
 }
 
@@ -933,6 +954,15 @@ sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr
     if (!c->have_state) return SPH_ERR_STATE;
     const int n = (int)c->n;
     const size_t vb = 3 * (size_t)n * sizeof(double);
+    if (rho && c->have_cells && c->cells_pending) {
+        // built with a and dr given and not stepped yet: sort and run the
+        // density pass now (a and dr travel with the sort)
+        SPH_TRY(run_sort(c, 0, 1));
+        SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
+                              c->nbl, c->nbc, c->st));
+        ++c->launches;
+        c->cells_pending = 0;
+    }
     const StateSet<double>& Sd = c->set[c->cur].d;
     const void* sv = c->prec == 64 ? (void*)c->set[c->cur].d.v : (void*)c->set[c->cur].f.v;
     const void* sa = c->prec == 64 ? (void*)c->set[c->cur].d.a : (void*)c->set[c->cur].f.a;

@@ -329,3 +329,40 @@ def test_multistep_trajectory_and_decay_rates(tgv2d_traj):
     assert abs(rate64 / rate_orc - 1.0) < 1e-9
     assert abs(rate32 / rate64 - 1.0) < 1e-3               # FP32 decay rate within 1e-3 of FP64
     assert rate64 < 0 and math.isfinite(rate32)
+
+
+def _build_and_step(c, precision, ad, rho_first):
+    sim = sph.Simulation(c, precision=precision)
+    try:
+        if ad is None:
+            sim.set_state()
+        else:
+            sim.set_state(a=ad["a"], dr=ad["dr"])
+        sim.build_cells()
+        first = sim.get_state() if rho_first else None
+        d0 = sim.diag()
+        sim.step(3)
+        assert sim.sync() is None
+        return first, d0, sim.get_state(), sim.diag()
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_build_with_a_and_dr_given_leaves_the_sort_to_the_first_step(precision):
+    """With a and dr given, sph_build_cells computes only the diagnostics
+    and dt_0; the first step sorts the particles itself.  The densities
+    reported before any step (sorted on demand) and the states after three
+    steps are bit for bit those of a build that computed a and dr itself,
+    whether or not the densities were asked for first."""
+    c = cases.tgv2d(40, jitter_dp=0.05, seed=6)
+    full_first, full_d0, full_after, full_d = _build_and_step(c, precision, None, True)
+    ad = {"a": full_first["a"], "dr": full_first["dr"]}
+    lazy_first, lazy_d0, lazy_after, lazy_d = _build_and_step(c, precision, ad, True)
+    _, _, direct_after, _ = _build_and_step(c, precision, ad, False)
+    assert np.array_equal(lazy_first["rho"], full_first["rho"])
+    assert lazy_d0["dt_next"] == full_d0["dt_next"] and lazy_d0["vmax"] == full_d0["vmax"]
+    for k in ("x", "v", "a", "dr", "rho"):
+        assert np.array_equal(lazy_after[k], full_after[k]), k
+        assert np.array_equal(direct_after[k], full_after[k]), k
+    assert lazy_d["steps"] == full_d["steps"] == 3
