@@ -28,6 +28,38 @@ __global__ void k_vec_out(int n, const Real* __restrict__ src, const int32_t* __
     for (int d = 0; d < 3; ++d) dst3[o + d] = d < DIM ? (double)src[(size_t)d * n + k] : 0.0;
 }
 
+// pos[id[k]] = k: where the particle the caller gave as number i sits in
+// the cell order.
+__global__ void k_inverse_perm(int n, const int32_t* __restrict__ id, int32_t* __restrict__ pos)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) pos[id[k]] = k;
+}
+
+// k_vec_out by gathering: dst3 row i (the caller's order) from the sorted
+// position pos[i], so the writes of a warp are contiguous (the destination
+// may be page-locked host memory written across the host link).
+template <typename Real, int DIM>
+__global__ void k_vec_out_gather(int n, const Real* __restrict__ src, const int32_t* __restrict__ pos,
+                                 double* __restrict__ dst3)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const size_t k = (size_t)pos[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dst3[3 * (size_t)i + d] = d < DIM ? (double)src[(size_t)d * n + k] : 0.0;
+}
+
+template <typename V4>
+__global__ void k_rho_out_gather(int n, const V4* __restrict__ vr, const int8_t* __restrict__ kind,
+                                 const int32_t* __restrict__ pos, double rho0, double* __restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = pos[i];
+    dst[i] = kind[k] ? rho0 : rho0 + (double)vr[k].w;
+}
+
 template <typename Real, int DIM>
 __global__ void k_walls_velocity(int n, const int8_t* __restrict__ kind, const double* __restrict__ vw3,
                                  Real* __restrict__ v)
@@ -193,6 +225,35 @@ cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, 
 {
     if (prec == 64) k_rho_out<double4_32a><<<nblk(n, 256), 256, 0, st>>>(n, (const double4_32a*)vr, kind, id, rho0, dst);
     else k_rho_out<float4><<<nblk(n, 256), 256, 0, st>>>(n, (const float4*)vr, kind, id, rho0, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_perm(int n, const int32_t* id, int32_t* pos, cudaStream_t st)
+{
+    k_inverse_perm<<<nblk(n, 256), 256, 0, st>>>(n, id, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_out_gather(int prec, int dim, int n, const void* src, const int32_t* pos, double* dst3,
+                                  cudaStream_t st)
+{
+    const int T = 256;
+    if (prec == 64) {
+        if (dim == 2) k_vec_out_gather<double, 2><<<nblk(n, T), T, 0, st>>>(n, (const double*)src, pos, dst3);
+        else k_vec_out_gather<double, 3><<<nblk(n, T), T, 0, st>>>(n, (const double*)src, pos, dst3);
+    } else {
+        if (dim == 2) k_vec_out_gather<float, 2><<<nblk(n, T), T, 0, st>>>(n, (const float*)src, pos, dst3);
+        else k_vec_out_gather<float, 3><<<nblk(n, T), T, 0, st>>>(n, (const float*)src, pos, dst3);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_out_gather(int prec, int n, const void* vr, const int8_t* kind, const int32_t* pos,
+                                  double rho0, double* dst, cudaStream_t st)
+{
+    if (prec == 64)
+        k_rho_out_gather<double4_32a><<<nblk(n, 256), 256, 0, st>>>(n, (const double4_32a*)vr, kind, pos, rho0, dst);
+    else k_rho_out_gather<float4><<<nblk(n, 256), 256, 0, st>>>(n, (const float4*)vr, kind, pos, rho0, dst);
     return cudaGetLastError();
 }
 

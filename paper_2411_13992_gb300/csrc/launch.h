@@ -87,6 +87,13 @@ cudaError_t launch_walls_velocity(int prec, int dim, int n, const int8_t* kind, 
 cudaError_t launch_init_ids(int n, int32_t* id, cudaStream_t st);
 cudaError_t launch_sigma0(int dim, int n, const double* h, const double* m, double rho0, double* s0,
                           cudaStream_t st);
+// Output by gathering (coalesced writes in the caller's order): pos from
+// launch_inverse_perm of the sorted ids.
+cudaError_t launch_inverse_perm(int n, const int32_t* id, int32_t* pos, cudaStream_t st);
+cudaError_t launch_vec_out_gather(int prec, int dim, int n, const void* src, const int32_t* pos, double* dst3,
+                                  cudaStream_t st);
+cudaError_t launch_rho_out_gather(int prec, int n, const void* vr, const int8_t* kind, const int32_t* pos,
+                                  double rho0, double* dst, cudaStream_t st);
 cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, const int32_t* id, double rho0,
                            double* dst, cudaStream_t st);
 cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,

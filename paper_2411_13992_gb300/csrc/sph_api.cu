@@ -557,26 +557,59 @@ bool is_host_ptr(const void* p)
 
 // Load a state (caller order) with the per-particle constants of the last
 // sph_set_state.  a and dr may be NULL (then computed by the force pass).
+// Address through which this device's kernels can reach p directly: p for
+// memory of the current device (or managed memory), the mapped alias of
+// page-locked host memory; nullptr otherwise (pageable host memory, another
+// device), which then goes through the staging buffer by a copy.
+void* device_view(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (attr.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (attr.type == cudaMemoryTypeDevice) return attr.device == dev ? const_cast<void*>(p) : nullptr;
+    if (attr.type == cudaMemoryTypeHost && attr.devicePointer) return attr.devicePointer;
+    return nullptr;
+}
+
+// [n][3] rows of src (host or device) into the per-component array dst of
+// precision prec: read in place when the device can reach src (page-locked
+// host memory streams across the host link inside the conversion kernel),
+// else copied to the staging buffer first.
+sph_status vec_in(sph_ctx* c, int prec, const double* src, void* dst)
+{
+    const size_t n = (size_t)c->n;
+    const double* dv = (const double*)device_view(src);
+    if (!dv) {
+        SPH_CU(cudaMemcpyAsync(c->stage, src, 3 * n * sizeof(double), cudaMemcpyDefault, c->st));
+        dv = c->stage;
+    }
+    SPH_CU(launch_vec_in(prec, c->dim, (int)n, dv, dst, c->st));
+    ++c->launches;
+    return SPH_OK;
+}
+
 sph_status reload_state(sph_ctx* c, const double* x, const double* v, const double* a, const double* dr)
 {
     const size_t n = (size_t)c->n;
-    const size_t vb = 3 * n * sizeof(double);
     const size_t rs = c->prec == 64 ? 8 : 4;
     c->cur = 0;
     StateSet<double>& Sd = c->set[0].d;
     void* sv = c->prec == 64 ? (void*)c->set[0].d.v : (void*)c->set[0].f.v;
     void* sa = c->prec == 64 ? (void*)c->set[0].d.a : (void*)c->set[0].f.a;
     void* sdr = c->prec == 64 ? (void*)c->set[0].d.dr : (void*)c->set[0].f.dr;
-    SPH_CU(cudaMemcpyAsync(c->stage, x, vb, cudaMemcpyDefault, c->st));
-    SPH_CU(launch_vec_in(64, c->dim, (int)n, c->stage, Sd.x, c->st));
-    SPH_CU(cudaMemcpyAsync(c->stage, v, vb, cudaMemcpyDefault, c->st));
-    SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sv, c->st));
+    SPH_TRY(vec_in(c, 64, x, Sd.x));
+    SPH_TRY(vec_in(c, c->prec, v, sv));
     if (a) {
-        SPH_CU(cudaMemcpyAsync(c->stage, a, vb, cudaMemcpyDefault, c->st));
-        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sa, c->st));
-        SPH_CU(cudaMemcpyAsync(c->stage, dr, vb, cudaMemcpyDefault, c->st));
-        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sdr, c->st));
-        c->launches += 2;
+        SPH_TRY(vec_in(c, c->prec, a, sa));
+        SPH_TRY(vec_in(c, c->prec, dr, sdr));
     } else {
         SPH_CU(cudaMemsetAsync(sa, 0, c->dim * n * rs, c->st));
         SPH_CU(cudaMemsetAsync(sdr, 0, c->dim * n * rs, c->st));
@@ -587,7 +620,7 @@ sph_status reload_state(sph_ctx* c, const double* x, const double* v, const doub
     SPH_CU(cudaMemcpyAsync(Sd.kind, c->orig_kind, n, cudaMemcpyDeviceToDevice, c->st));
     SPH_CU(launch_walls_velocity(c->prec, c->dim, (int)n, Sd.kind, c->orig_vw, sv, c->st));
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
-    c->launches += 4;
+    c->launches += 2;
     c->have_state = 1;
     c->have_cells = 0;
     c->ad_given = a != nullptr;
@@ -796,16 +829,11 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     void* sdr = c->prec == 64 ? (void*)c->set[0].d.dr : (void*)c->set[0].f.dr;
     (void)S;
     const size_t rs = c->prec == 64 ? 8 : 4;
-    SPH_CU(cudaMemcpyAsync(c->stage, x, vb, cudaMemcpyDefault, c->st));
-    SPH_CU(launch_vec_in(64, c->dim, (int)n, c->stage, Sd.x, c->st));
-    SPH_CU(cudaMemcpyAsync(c->stage, v, vb, cudaMemcpyDefault, c->st));
-    SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sv, c->st));
+    SPH_TRY(vec_in(c, 64, x, Sd.x));
+    SPH_TRY(vec_in(c, c->prec, v, sv));
     if (a) {
-        SPH_CU(cudaMemcpyAsync(c->stage, a, vb, cudaMemcpyDefault, c->st));
-        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sa, c->st));
-        SPH_CU(cudaMemcpyAsync(c->stage, dr, vb, cudaMemcpyDefault, c->st));
-        SPH_CU(launch_vec_in(c->prec, c->dim, (int)n, c->stage, sdr, c->st));
-        c->launches += 2;
+        SPH_TRY(vec_in(c, c->prec, a, sa));
+        SPH_TRY(vec_in(c, c->prec, dr, sdr));
     } else {
         SPH_CU(cudaMemsetAsync(sa, 0, c->dim * n * rs, c->st));
         SPH_CU(cudaMemsetAsync(sdr, 0, c->dim * n * rs, c->st));
@@ -828,7 +856,7 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
     if (Sd.drho) SPH_CU(cudaMemsetAsync(Sd.drho, 0, n * rs, c->st));
-    c->launches += 5;
+    c->launches += 3;
     if (c->P.adjoint_steps > 0) {
         SPH_CU(cudaMemcpyAsync(c->orig_h, Sd.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         SPH_CU(cudaMemcpyAsync(c->orig_m, Sd.m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -967,20 +995,31 @@ sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr
     const void* sv = c->prec == 64 ? (void*)c->set[c->cur].d.v : (void*)c->set[c->cur].f.v;
     const void* sa = c->prec == 64 ? (void*)c->set[c->cur].d.a : (void*)c->set[c->cur].f.a;
     const void* sdr = c->prec == 64 ? (void*)c->set[c->cur].d.dr : (void*)c->set[c->cur].f.dr;
+    if (rho && !c->have_cells) return SPH_ERR_STATE;
     bool host = false;
     struct Out { double* dst; const void* src; int prec; } outs[4] = {{x, Sd.x, 64}, {v, sv, c->prec},
                                                                     {a, sa, c->prec}, {dr, sdr, c->prec}};
+    // rows in the caller's order, gathered from the sorted positions (pos in
+    // the scratch of the sort); written in place into device memory, and
+    // through the staging buffer and a copy into host memory (a copy reaches
+    // about 3x the rate of kernel stores across the host link)
+    int32_t* pos = c->perm_tmp;
+    if (x || v || a || dr || rho) {
+        SPH_CU(launch_inverse_perm(n, Sd.id, pos, c->st));
+        ++c->launches;
+    }
     for (auto& o : outs) {
         if (!o.dst) continue;
-        SPH_CU(launch_vec_out(o.prec, c->dim, n, o.src, Sd.id, c->stage, c->st));
-        SPH_CU(cudaMemcpyAsync(o.dst, c->stage, vb, cudaMemcpyDefault, c->st));
+        double* dv = is_host_ptr(o.dst) ? nullptr : (double*)device_view(o.dst);
+        SPH_CU(launch_vec_out_gather(o.prec, c->dim, n, o.src, pos, dv ? dv : c->stage, c->st));
+        if (!dv) SPH_CU(cudaMemcpyAsync(o.dst, c->stage, vb, cudaMemcpyDefault, c->st));
         ++c->launches;
         host = host || is_host_ptr(o.dst);
     }
     if (rho) {
-        if (!c->have_cells) return SPH_ERR_STATE;
-        SPH_CU(launch_rho_out(c->prec, n, c->vr, Sd.kind, Sd.id, c->P.rho0, c->stage, c->st));
-        SPH_CU(cudaMemcpyAsync(rho, c->stage, (size_t)n * sizeof(double), cudaMemcpyDefault, c->st));
+        double* dv = is_host_ptr(rho) ? nullptr : (double*)device_view(rho);
+        SPH_CU(launch_rho_out_gather(c->prec, n, c->vr, Sd.kind, pos, c->P.rho0, dv ? dv : c->stage, c->st));
+        if (!dv) SPH_CU(cudaMemcpyAsync(rho, c->stage, (size_t)n * sizeof(double), cudaMemcpyDefault, c->st));
         ++c->launches;
         host = host || is_host_ptr(rho);
     }
