@@ -101,6 +101,27 @@ __device__ __forceinline__ Real wendland_W(Real r, Real inv_h)
     return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * (t2 * t2) * (Real(2) * q + Real(1));
 }
 
+// W(r, h) for r < 2h with a_D h^-D given (wnorm = kernel_norm * pow_dim(1/h),
+// computed in that order): the same value as wendland_W.
+template <int DIM>
+__device__ __forceinline__ double wendland_W_scaled(double r, double inv_h, double wnorm)
+{
+    double q = r * inv_h;
+    double t = 1.0 - 0.5 * q;
+    double t2 = t * t;
+    return wnorm * (t2 * t2) * (2.0 * q + 1.0);
+}
+
+// dW/dr (r, h) for r < 2h with a_D h^-(D+1) given (dwnorm = kernel_norm *
+// pow_dim(1/h) * (1/h), in that order): the same value as wendland_dW.
+template <int DIM>
+__device__ __forceinline__ double wendland_dW_scaled(double r, double inv_h, double dwnorm)
+{
+    double q = r * inv_h;
+    double t = 1.0 - 0.5 * q;
+    return dwnorm * (-5.0 * q) * (t * t * t);
+}
+
 // dW/dr (r, h) for r < 2h.
 template <int DIM, typename Real>
 __device__ __forceinline__ Real wendland_dW(Real r, Real inv_h)

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
                                                      Grid G, Consts<double> K, double4_32a* __restrict__ vr,
                                                      const float4* __restrict__ pos4,
                                                      const int32_t* __restrict__ cell_of, uint32_t* __restrict__ nbl,
-                                                     int32_t* __restrict__ nbc, int cap)
+                                                     int32_t* __restrict__ nbc, int cap, double* __restrict__ inv_rho)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -62,33 +62,62 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     const double hi = S.h[i];
     const float4 pi = pos4[i];
     const float oi[3] = {pi.x, pi.y, pi.z};
+    const int cell_i = cell_of[i];
+    int ci[3];
+    cell_decode(G, cell_i, ci);
     // reach of the walk: the largest support radius 2 h_ij of i (h_j <= h_max)
     const float reach = (float)(2.0 * pair_h(K, hi, K.h_u));
+    // uniform resolution: h_ij = h for every pair, so the support, the
+    // prefilter bound and a_D h^-D are constants (the same values, computed
+    // once instead of per candidate on the FP64 pipe)
+    const bool uni = K.uniform_h != 0;
+    const double two_hu = 2.0 * K.h_u;
+    const float lim_u = (float)two_hu;
+    const float lim2_u = lim_u * lim_u * 1.0001f;
+    const double wnorm_u = kernel_norm<DIM, double>() * pow_dim<DIM, double>(K.inv_h_u);
     double sigma = 0.0;
     int cnt = 0;
     auto visit = [&](int j, uint32_t code, const float4&, float r2f, float, float, float) {
-        const double hij = pair_h(K, hi, S.h[j]);
-        const float lim = (float)(2.0 * hij);
-        if (!(r2f <= lim * lim * 1.0001f)) return;       // FP32 prefilter, 1e-4 margin
+        double hij = K.h_u;
+        float lim2 = lim2_u;
+        if (!uni) {
+            hij = pair_h(K, hi, S.h[j]);
+            const float lim = (float)(2.0 * hij);
+            lim2 = lim * lim * 1.0001f;
+        }
+        if (!(r2f <= lim2)) return;                      // FP32 prefilter, 1e-4 margin
+        // x_i - x_j with the periodic image of the stencil step (the nearest
+        // image of every neighbour: the same operations as min_image)
+        const int step[3] = {(int)(code % kSide) - kStencilR, (int)((code / kSide) % kSide) - kStencilR,
+                             (int)(code / (kSide * kSide)) - kStencilR};
         double r2 = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            double t = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+            double t = __dsub_rn(xi[d], S.x[(size_t)d * n + j]);
+            if (G.periodic[d]) {
+                const int sc = ci[d] + step[d];
+                if (sc >= G.nc[d]) t = __dsub_rn(t, G.L[d]);
+                else if (sc < 0) t = __dadd_rn(t, G.L[d]);
+            }
             r2 += t * t;
         }
         const double r = sqrt(r2);
-        if (r < 2.0 * hij) {
-            sigma += wendland_W<DIM, double>(r, K.uniform_h ? K.inv_h_u : 1.0 / hij);
+        if (r < (uni ? two_hu : 2.0 * hij)) {
+            sigma += uni ? wendland_W_scaled<DIM>(r, K.inv_h_u, wnorm_u) : wendland_W<DIM, double>(r, 1.0 / hij);
             if (nbl && j != i && r2 > 0.0) {
                 if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
                 ++cnt;
             }
         }
     };
-    for_candidates_rows<DIM, false>(oi, reach, cell_of[i], G, start, cell_of, pos4, visit);
+    for_candidates_rows<DIM, false>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
     if (nbc) nbc[i] = cnt;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
-    vr[i] = make_double4_32a(vi[0], vi[1], vi[2], __dsub_rn(rho, K.rho0));
+    const double w = __dsub_rn(rho, K.rho0);
+    vr[i] = make_double4_32a(vi[0], vi[1], vi[2], w);
+    // 1/rho_j for the force pass, once per particle instead of once per pair
+    // (the force pass's own expression: rho0 + w, then the division)
+    if (inv_rho) inv_rho[i] = 1.0 / (K.rho0 + w);
 }
 
 template <int DIM>
@@ -97,7 +126,8 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
                                                     const uint32_t* __restrict__ nbl, const int32_t* __restrict__ nbc,
                                                     int cap, const double* __restrict__ dt_ptr, int kick_on,
                                                     int write_ad, double* __restrict__ Rout,
-                                                    double* __restrict__ chi_out, double* __restrict__ partials)
+                                                    double* __restrict__ chi_out, double* __restrict__ partials,
+                                                    const double* __restrict__ inv_rho)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part[kNPart];
@@ -116,32 +146,58 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double inv_rho_i = 1.0 / rho_i;
         const double p_i = K.c2 * me.w;
         PlainD acc_a[DIM], acc_R[DIM];
-        // one neighbour j (j != i); returns without work outside the support
-        auto visit = [&](int j) {
+        // uniform resolution: h_ij = h for every pair, so the support bounds
+        // and a_D h^-(D+1) are constants (the same values, computed once)
+        const bool uni = K.uniform_h != 0;
+        const double far_u = 4.0 * K.h_u * K.h_u * (1.0 + 1e-12), two_hu = 2.0 * K.h_u;
+        const double dwnorm_u = kernel_norm<DIM, double>() * pow_dim<DIM, double>(K.inv_h_u) * K.inv_h_u;
+        // the cell of i (as the sort computed it from these positions)
+        const int ci[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
+        // one neighbour j (j != i); returns without work outside the support.
+        // code >= 0: the stencil step of j's cell (a list entry), which fixes
+        // the periodic image (the nearest one for every neighbour: the same
+        // operations as min_image); code < 0: min_image
+        auto visit = [&](int j, int code) {
             double rv[3] = {0, 0, 0};
             double r2 = 0.0;
+            const int step[3] = {code % kSide - kStencilR, (code / kSide) % kSide - kStencilR,
+                                 code / (kSide * kSide) - kStencilR};
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+                if (code >= 0) {
+                    double t = __dsub_rn(xi[d], S.x[(size_t)d * n + j]);
+                    if (G.periodic[d]) {
+                        const int sc = ci[d] + step[d];
+                        if (sc >= G.nc[d]) t = __dsub_rn(t, G.L[d]);
+                        else if (sc < 0) t = __dadd_rn(t, G.L[d]);
+                    }
+                    rv[d] = t;
+                } else {
+                    rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+                }
                 r2 += rv[d] * rv[d];
             }
-            const double hij = pair_h(K, hi, S.h[j]);
-            if (r2 > 4.0 * hij * hij * (1.0 + 1e-12)) return;   // far: no FP64 square root
+            const double hij = uni ? K.h_u : pair_h(K, hi, S.h[j]);
+            if (r2 > (uni ? far_u : 4.0 * hij * hij * (1.0 + 1e-12))) return;   // far: no FP64 square root
             if (!(r2 > 0.0)) return;
             const double inv_r = rsqrt(r2);
             const double r = r2 * inv_r;
-            if (!(r < 2.0 * hij)) return;
-            const double dw = wendland_dW<DIM, double>(r, K.uniform_h ? K.inv_h_u : 1.0 / hij);
+            if (!(r < (uni ? two_hu : 2.0 * hij))) return;
+            const double dw = uni ? wendland_dW_scaled<DIM>(r, K.inv_h_u, dwnorm_u)
+                                  : wendland_dW<DIM, double>(r, 1.0 / hij);
             double4_32a oj = vr[j];
             double vj[3] = {oj.x, oj.y, oj.z};
-            pair_force<double, DIM, PlainD>(K, rv, r, inv_r, dw, vi, rho_i, inv_rho_i, p_i, vj, oj.w, S.m[j], acc_a,
-                                            acc_R);
+            pair_force<double, DIM, PlainD>(K, rv, r, inv_r, dw, vi, rho_i, inv_rho_i, p_i, vj, oj.w, S.m[j],
+                                            inv_rho[j], acc_a, acc_R);
         };
         const int cnt = nbl ? nbc[i] : cap + 1;
         if (cnt <= cap) {
             // the density pass's list: the same neighbours in the same order as
             // the cell scan below, so the sums are bit-identical
-            for (int k = 0; k < cnt; ++k) visit((int)(nbl[(size_t)k * n + i] >> kCodeBits));
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t e = nbl[(size_t)k * n + i];
+                visit((int)(e >> kCodeBits), (int)(e & ((1u << kCodeBits) - 1u)));
+            }
         } else {
             int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
             const int SR = G.R, zr = DIM == 3 ? SR : 0;
@@ -156,7 +212,7 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
                         if (cx < 0) continue;
                         int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
                         for (int j = start[cell]; j < start[cell + 1]; ++j)
-                            if (j != i) visit(j);
+                            if (j != i) visit(j, -1);
                     }
                 }
             }
@@ -331,7 +387,7 @@ int pair_blocks(int prec, int n, int sms) { return nblk(n, pair_threads(prec, n,
 
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st)
+                           cudaStream_t st, double* inv_rho)
 {
     const int T = pair_threads(prec, n, G.sms);
     if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st);
@@ -339,16 +395,18 @@ cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* sta
     auto k = *(const Consts<double>*)K;
     const int cap = nbl_capacity(dim);
     if (dim == 2)
-        k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap);
+        k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap,
+                                                   inv_rho);
     else
-        k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap);
+        k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap,
+                                                   inv_rho);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
-                          void* Rout, void* chi, double* partials, cudaStream_t st)
+                          void* Rout, void* chi, double* partials, cudaStream_t st, const double* inv_rho)
 {
     const int T = pair_threads(prec, n, G.sms);
     if (prec == 32)
@@ -359,10 +417,10 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
     const int cap = nbl_capacity(dim);
     if (dim == 2)
         k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
-                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials);
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, inv_rho);
     else
         k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
-                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials);
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, inv_rho);
     return cudaGetLastError();
 }
 

@@ -33,17 +33,18 @@ __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
 }
 
 // Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, r = |rv|,
-// inv_r = 1/r, dw = W'(r, h_ij), inv_rho_i = 1/rho_i).  Adds into the
-// caller's accumulators.  One reciprocal per neighbour density serves both
-// V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU).
+// inv_r = 1/r, dw = W'(r, h_ij), inv_rho_i = 1/rho_i, inv_rho_j = 1/rho_j
+// computed once per particle by the density pass, unused for a wall j).
+// Adds into the caller's accumulators.  The one reciprocal of each density
+// serves both V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU).
 template <typename Real, int DIM, typename Acc>
 __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real inv_r, Real dw,
                                            const Real* vi, Real rho_i, Real inv_rho_i, Real p_i, const Real* vj,
-                                           Real w_j, Real m_j, Acc* acc_a, Acc* acc_R)
+                                           Real w_j, Real m_j, Real inv_rho_jd, Acc* acc_a, Acc* acc_R)
 {
     const bool wall = isinf(w_j);
     const Real rho_j = wall ? rho_i : K.rho0 + w_j;
-    const Real inv_rho_j = wall ? inv_rho_i : Real(1) / rho_j;
+    const Real inv_rho_j = wall ? inv_rho_i : inv_rho_jd;
     const Real p_j = wall ? p_i : K.c2 * w_j;
     Real ul = Real(0), ur = Real(0);
 #pragma unroll
