@@ -100,3 +100,40 @@ def test_isolated_particles_follow_the_parabola_in_one_advection_step():
     np.testing.assert_allclose(got["x"], x + v * Dt + 0.5 * g * Dt ** 2, rtol=0, atol=1e-13)
     np.testing.assert_allclose(got["v"], v + g * Dt, rtol=0, atol=1e-14)
     assert d["substeps"] >= 2
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_single_particle_falls_freely_with_its_self_density(precision):
+    """One particle (the smallest input the library takes): its density is
+    its own kernel value, rho0 W(0) / sigma0 with W(0) = 7 / (4 pi h^2) in
+    2-D (Wendland C2, Sec. 4); it has no neighbour, so no pressure, viscous
+    or correction term, and kick-drift-kick steps of fixed dt under gravity
+    land on the parabola x0 + v0 t + g t^2 / 2 (exact for a constant
+    acceleration)."""
+    h = 1.3
+    x = np.array([[4.0, 6.0, 0.0]])
+    v = np.array([[0.2, -0.1, 0.0]])
+    c = {"name": "single", "dim": 2, "n": 1, "x": x, "v": v, "h": np.full(1, h), "m": np.ones(1),
+         "kind": np.zeros(1, np.int8), "vw": np.zeros((1, 3)), "lo": (0.0, 0.0, 0.0), "L": (20.0, 20.0, 1.0),
+         "periodic": (0, 0, 0), "rho0": 1.0, "c": 10.0, "eta": 0.01, "g": (0.0, -0.5, 0.0), "h_min": h,
+         "h_max": h, "u_ref": 0.4}
+    dt, steps = 0.01, 10
+    sim = sph.Simulation(c, precision=precision, fixed_dt=dt)
+    try:
+        sim.set_state()
+        sim.build_cells()
+        rho0 = sim.get_state()["rho"][0]
+        sim.step(steps)
+        assert sim.sync() is None
+        got = sim.get_state()
+    finally:
+        sim.close()
+    s0 = oracle.sigma0_for(c, 2)[0]
+    w0 = 7.0 / (4.0 * np.pi * h * h)
+    tol = 1e-14 if precision == 64 else 1e-6
+    assert rho0 == pytest.approx(w0 / s0, rel=tol)
+    t = steps * dt
+    g = np.array([0.0, -0.5, 0.0])
+    np.testing.assert_allclose(got["x"], x + v * t + 0.5 * g * t * t, rtol=0, atol=1e-12 if precision == 64 else 1e-6)
+    np.testing.assert_allclose(got["v"], v + g * t, rtol=0, atol=1e-13 if precision == 64 else 1e-6)
+    assert np.abs(got["dr"]).max() == 0.0
