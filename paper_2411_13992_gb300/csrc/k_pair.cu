@@ -20,8 +20,9 @@
 // density, c_bar = c; h_ij = (h_i + h_j)/2 (or max); a wall j stands in with
 // rho_j = rho_i, p_j = p_i, V_j = m_j / rho_i and its prescribed velocity.
 //
-// FP64 form (this file): absolute FP64 positions, minimum image per pair,
-// plain sums.  FP32 form: k_pair32.cu.
+// FP64 form (this file): absolute FP64 positions, the nearest periodic
+// image of each pair (fixed by the stencil step of its cell), plain sums;
+// 1/rho_i once per particle.  FP32 form: k_pair32.cu.
 #include "common.cuh"
 #include "launch.h"
 #include "pair_physics.cuh"
