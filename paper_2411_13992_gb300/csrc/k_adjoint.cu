@@ -108,16 +108,18 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
 
 // Reverse of one pair term of a_i (Eq. 3, 5-7) and R_i (Eq. 14) for the pair
 // (i, j), given the cotangents Ai of a_i and Rbi of R_i.  rv = x_i - x_j,
-// r = |rv|, w = W'(r), w2 = W''(r); rho_j, p_j and vj are the stand-ins of
-// a wall neighbour when j is a wall.  Outputs: rb (cotangent of rv), dvb (of
-// v_i - v_j), rho_ib, rho_jb (of rho_i, rho_j), etab (of eta).
+// r = |rv|, inv_r = 1/r, w = W'(r), w2 = W''(r); rho_j, p_j and vj are the
+// stand-ins of a wall neighbour when j is a wall; inv_rho_i, inv_rho_j are
+// the reciprocals of the densities (each division once per pair or per
+// particle, not six times per call).  Outputs: rb (cotangent of rv), dvb
+// (of v_i - v_j), rho_ib, rho_jb (of rho_i, rho_j), etab (of eta).
 template <typename Real, int DIM>
-__device__ __forceinline__ void pair_adjoint(const Consts<Real>& K, const Real* rv, Real r, Real w, Real w2,
-                                             const Real* vi, Real rho_i, Real p_i, const Real* vj, Real rho_j,
-                                             Real p_j, Real m_j, const Real* Ai, const Real* Rbi, Real* rb, Real* dvb,
-                                             Real& rho_ib, Real& rho_jb, Real& etab)
+__device__ __forceinline__ void pair_adjoint(const Consts<Real>& K, const Real* rv, Real r, Real inv_r, Real w,
+                                             Real w2, const Real* vi, Real rho_i, Real inv_rho_i, Real p_i,
+                                             const Real* vj, Real rho_j, Real inv_rho_j, Real p_j, Real m_j,
+                                             const Real* Ai, const Real* Rbi, Real* rb, Real* dvb, Real& rho_ib,
+                                             Real& rho_jb, Real& etab)
 {
-    const Real inv_r = Real(1) / r;
     Real u[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
     Real udv = 0, Au = 0, Adv = 0, Ru = 0;
 #pragma unroll
@@ -136,8 +138,8 @@ __device__ __forceinline__ void pair_adjoint(const Consts<Real>& K, const Real* 
     const Real dbeta = (braw > Real(0) && braw < Real(1)) ? slope : Real(0);
     const Real rbar = Real(0.5) * (rho_i + rho_j);
     const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rbar * K.c * dU;
-    const Real Kf = m_j / (rho_i * rho_j);
-    const Real Vj = m_j / rho_j;
+    const Real Kf = m_j * (inv_rho_i * inv_rho_j);      // m_j / (rho_i rho_j)
+    const Real Vj = m_j * inv_rho_j;
     const Real wq = w * inv_r;
     const Real Pb = Real(-2) * Kf * w * Au;
     const Real Kb = Real(-2) * pstar * w * Au + K.two_eta * wq * Adv;
@@ -146,8 +148,8 @@ __device__ __forceinline__ void pair_adjoint(const Consts<Real>& K, const Real* 
     etab = Real(2) * Kf * wq * Adv;
     const Real dUb = Pb * Real(0.5) * rbar * K.c * (beta + dU * dbeta);
     const Real rbarb = Pb * Real(0.5) * beta * K.c * dU;
-    rho_ib = -Kf / rho_i * Kb + Real(0.5) * rbarb + K.c2 * Real(0.5) * Pb;
-    rho_jb = -Kf / rho_j * Kb + Real(0.5) * rbarb + K.c2 * Real(0.5) * Pb - Vj / rho_j * w * Ru;
+    rho_ib = -Kf * inv_rho_i * Kb + Real(0.5) * rbarb + K.c2 * Real(0.5) * Pb;
+    rho_jb = -Kf * inv_rho_j * Kb + Real(0.5) * rbarb + K.c2 * Real(0.5) * Pb - Vj * inv_rho_j * w * Ru;
     Real ub[3] = {0, 0, 0};
     Real uu = 0;
 #pragma unroll
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
         const Real vk[3] = {mk.x, mk.y, mk.z};
         const Real rho_k = K.rho0 + mk.w;
         const Real p_k = K.c2 * mk.w;
+        const Real inv_rho_k = Real(1) / rho_k;
         const Real m_k = (Real)T.m[k];
         Real Ak[3] = {0, 0, 0}, Rk[3] = {0, 0, 0};
         for (int d = 0; d < DIM; ++d) {
@@ -241,11 +244,13 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
             const Real vj[3] = {mj.x, mj.y, mj.z};
             const bool wall = isinf(mj.w);
             const Real rho_j = wall ? rho_k : K.rho0 + mj.w;
+            const Real inv_rho_j = wall ? inv_rho_k : Real(1) / rho_j;
             const Real p_j = wall ? p_k : K.c2 * mj.w;
+            const Real inv_r = Real(1) / r;
             Real rb[3], dvb[3], rib, rjb, eb;
             // k's own sums (k as i)
-            pair_adjoint<Real, DIM>(K, rv, r, w, w2, vk, rho_k, p_k, vj, rho_j, p_j, (Real)T.m[j], Ak, Rk, rb, dvb,
-                                    rib, rjb, eb);
+            pair_adjoint<Real, DIM>(K, rv, r, inv_r, w, w2, vk, rho_k, inv_rho_k, p_k, vj, rho_j, inv_rho_j, p_j,
+                                    (Real)T.m[j], Ak, Rk, rb, dvb, rib, rjb, eb);
             for (int d = 0; d < DIM; ++d) {
                 ax[d].add(rb[d]);
                 av[d].add(dvb[d]);
@@ -260,8 +265,8 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
                 Rj[d] = Rb[(size_t)d * n + j];
                 mrv[d] = -rv[d];
             }
-            pair_adjoint<Real, DIM>(K, mrv, r, w, w2, vj, rho_j, p_j, vk, rho_k, p_k, m_k, Aj, Rj, rb, dvb, rib, rjb,
-                                    eb);
+            pair_adjoint<Real, DIM>(K, mrv, r, inv_r, w, w2, vj, rho_j, inv_rho_j, p_j, vk, rho_k, inv_rho_k, p_k,
+                                    m_k, Aj, Rj, rb, dvb, rib, rjb, eb);
             for (int d = 0; d < DIM; ++d) {
                 ax[d].add(-rb[d]);
                 av[d].add(-dvb[d]);

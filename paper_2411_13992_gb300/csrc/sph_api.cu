@@ -972,6 +972,7 @@ sph_status sph_set_dt(sph_ctx* c, double dt)
 sph_status sph_set_eta(sph_ctx* c, double eta)
 {
     if (!c || !(eta >= 0) || !std::isfinite(eta)) return SPH_ERR_ARG;
+    if (eta == c->P.eta) return SPH_OK;    // unchanged: the captured graphs stay valid
     c->P.eta = eta;
     c->K64 = make_consts<double>(&c->P);
     c->K32 = make_consts<float>(&c->P);
