@@ -402,6 +402,9 @@ def run_native(args):
     # ---- adjoint / forward time on the adjoint workload
     adjoint = _adjoint_ratio(torch, sph, cases) if not args.no_adjoint else None
 
+    # ---- the other generated workloads (rank 0 of a single-GPU run only)
+    others = _other_configs(torch, sph, cases, args) if (world == 1 and not args.no_configs) else None
+
     # ---- rooflines of the two pair kernels (live event timing); the line's
     # "roofline" is the one that takes the larger share of the step
     peaks, src = _peaks()
@@ -462,6 +465,7 @@ def run_native(args):
             "kernels": kernels,
             "e2e": e2e,
             "adjoint": adjoint,
+            "other_configs": others,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -554,6 +558,30 @@ def _e2e(torch, sph, case, args, dist):
             "path": "sph_set_state (pinned host) + sph_build_cells + sph_step(1) + sph_get_state (pinned host)"}
 
 
+def _other_configs(torch, sph, cases, args):
+    """Throughput of the other generated workloads (device-resident, CUDA
+    events on the library stream, after 3 warm-up steps): the 2-D
+    Taylor-Green 50^2 (FP64), the lid-driven cavity 256^2 with its walls
+    (FP32 and FP64) and the variable-resolution cylinder (per-particle h,
+    FP32 and FP64).  Context for the headline workload, not bench lines."""
+    plan = [("2-D Taylor-Green 50^2 = 2,500 particles", cases.tgv2d(50), ((64, 200),)),
+            ("lid-driven cavity 256^2 fluid + 3 wall layers, U = 1", cases.cavity2d(256, U=1.0), ((32, 50), (64, 10))),
+            ("variable-resolution cylinder (h ratio 2, per-particle h, walls)", cases.cylinder2d(), ((32, 20), (64, 3)))]
+    out = []
+    for name, c, runs in plan:
+        for prec, k in runs:
+            sim = sph.Simulation(c, precision=prec)
+            sim.set_state()
+            sim.build_cells()
+            sim.step(3)
+            sim.sync()
+            ms, _ = _timed_steps(torch, sim, k, profile=False)
+            sim.close()
+            out.append({"workload": name, "particles": int(c["n"]), "precision": "FP%d" % prec, "steps": k,
+                        "ms_per_step": ms / k, "value": c["n"] * k / (ms * 1e-3), "unit": UNIT})
+    return out
+
+
 def _adjoint_ratio(torch, sph, cases):
     """Backward / forward time of a checkpointed rollout: 2-D Taylor-Green
     256^2 = 65,536 particles, 50 steps, checkpoints every 10 steps, loss =
@@ -604,6 +632,7 @@ def main():
     ap.add_argument("--ref-n", type=int, default=64, help="lattice side of the reference arm's per-step sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the throughput of the other generated workloads")
     ap.add_argument("--no-dual", action="store_true", help="skip the dual-criteria integrator timing")
     ap.add_argument("--dual-steps", type=int, default=10)
     args = ap.parse_args()
