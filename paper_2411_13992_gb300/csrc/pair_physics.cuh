@@ -46,14 +46,16 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
     const Real rho_j = wall ? rho_i : K.rho0 + w_j;
     const Real inv_rho_j = wall ? inv_rho_i : inv_rho_jd;
     const Real p_j = wall ? p_i : K.c2 * w_j;
-    Real ul = Real(0), ur = Real(0);
+    // U_l - U_r = (v_i - v_j).e_ij with e_ij = -rv / r: one dot product with
+    // the velocity difference, which the viscous term uses as well
+    Real dv[3] = {Real(0), Real(0), Real(0)};
+    Real dvr = Real(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        Real e = -rv[d] * inv_r;
-        ul += vi[d] * e;
-        ur += vj[d] * e;
+        dv[d] = vi[d] - vj[d];
+        dvr += dv[d] * rv[d];
     }
-    Real du = ul - ur;
+    const Real du = -dvr * inv_r;
     Real beta = K.beta_slope * (du * K.inv_c);
     beta = beta > Real(0) ? beta : Real(0);
     beta = beta < Real(1) ? beta : Real(1);
@@ -61,13 +63,13 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
     const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
     const Real inv_rr = inv_rho_i * inv_rho_j;
     const Real cp = Real(-2) * m_j * pstar * inv_rr;
-    const Real cv = K.two_eta * m_j * inv_rr * dw * inv_r;
-    const Real V_j = m_j * inv_rho_j;
     const Real dwr = dw * inv_r;
+    const Real cv = K.two_eta * m_j * inv_rr * dwr;
+    const Real V_j = m_j * inv_rho_j;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         Real gw = dwr * rv[d];
-        acc_a[d].add(cp * gw + cv * (vi[d] - vj[d]));
+        acc_a[d].add(cp * gw + cv * dv[d]);
         acc_R[d].add(V_j * gw);
     }
 }
