@@ -112,14 +112,13 @@ __device__ __forceinline__ double wendland_W_scaled(double r, double inv_h, doub
     return wnorm * (t2 * t2) * (2.0 * q + 1.0);
 }
 
-// dW/dr (r, h) for r < 2h with a_D h^-(D+1) given (dwnorm = kernel_norm *
-// pow_dim(1/h) * (1/h), in that order): the same value as wendland_dW.
+// W'(r)/r for r < 2h, given dwrnorm = -5 a_D h^-(D+2): W' = a_D h^-(D+1)
+// (-5 q) t^3 with q = r/h, t = 1 - q/2, and q / r = 1/h.
 template <int DIM>
-__device__ __forceinline__ double wendland_dW_scaled(double r, double inv_h, double dwnorm)
+__device__ __forceinline__ double wendland_dWr_scaled(double r, double inv_h, double dwrnorm)
 {
-    double q = r * inv_h;
-    double t = 1.0 - 0.5 * q;
-    return dwnorm * (-5.0 * q) * (t * t * t);
+    double t = 1.0 - 0.5 * (r * inv_h);
+    return dwrnorm * (t * t * t);
 }
 
 // dW/dr (r, h) for r < 2h.

@@ -32,13 +32,15 @@ __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
     return Real(0);
 }
 
-// Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, r = |rv|,
-// inv_r = 1/r, dw = W'(r, h_ij), inv_rho_i = 1/rho_i, inv_rho_j = 1/rho_j
-// computed once per particle by the density pass, unused for a wall j).
-// Adds into the caller's accumulators.  The one reciprocal of each density
-// serves both V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU).
+// Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, inv_r = 1/r,
+// dwr = W'(r, h_ij)/r, inv_rho_i = 1/rho_i, inv_rho_j = 1/rho_j computed
+// once per particle by the density pass, unused for a wall j).  Adds into
+// the caller's accumulators.  The one reciprocal of each density serves both
+// V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU); products of
+// constants (eta_R / c, c / 2) are written so that the compiler takes them
+// out of the neighbour loop.
 template <typename Real, int DIM, typename Acc>
-__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real r, Real inv_r, Real dw,
+__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real inv_r, Real dwr,
                                            const Real* vi, Real rho_i, Real inv_rho_i, Real p_i, const Real* vj,
                                            Real w_j, Real m_j, Real inv_rho_jd, Acc* acc_a, Acc* acc_R)
 {
@@ -56,14 +58,13 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
         dvr += dv[d] * rv[d];
     }
     const Real du = -dvr * inv_r;
-    Real beta = K.beta_slope * (du * K.inv_c);
+    Real beta = (K.beta_slope * K.inv_c) * du;
     beta = beta > Real(0) ? beta : Real(0);
     beta = beta < Real(1) ? beta : Real(1);
     const Real rhobar = Real(0.5) * (rho_i + rho_j);
-    const Real pstar = Real(0.5) * (p_i + p_j) + Real(0.5) * beta * rhobar * K.c * du;
+    const Real pstar = Real(0.5) * (p_i + p_j) + (Real(0.5) * K.c) * (beta * rhobar * du);
     const Real inv_rr = inv_rho_i * inv_rho_j;
     const Real cp = Real(-2) * m_j * pstar * inv_rr;
-    const Real dwr = dw * inv_r;
     const Real cv = K.two_eta * m_j * inv_rr * dwr;
     const Real V_j = m_j * inv_rho_j;
 #pragma unroll
