@@ -77,16 +77,9 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     const float lim2_u = lim_u * lim_u * 1.0001f;
     const double wnorm_u = kernel_norm<DIM, double>() * pow_dim<DIM, double>(K.inv_h_u);
     double sigma = 0.0;
-    int cnt = 0;
-    auto visit = [&](int j, uint32_t code, const float4&, float r2f, float, float, float) {
-        double hij = K.h_u;
-        float lim2 = lim2_u;
-        if (!uni) {
-            hij = pair_h(K, hi, S.h[j]);
-            const float lim = (float)(2.0 * hij);
-            lim2 = lim * lim * 1.0001f;
-        }
-        if (!(r2f <= lim2)) return;                      // FP32 prefilter, 1e-4 margin
+    // the exact FP64 test of a candidate that passed the FP32 prefilter: adds
+    // W to sigma; true for a force neighbour (j != i, 0 < r < 2 h_ij)
+    auto exact = [&](int j, uint32_t code, double hij) {
         // x_i - x_j with the periodic image of the stencil step (the nearest
         // image of every neighbour: the same operations as min_image)
         const int step[3] = {(int)(code % kSide) - kStencilR, (int)((code / kSide) % kSide) - kStencilR,
@@ -103,15 +96,65 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
             r2 += t * t;
         }
         const double r = sqrt(r2);
-        if (r < (uni ? two_hu : 2.0 * hij)) {
-            sigma += uni ? wendland_W_scaled<DIM>(r, K.inv_h_u, wnorm_u) : wendland_W<DIM, double>(r, 1.0 / hij);
-            if (nbl && j != i && r2 > 0.0) {
-                if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
-                ++cnt;
-            }
+        if (!(r < (uni ? two_hu : 2.0 * hij))) return false;
+        sigma += uni ? wendland_W_scaled<DIM>(r, K.inv_h_u, wnorm_u) : wendland_W<DIM, double>(r, 1.0 / hij);
+        return j != i && r2 > 0.0;
+    };
+    // FP32 prefilter bound (1e-4 margin) of the pair (i, j); pj_w = (float)h_j
+    // when h varies
+    const float hi_f = (float)hi;
+    auto prefilter2 = [&](float pj_w) {
+        if (uni) return lim2_u;
+        const float lim = 2.f * (K.h_pair_max ? fmaxf(hi_f, pj_w) : 0.5f * (hi_f + pj_w));
+        return lim * lim * 1.0001f;
+    };
+    int cnt = 0;
+    // one pass: the exact test inside the walk (the lanes whose candidate
+    // passed the prefilter run it while the others wait)
+    auto visit = [&](int j, uint32_t code, const float4&, float r2f, float, float, float) {
+        double hij = K.h_u;
+        float lim2 = lim2_u;
+        if (!uni) {
+            hij = pair_h(K, hi, S.h[j]);
+            const float lim = (float)(2.0 * hij);
+            lim2 = lim * lim * 1.0001f;
+        }
+        if (!(r2f <= lim2)) return;                      // FP32 prefilter, 1e-4 margin
+        if (exact(j, code, hij) && nbl) {
+            if (cnt < cap) nbl[(size_t)cnt * n + i] = ((uint32_t)j << kCodeBits) | code;
+            ++cnt;
         }
     };
-    for_candidates_rows<DIM, false>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
+    bool staged = false;
+    if (nbl) {
+        // two passes: the walk stages the candidates that pass the prefilter
+        // in the particle's list, then the exact FP64 test runs over them
+        // with every lane busy (the FP64 pipe serves a warp instruction
+        // whole, however few of its lanes are active), and the list is
+        // compacted in place to the force neighbours.  Same tests, in the
+        // same order, as the one pass.
+        int nf = 0;
+        uint32_t* lp = nbl + i;
+        auto stage = [&](int j, uint32_t code, const float4& pj, float r2f, float, float, float) {
+            if (!(r2f <= prefilter2(pj.w))) return;
+            if (nf < cap) {
+                *lp = ((uint32_t)j << kCodeBits) | code;
+                lp += n;
+            }
+            ++nf;
+        };
+        for_candidates_rows<DIM, false>(oi, reach, cell_i, G, start, cell_of, pos4, stage);
+        if (nf <= cap) {
+            staged = true;
+            for (int k = 0; k < nf; ++k) {
+                const uint32_t e = nbl[(size_t)k * n + i];
+                const int j = (int)(e >> kCodeBits);
+                const double hij = uni ? K.h_u : pair_h(K, hi, S.h[j]);
+                if (exact(j, e & ((1u << kCodeBits) - 1u), hij)) nbl[(size_t)cnt++ * n + i] = e;
+            }
+        }
+    }
+    if (!staged) for_candidates_rows<DIM, false>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
     if (nbc) nbc[i] = cnt;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     const double w = __dsub_rn(rho, K.rho0);
