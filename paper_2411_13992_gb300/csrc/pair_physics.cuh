@@ -63,15 +63,14 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
     beta = beta < Real(1) ? beta : Real(1);
     const Real rhobar = Real(0.5) * (rho_i + rho_j);
     const Real pstar = Real(0.5) * (p_i + p_j) + (Real(0.5) * K.c) * (beta * rhobar * du);
-    const Real inv_rr = inv_rho_i * inv_rho_j;
-    const Real cp = Real(-2) * m_j * pstar * inv_rr;
-    const Real cv = K.two_eta * m_j * inv_rr * dwr;
-    const Real V_j = m_j * inv_rho_j;
+    const Real mr = m_j * (inv_rho_i * inv_rho_j);         // m_j / (rho_i rho_j)
+    const Real cpw = Real(-2) * mr * pstar * dwr;          // pressure: cp W'/r
+    const Real cv = K.two_eta * mr * dwr;                  // viscous
+    const Real vw = m_j * inv_rho_j * dwr;                 // residual: V_j W'/r
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        Real gw = dwr * rv[d];
-        acc_a[d].add(cp * gw + cv * dv[d]);
-        acc_R[d].add(V_j * gw);
+        acc_a[d].add(cpw * rv[d] + cv * dv[d]);
+        acc_R[d].add(vw * rv[d]);
     }
 }
 
