@@ -486,11 +486,12 @@ def _pairs_per_launch(case) -> int:
     return case["n"] * 80
 
 
-def _profiled_traffic(kernel: str):
-    """DRAM bytes per launch of a pair kernel ("density" or "forces") from
-    the committed ncu summary (profiles/pair_traffic.json), or None when the
-    kernel sources have changed since those counters were taken (the summary
-    records a SHA-1 of the sources it was measured on)."""
+def _profiled_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of a pair kernel ("density" or "forces") for n
+    particles, from the committed ncu summary (profiles/pair_traffic.json,
+    captured at 96^3 = 884,736 particles and scaled by the particle count),
+    or None when the kernel sources have changed since those counters were
+    taken (the summary records a SHA-1 of the sources it was measured on)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "pair_traffic.json")
     try:
@@ -502,7 +503,7 @@ def _profiled_traffic(kernel: str):
                 h.update(f.read())
         if h.hexdigest() != d["source_sha1"]:
             return None
-        return d["kernels"][kernel]["dram_bytes_per_launch_full"]
+        return d["kernels"][kernel]["dram_bytes_per_launch_small"] * n / 884736.0
     except (OSError, ValueError, KeyError):
         return None
 
@@ -513,7 +514,7 @@ def _alu_roofline(name, kernel, prof, pairs, flops_per_pair, bytes_per_particle,
     achieved = pairs * flops_per_pair / avg_s / 1e12
     hbm = n * bytes_per_particle / avg_s / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": _profiled_traffic(name), "kernel": kernel,
+            "frac": achieved / peak_tflops, "traffic": _profiled_traffic(name, n), "kernel": kernel,
             "pairs_per_launch": pairs, "flops_per_pair": flops_per_pair, "avg_launch_ms": avg_s * 1e3,
             "hbm_algorithmic_gbs": hbm, "hbm_peak_gbs": hbm_gbs, "hbm_frac": hbm / hbm_gbs}
 
