@@ -56,7 +56,6 @@ struct DualK {
     StateSet<Real> S;
     typename V4<Real>::T* vr;
     float4* pos4;            // cell-relative offsets (the FP32 form's drifts keep them current), m or h
-    const int32_t* cell_of;  // FP32 form: home cell of the advection step
     const float* mf;         // FP32 form: masses
     const uint32_t* nbl;
     const int32_t* nbc;
@@ -197,20 +196,6 @@ __device__ __forceinline__ Real recip(Real x)
     else return rcp_approx(x);
 }
 
-// FP32 x offsets of particle i from its home cell's origin (as the permute forms them).
-template <int DIM>
-__device__ __forceinline__ void store_offsets(float4* pos4, const int32_t* cell_of, const Grid& G, int i,
-                                             const double* xs)
-{
-    int c[3];
-    cell_decode(G, cell_of[i], c);
-    float4 p = pos4[i];
-    float o[3] = {p.x, p.y, p.z};
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d] = (float)(xs[d] - (G.lo[d] + (double)c[d] * G.edge[d]));
-    pos4[i] = make_float4(o[0], o[1], o[2], p.w);
-}
-
 template <typename Real>
 __device__ __forceinline__ Real fma_free_add(Real a, Real b);
 template <> __device__ __forceinline__ double fma_free_add<double>(double a, double b) { return __dadd_rn(a, b); }
@@ -347,17 +332,28 @@ __global__ void __launch_bounds__(256) k_dual_first_half(DualK<Real> A, Grid G)
     w = fma_free_add<Real>(w, fma_free_mul<Real>((Real)hdt, dr));
     me.w = w;
     A.vr[i] = me;
-    double xs[3] = {0.0, 0.0, 0.0};
+    // FP32 form: the cell-relative offsets take the same displacement in
+    // FP32 (the permute recomputes them from the FP64 positions at the next
+    // advection step), which keeps the FP64 origin arithmetic off the
+    // substeps
+    float4 p = sizeof(Real) == 4 ? A.pos4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float of[3] = {p.x, p.y, p.z};
+    const float hdtf = (float)hdt;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const size_t o = (size_t)d * n + i;
+        const Real v = A.S.v[o];
         double x = A.S.x[o];
-        if (first) x = __dadd_rn(x, (double)A.S.dr[o]);
-        x = __dadd_rn(x, __dmul_rn(hdt, (double)A.S.v[o]));
+        if (first) {
+            const Real drd = A.S.dr[o];
+            x = __dadd_rn(x, (double)drd);
+            of[d] = __fadd_rn(of[d], (float)drd);
+        }
+        x = __dadd_rn(x, __dmul_rn(hdt, (double)v));
+        of[d] = __fmaf_rn(hdtf, (float)v, of[d]);
         A.S.x[o] = x;
-        xs[d] = x;
     }
-    if (sizeof(Real) == 4) store_offsets<DIM>(A.pos4, A.cell_of, G, i, xs);
+    if (sizeof(Real) == 4) A.pos4[i] = make_float4(of[0], of[1], of[2], p.w);
 }
 
 template <typename Real, int DIM, typename Acc, bool UNIFORM>
@@ -422,18 +418,20 @@ __global__ void __launch_bounds__(256) k_dual_drift(DualK<Real> A, Grid G)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || A.S.kind[i]) return;
     const double hdt = 0.5 * A.du[DU_DT];
-    double xs[3] = {0.0, 0.0, 0.0};
+    const float hdtf = (float)hdt;
+    float4 p = sizeof(Real) == 4 ? A.pos4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float of[3] = {p.x, p.y, p.z};
     Real v[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const size_t o = (size_t)d * n + i;
         v[d] = A.S.v[o];
-        xs[d] = __dadd_rn(A.S.x[o], __dmul_rn(hdt, (double)v[d]));
-        A.S.x[o] = xs[d];
+        A.S.x[o] = __dadd_rn(A.S.x[o], __dmul_rn(hdt, (double)v[d]));
+        of[d] = __fmaf_rn(hdtf, (float)v[d], of[d]);    // the offsets follow in FP32 (k_dual_first_half)
     }
     const Real w = A.vr[i].w;
     A.vr[i] = V4<Real>::make(v[0], v[1], v[2], w);
-    if (sizeof(Real) == 4) store_offsets<DIM>(A.pos4, A.cell_of, G, i, xs);
+    if (sizeof(Real) == 4) A.pos4[i] = make_float4(of[0], of[1], of[2], p.w);
 }
 
 template <typename Real, int DIM, typename Acc, bool UNIFORM>
@@ -597,7 +595,6 @@ DualK<Real> dual_k(const DualArgs& a)
     k.S = *(const StateSet<Real>*)a.S;
     k.vr = (typename V4<Real>::T*)a.vr;
     k.pos4 = a.pos4;
-    k.cell_of = a.cell_of;
     k.mf = a.mf;
     k.nbl = a.nbl;
     k.nbc = a.nbc;
