@@ -480,14 +480,23 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
         A.S.drho[i] = Real(2) * rho_i * s.value();
         // max |v| for the next substep size; the other diagnostics only after
         // the last substep of the advection step (FP64 is 1/74 of the FP32 rate)
-        double v2 = 0.0;
+        // |v|^2 in the precision of v for the substep's max |v|; in FP64 for the
+        // kinetic energy after the last substep
+        Real v2r = Real(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const double v = (double)A.S.v[(size_t)d * n + i];
-            v2 += v * v;
+            const Real v = A.S.v[(size_t)d * n + i];
+            v2r += v * v;
         }
-        part[6] = v2;                 // squares: block_partials takes the roots
+        part[6] = (double)v2r;        // squares: block_partials takes the roots
         if (A.du[DU_LAST] != 0.0) {
+            double v2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const double v = (double)A.S.v[(size_t)d * n + i];
+                v2 += v * v;
+            }
+            part[6] = v2;
             const double inv_Dt = 1.0 / A.du[DU_DT_AD];
             const double m_i = A.S.m[i];
             double vt2 = 0.0, dr2 = 0.0;
@@ -510,7 +519,9 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
     } else if (i < n) {
         A.S.drho[i] = Real(0);
     }
-    block_partials<true>(part, A.partials + (size_t)blockIdx.x * kNPart);
+    // the sums (mass, momentum, KE) only after the last substep: in the others
+    // they are all zero, and their FP64 shuffles would cost every substep
+    block_partials<true>(part, A.partials + (size_t)blockIdx.x * kNPart, A.du[DU_LAST] != 0.0);
 }
 
 // Reduce the substep's partials (in a fixed order); advance t; pick the next

@@ -84,22 +84,29 @@ __device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv
 // order.  With FIRST the flags are counted with a ballot and the maxima of
 // the non-negative squares are integer maxima of their bit patterns (a NaN
 // counts as 0, as fmax ignores it), which keeps both off the FP64 pipe
-// (1/64 of the FP32 rate on this part).
+// (1/64 of the FP32 rate on this part).  sums = false (the same for every
+// thread of the grid) when the caller's sums are all zero: they are skipped.
 template <bool FIRST>
-__device__ __forceinline__ void block_partials(double* vals, double* out_block)
+__device__ __forceinline__ void block_partials(double* vals, double* out_block, bool sums = true)
 {
     __shared__ double sh[32][kNPart];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     constexpr int kSums = FIRST ? 5 : 9;
+    if (FIRST && !sums) {
+        // the caller's sums are all zero (uniform over the grid): skip them
+        if (lane == 0)
+            for (int k = 0; k < 5; ++k) sh[w][k] = 0.0;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kSums; ++k) {
-        double x = vals[k];
+        for (int k = 0; k < kSums; ++k) {
+            double x = vals[k];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double y = __shfl_down_sync(0xffffffffu, x, off);
-            x = (k >= 6 && k <= 8) ? fmax(x, y) : x + y;
+            for (int off = 16; off > 0; off >>= 1) {
+                double y = __shfl_down_sync(0xffffffffu, x, off);
+                x = (k >= 6 && k <= 8) ? fmax(x, y) : x + y;
+            }
+            if (lane == 0) sh[w][k] = x;
         }
-        if (lane == 0) sh[w][k] = x;
     }
     if (FIRST) {
         const unsigned flags = __ballot_sync(0xffffffffu, __double_as_longlong(vals[5]) != 0);
