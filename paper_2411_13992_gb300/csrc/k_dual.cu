@@ -478,10 +478,10 @@ __global__ void __launch_bounds__(sizeof(Real) == 8 ? 256 : 128) k_dual_continui
         };
         for_list<Real, DIM>(A, G, tab, i, cnt, pair);
         A.S.drho[i] = Real(2) * rho_i * s.value();
-        // max |v| for the next substep size; the other diagnostics only after
-        // the last substep of the advection step (FP64 is 1/74 of the FP32 rate)
-        // |v|^2 in the precision of v for the substep's max |v|; in FP64 for the
-        // kinetic energy after the last substep
+        // max |v| for the next substep size, from |v|^2 in the precision of v;
+        // the other diagnostics (and |v|^2 in FP64 for the kinetic energy) only
+        // after the last substep of the advection step (FP64 is 1/74 of the
+        // FP32 rate)
         Real v2r = Real(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
