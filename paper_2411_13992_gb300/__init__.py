@@ -166,6 +166,9 @@ def _check(status: int, where: str) -> None:
 
 # ------------------------------------------------------------------ marshalling
 
+_ASYNC_TEMP = object()   # marker in a keep list: a temporary read after the call returns
+
+
 def _ptr(a, keep: list, dtype, shape_tail=None):
     """Pointer to a contiguous array of ``dtype`` (numpy or torch), or None."""
     if a is None:
@@ -178,6 +181,11 @@ def _ptr(a, keep: list, dtype, shape_tail=None):
             if shape_tail == 3 and t.dim() == 2 and t.shape[1] == 2:
                 t = torch.nn.functional.pad(t, (0, 1))
             keep.append(t)
+            if t.data_ptr() != a.data_ptr() and (t.is_cuda or t.is_pinned()):
+                # a converted copy that the library reads asynchronously (in
+                # place, or by an asynchronous copy): the caller of the ABI
+                # wrapper waits for the stream before it is dropped
+                keep.append(_ASYNC_TEMP)
             return t.data_ptr()
     except ImportError:
         pass
@@ -215,6 +223,8 @@ def sph_set_state(ctx, x, v, a=None, dr=None, h=None, m=None, kind=None, vw=None
             _ptr(dr, keep, np.float64, 3), _ptr(h, keep, np.float64), _ptr(m, keep, np.float64),
             _ptr(kind, keep, np.int8), _ptr(vw, keep, np.float64, 3), _ptr(sigma0, keep, np.float64)]
     _check(load().sph_set_state(ctx, *[_vp(p) if p else None for p in args]), "sph_set_state")
+    if any(k is _ASYNC_TEMP for k in keep):
+        sph_sync(ctx)            # the converted copies must outlive the stream work that reads them
 
 
 def sph_build_cells(ctx) -> None:
