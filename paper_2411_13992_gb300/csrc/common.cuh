@@ -178,9 +178,21 @@ struct PlainD {
 // saturates large values and maps NaN to 0 (the kick-drift kernel flags
 // non-finite positions separately).  Two FP64 operations and a conversion:
 // GB300's FP64 pipe is narrow.
+// Order key of a double on the integer ALU: for non-NaN a and b, a < b
+// exactly when dkey(a) < dkey(b) (the magnitude bits of negative values
+// inverted, -0.0 folded onto +0.0), which keeps comparisons off the FP64 pipe.
+__device__ __forceinline__ long long dkey(double a)
+{
+    long long k = __double_as_longlong(a);
+    if (k == (long long)0x8000000000000000ULL) k = 0;
+    return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
+
 __device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
 {
-    const int c = __double2int_rz(__dsub_rn(x, G.lo[d]) * G.inv_edge[d]);
+    // x - lo is x itself when lo = 0 (bit for bit), one FP64 operation fewer
+    const double t = G.lo[d] == 0.0 ? x : __dsub_rn(x, G.lo[d]);
+    const int c = __double2int_rz(t * G.inv_edge[d]);
     return min(max(c, 0), G.nc[d] - 1);
 }
 

@@ -48,8 +48,9 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
         for (int d = 0; d < DIM; ++d) {
             if (!G.periodic[d]) continue;
             double xn = xs[d];
-            if (xn < G.lo[d]) xn = __dadd_rn(xn, G.L[d]);
-            else if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
+            const long long kx = dkey(xn);
+            if (kx < dkey(G.lo[d])) xn = __dadd_rn(xn, G.L[d]);
+            else if (kx >= dkey(G.hi[d])) xn = __dsub_rn(xn, G.L[d]);
             if (xn != xs[d]) S.x[(size_t)d * n + i] = xn;
             xs[d] = xn;
         }
@@ -63,8 +64,10 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
             S.v[o] = vh;
             double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, (double)vh)), (double)S.dr[o]);
             if (G.periodic[d]) {
-                if (xn < G.lo[d]) xn = __dadd_rn(xn, G.L[d]);
-                else if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
+                // xn < lo, xn >= hi as integer comparisons (dkey)
+                const long long kx = dkey(xn);
+                if (kx < dkey(G.lo[d])) xn = __dadd_rn(xn, G.L[d]);
+                else if (kx >= dkey(G.hi[d])) xn = __dsub_rn(xn, G.L[d]);
             }
             xs[d] = xn;
             S.x[o] = xn;
@@ -73,7 +76,7 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         if (!finite_bits(xs[d])) e |= ERRB_NAN;
-        else if (!G.periodic[d] && (xs[d] < G.lo[d] || xs[d] > G.hi[d])) e |= ERRB_DOMAIN;
+        else if (!G.periodic[d] && (dkey(xs[d]) < dkey(G.lo[d]) || dkey(xs[d]) > dkey(G.hi[d]))) e |= ERRB_DOMAIN;
     }
     if (e) atomicOr(err, e);
     int k = cell_index<DIM>(G, xs);
