@@ -188,11 +188,47 @@ __device__ __forceinline__ long long dkey(double a)
     return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
 }
 
+// The value of a float as a double, exactly, on the integer ALU (IEEE 754
+// binary32 -> binary64: same sign, exponent rebased by 1023 - 127, fraction
+// shifted by 52 - 23; zero keeps its sign); subnormal, infinite and NaN
+// floats take the hardware conversion.  Keeps the conversion off the FP64
+// pipe, which the position update saturates.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0u) {
+        if ((u & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
+        return (double)f;
+    }
+    if (e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// max(trunc(t), 0) on the integer ALU for the cell index (the callers clamp
+// it to [0, nc - 1]), as the hardware conversion toward zero then the clamp
+// would give it: 0 for t < 1 (and -0.0, negative t, NaN), the integer part
+// read from the binary64 fraction for 1 <= t < 2^31, INT_MAX beyond.
+__device__ __forceinline__ int trunc_nonneg(double t)
+{
+    const long long b = __double_as_longlong(t);
+    if (b < 0) return 0;
+    const int E = (int)((b >> 52) & 0x7ff) - 1023;
+    if (E < 0) return 0;
+    if (E == 1024 && (b & 0xfffffffffffffLL) != 0) return 0;     // NaN
+    if (E > 30) return 0x7fffffff;
+    const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+    return (int)(m >> (52 - E));
+}
+
 __device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
 {
-    // x - lo is x itself when lo = 0 (bit for bit), one FP64 operation fewer
+    // x - lo is x itself when lo = 0 (bit for bit), one FP64 operation fewer;
+    // the truncation (toward zero, then clamped) on the integer ALU
     const double t = G.lo[d] == 0.0 ? x : __dsub_rn(x, G.lo[d]);
-    const int c = __double2int_rz(t * G.inv_edge[d]);
+    const int c = trunc_nonneg(t * G.inv_edge[d]);
     return min(max(c, 0), G.nc[d] - 1);
 }
 

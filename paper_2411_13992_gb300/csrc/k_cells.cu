@@ -31,6 +31,10 @@ __device__ __forceinline__ float kick<float>(float v, double hdt, float a)
     return __fadd_rn(v, __fmul_rn((float)hdt, a));
 }
 
+// FP64 value of a velocity or displacement component (exact either way).
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_exact(x); }
+
 template <typename Real, int DIM>
 __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restrict__ dt_ptr, int drift, Grid G,
                                  int32_t* __restrict__ key, int32_t* __restrict__ count, uint32_t* err)
@@ -62,7 +66,7 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
             size_t o = (size_t)d * n + i;
             Real vh = kick<Real>(S.v[o], hdt, S.a[o]);
             S.v[o] = vh;
-            double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, (double)vh)), (double)S.dr[o]);
+            double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(S.dr[o]));
             if (G.periodic[d]) {
                 // xn < lo, xn >= hi as integer comparisons (dkey)
                 const long long kx = dkey(xn);
