@@ -188,7 +188,6 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
         const double hi = S.h[i];
         const double rho_i = K.rho0 + me.w;
         const double inv_rho_i = 1.0 / rho_i;
-        const double p_i = K.c2 * me.w;
         PlainD acc_a[DIM], acc_R[DIM];
         // uniform resolution: h_ij = h for every pair, so the support bounds
         // and -5 a_D h^-(D+2) are constants
@@ -198,18 +197,34 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
                                  K.inv_h_u;
         // the cell of i (as the sort computed it from these positions)
         const int ci[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
-        // one neighbour j (j != i); returns without work outside the support.
-        // code >= 0: the stencil step of j's cell (a list entry), which fixes
-        // the periodic image (the nearest one for every neighbour: the same
-        // operations as min_image); code < 0: min_image
-        auto visit = [&](int j, int code) {
-            double rv[3] = {0, 0, 0};
-            double r2 = 0.0;
-            const int step[3] = {code % kSide - kStencilR, (code / kSide) % kSide - kStencilR,
-                                 code / (kSide * kSide) - kStencilR};
+        const PairI64 I = pair_i64(K, me.w, inv_rho_i);
+        // a neighbour j (0 < r < 2 h_ij) at rv = x_i - x_j, r2 = |rv|^2
+        auto body = [&](int j, const double* rv, double r2) {
+            const double inv_r = rsqrt(r2);
+            const double r = r2 * inv_r;
+            const double dwr = uni ? wendland_dWr_scaled<DIM>(r, K.inv_h_u, dwrnorm_u)
+                                   : wendland_dW<DIM, double>(r, 1.0 / pair_h(K, hi, S.h[j])) * inv_r;
+            const double4_32a oj = vr[j];
+            const double vj[3] = {oj.x, oj.y, oj.z};
+            pair_force64<DIM>(K, I, rv, inv_r, dwr, vi, vj, oj.w, S.m[j], inv_rho[j], acc_a, acc_R);
+        };
+        const int cnt = nbl ? nbc[i] : cap + 1;
+        if (cnt <= cap) {
+            // the density pass's list: exactly the pairs with 0 < r < 2 h_ij
+            // (its exact FP64 test), in the order of the cell scan below, so
+            // no test is repeated here.  The stencil step of j's cell fixes
+            // the periodic image (the nearest one for every neighbour: the
+            // same operations as min_image).
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t e = nbl[(size_t)k * n + i];
+                const int j = (int)(e >> kCodeBits);
+                const int code = (int)(e & ((1u << kCodeBits) - 1u));
+                const int step[3] = {code % kSide - kStencilR, (code / kSide) % kSide - kStencilR,
+                                     code / (kSide * kSide) - kStencilR};
+                double rv[3] = {0, 0, 0};
+                double r2 = 0.0;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                if (code >= 0) {
+                for (int d = 0; d < DIM; ++d) {
                     double t = __dsub_rn(xi[d], S.x[(size_t)d * n + j]);
                     if (G.periodic[d]) {
                         const int sc = ci[d] + step[d];
@@ -217,47 +232,39 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
                         else if (sc < 0) t = __dadd_rn(t, G.L[d]);
                     }
                     rv[d] = t;
-                } else {
-                    rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+                    r2 += t * t;
                 }
-                r2 += rv[d] * rv[d];
-            }
-            const double hij = uni ? K.h_u : pair_h(K, hi, S.h[j]);
-            if (r2 > (uni ? far_u : 4.0 * hij * hij * (1.0 + 1e-12))) return;   // far: no FP64 square root
-            if (!(r2 > 0.0)) return;
-            const double inv_r = rsqrt(r2);
-            const double r = r2 * inv_r;
-            if (!(r < (uni ? two_hu : 2.0 * hij))) return;
-            const double dwr = uni ? wendland_dWr_scaled<DIM>(r, K.inv_h_u, dwrnorm_u)
-                                   : wendland_dW<DIM, double>(r, 1.0 / hij) * inv_r;
-            double4_32a oj = vr[j];
-            double vj[3] = {oj.x, oj.y, oj.z};
-            pair_force<double, DIM, PlainD>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, vj, oj.w, S.m[j],
-                                            inv_rho[j], acc_a, acc_R);
-        };
-        const int cnt = nbl ? nbc[i] : cap + 1;
-        if (cnt <= cap) {
-            // the density pass's list: the same neighbours in the same order as
-            // the cell scan below, so the sums are bit-identical
-            for (int k = 0; k < cnt; ++k) {
-                const uint32_t e = nbl[(size_t)k * n + i];
-                visit((int)(e >> kCodeBits), (int)(e & ((1u << kCodeBits) - 1u)));
+                body(j, rv, r2);
             }
         } else {
-            int c[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
+            // no list (or more neighbours than it holds): scan the cells with
+            // the minimum image and the support test
             const int SR = G.R, zr = DIM == 3 ? SR : 0;
             for (int dz = -zr; dz <= zr; ++dz) {
-                int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+                int cz = DIM == 3 ? cell_step(G, ci[2], dz, 2) : 0;
                 if (cz < 0) continue;
                 for (int dy = -SR; dy <= SR; ++dy) {
-                    int cy = cell_step(G, c[1], dy, 1);
+                    int cy = cell_step(G, ci[1], dy, 1);
                     if (cy < 0) continue;
                     for (int dx = -SR; dx <= SR; ++dx) {
-                        int cx = cell_step(G, c[0], dx, 0);
+                        int cx = cell_step(G, ci[0], dx, 0);
                         if (cx < 0) continue;
                         int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                        for (int j = start[cell]; j < start[cell + 1]; ++j)
-                            if (j != i) visit(j, -1);
+                        for (int j = start[cell]; j < start[cell + 1]; ++j) {
+                            if (j == i) continue;
+                            double rv[3] = {0, 0, 0};
+                            double r2 = 0.0;
+#pragma unroll
+                            for (int d = 0; d < DIM; ++d) {
+                                rv[d] = min_image(G, xi[d], S.x[(size_t)d * n + j], d);
+                                r2 += rv[d] * rv[d];
+                            }
+                            const double hij = uni ? K.h_u : pair_h(K, hi, S.h[j]);
+                            if (r2 > (uni ? far_u : 4.0 * hij * hij * (1.0 + 1e-12))) continue;
+                            if (!(r2 > 0.0)) continue;
+                            if (!(sqrt(r2) < (uni ? two_hu : 2.0 * hij))) continue;
+                            body(j, rv, r2);
+                        }
                     }
                 }
             }

@@ -36,7 +36,7 @@ __device__ __forceinline__ float support2(const Consts<float>& K, float hi, floa
 }
 
 // One neighbour's contribution to a_i and R_i in the FP32 form, given
-// rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force
+// rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force64
 // (Eq. 3, 5-7, 14) arranged for FP32 throughput -- W' only enters through
 // W'/r, (U_l - U_r) = -(v_i - v_j).r_ij / r, and each density is inverted
 // once (1/(rho_i rho_j) = (1/rho_i)(1/rho_j), V_j = m_j/rho_j).

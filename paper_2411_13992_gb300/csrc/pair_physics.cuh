@@ -1,8 +1,9 @@
-// pair_physics.cuh -- the per-pair arithmetic of the method, shared by the
-// FP64 and FP32 pair kernels: pair smoothing length, the transport-velocity
-// limiter (Eq. 15), one neighbour's contribution to the pressure (Eq. 3,
-// 5-6) and viscous (Eq. 7) accelerations and to the residual of Eq. 14, and
-// the block reduction of the FP64 diagnostics partials.
+// pair_physics.cuh -- per-pair arithmetic of the method used by the pair
+// kernels: pair smoothing length, the transport-velocity limiter (Eq. 15),
+// one neighbour's contribution to the pressure (Eq. 3, 5-6) and viscous
+// (Eq. 7) accelerations and to the residual of Eq. 14 in the FP64 form (the
+// FP32 form is pair_force32 in k_pair32.cu), and the block reduction of the
+// FP64 diagnostics partials.
 //
 // Readings of the paper: e_ij points from i to j (Riemann states U_l, U_r);
 // grad W_ij is grad_i W_ij = W'(r) (x_i - x_j)/r; V_j = m_j / rho_j;
@@ -32,45 +33,75 @@ __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
     return Real(0);
 }
 
-// Contribution of neighbour j to a_i and R_i (rv = x_i - x_j, inv_r = 1/r,
-// dwr = W'(r, h_ij)/r, inv_rho_i = 1/rho_i, inv_rho_j = 1/rho_j computed
-// once per particle by the density pass, unused for a wall j).  Adds into
-// the caller's accumulators.  The one reciprocal of each density serves both
-// V_j and 1/(rho_i rho_j) (FP64 division is costly on this GPU); products of
-// constants (eta_R / c, c / 2) are written so that the compiler takes them
-// out of the neighbour loop.
-template <typename Real, int DIM, typename Acc>
-__device__ __forceinline__ void pair_force(const Consts<Real>& K, const Real* rv, Real inv_r, Real dwr,
-                                           const Real* vi, Real rho_i, Real inv_rho_i, Real p_i, const Real* vj,
-                                           Real w_j, Real m_j, Real inv_rho_jd, Acc* acc_a, Acc* acc_R)
+// Per-particle values of i shared by all pairs of i in the FP64 force pass.
+struct PairI64 {
+    double w;          // rho_i - rho0
+    double inv_rho;    // 1 / rho_i
+    double rho_half;   // rho0 + w / 2, so that rho_bar = rho_half + w_j / 2
+    double m2_ir;      // -2 / rho_i
+    double eta_ir;     // 2 eta / rho_i
+};
+
+__device__ __forceinline__ PairI64 pair_i64(const Consts<double>& K, double w, double inv_rho)
 {
-    const bool wall = isinf(w_j);
-    const Real rho_j = wall ? rho_i : K.rho0 + w_j;
-    const Real inv_rho_j = wall ? inv_rho_i : inv_rho_jd;
-    const Real p_j = wall ? p_i : K.c2 * w_j;
-    // U_l - U_r = (v_i - v_j).e_ij with e_ij = -rv / r: one dot product with
-    // the velocity difference, which the viscous term uses as well
-    Real dv[3] = {Real(0), Real(0), Real(0)};
-    Real dvr = Real(0);
+    PairI64 I;
+    I.w = w;
+    I.inv_rho = inv_rho;
+    I.rho_half = K.rho0 + 0.5 * w;
+    I.m2_ir = -2.0 * inv_rho;
+    I.eta_ir = K.two_eta * inv_rho;
+    return I;
+}
+
+// min(max(x, 0), 1) by the sign and order of the binary64 bit pattern (the
+// order of non-negative doubles is that of their patterns): integer selects
+// instead of two FP64 comparisons.
+__device__ __forceinline__ double clamp01(double x)
+{
+    const long long b = __double_as_longlong(x);
+    if (b < 0) return 0.0;
+    if (b >= 0x3ff0000000000000LL) return 1.0;
+    return x;
+}
+
+// Contribution of neighbour j to a_i and R_i in the FP64 form: Eq. 3
+// (pressure, with P* of Eq. 5-6), Eq. 7 (viscous) and the residual of
+// Eq. 14, arranged for the FP64 pipe (1/64 of the FP32 rate here): the wall test
+// and the limiter's clamp on the integer ALU, P* from the density
+// deviations (p_i + p_j = c^2 (w_i + w_j), rho_bar = rho0 + (w_i + w_j)/2),
+// and one product m_j W'/(r rho_j) = V_j W'/r that the pressure, viscous and
+// residual terms share.  rv = x_i - x_j, inv_r = 1/r, dwr = W'(r, h_ij)/r,
+// w_j = rho_j - rho0 (+inf: a wall, which stands in with w_i),
+// inv_rho_jd = 1/rho_j (unused for a wall).
+template <int DIM>
+__device__ __forceinline__ void pair_force64(const Consts<double>& K, const PairI64& I, const double* rv,
+                                             double inv_r, double dwr, const double* vi, const double* vj,
+                                             double w_j, double m_j, double inv_rho_jd, PlainD* acc_a,
+                                             PlainD* acc_R)
+{
+    const bool wall = (__double_as_longlong(w_j) & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL;
+    const double wj = wall ? I.w : w_j;
+    const double inv_rho_j = wall ? I.inv_rho : inv_rho_jd;
+    double dv[3] = {0.0, 0.0, 0.0};
+    double dvr = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         dv[d] = vi[d] - vj[d];
         dvr += dv[d] * rv[d];
     }
-    const Real du = -dvr * inv_r;
-    Real beta = (K.beta_slope * K.inv_c) * du;
-    beta = beta > Real(0) ? beta : Real(0);
-    beta = beta < Real(1) ? beta : Real(1);
-    const Real rhobar = Real(0.5) * (rho_i + rho_j);
-    const Real pstar = Real(0.5) * (p_i + p_j) + (Real(0.5) * K.c) * (beta * rhobar * du);
-    const Real mr = m_j * (inv_rho_i * inv_rho_j);         // m_j / (rho_i rho_j)
-    const Real cpw = Real(-2) * mr * pstar * dwr;          // pressure: cp W'/r
-    const Real cv = K.two_eta * mr * dwr;                  // viscous
-    const Real vw = m_j * inv_rho_j * dwr;                 // residual: V_j W'/r
+    const double du = -dvr * inv_r;                                   // U_l - U_r
+    const double beta = clamp01((K.beta_slope * K.inv_c) * du);
+    const double half_psum = (0.5 * K.c2) * (I.w + wj);              // (p_i + p_j) / 2
+    const double rhobar = fma(0.5, wj, I.rho_half);
+    const double pstar = fma((0.5 * K.c) * (beta * du), rhobar, half_psum);
+    const double vw = (m_j * inv_rho_j) * dwr;                        // V_j W'/r
+    const double cpw = I.m2_ir * (vw * pstar);                        // -2 m_j P* / (rho_i rho_j) W'/r
+    const double cv = I.eta_ir * vw;                                  // 2 eta m_j / (rho_i rho_j) W'/r
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        acc_a[d].add(cpw * rv[d] + cv * dv[d]);
-        acc_R[d].add(vw * rv[d]);
+        acc_a[d].s = fma(cpw, rv[d], acc_a[d].s);
+        acc_a[d].s = fma(cv, dv[d], acc_a[d].s);
+        acc_R[d].s = fma(vw, rv[d], acc_R[d].s);
     }
 }
 
