@@ -76,9 +76,13 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     const float lim_u = (float)two_hu;
     const float lim2_u = lim_u * lim_u * 1.0001f;
     const double wnorm_u = kernel_norm<DIM, double>() * pow_dim<DIM, double>(K.inv_h_u);
+    // sigma; at uniform resolution the sum of W / (a_D h^-D), the constant
+    // applied once at the end
     double sigma = 0.0;
     // the exact FP64 test of a candidate that passed the FP32 prefilter: adds
-    // W to sigma; true for a force neighbour (j != i, 0 < r < 2 h_ij)
+    // W to sigma; true for a force neighbour (j != i, 0 < r < 2 h_ij).  The
+    // comparisons of non-negative doubles are made on their bit patterns
+    // (same order) by the integer ALU, off the FP64 pipe.
     auto exact = [&](int j, uint32_t code, double hij) {
         // x_i - x_j with the periodic image of the stencil step (the nearest
         // image of every neighbour: the same operations as min_image)
@@ -96,9 +100,19 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
             r2 += t * t;
         }
         const double r = sqrt(r2);
-        if (!(r < (uni ? two_hu : 2.0 * hij))) return false;
-        sigma += uni ? wendland_W_scaled<DIM>(r, K.inv_h_u, wnorm_u) : wendland_W<DIM, double>(r, 1.0 / hij);
-        return j != i && r2 > 0.0;
+        // r < 2 h_ij (a NaN has a pattern above every finite value's)
+        if (!((unsigned long long)__double_as_longlong(r) <
+              (unsigned long long)__double_as_longlong(uni ? two_hu : 2.0 * hij)))
+            return false;
+        if (uni) {
+            const double q = r * K.inv_h_u;
+            const double t = 1.0 - 0.5 * q;
+            const double t2 = t * t;
+            sigma = fma(t2 * t2, 2.0 * q + 1.0, sigma);
+        } else {
+            sigma += wendland_W<DIM, double>(r, 1.0 / hij);
+        }
+        return j != i && __double_as_longlong(r2) != 0;               // r2 >= +0
     };
     // FP32 prefilter bound (1e-4 margin) of the pair (i, j); pj_w = (float)h_j
     // when h varies
@@ -150,12 +164,16 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
                 const uint32_t e = nbl[(size_t)k * n + i];
                 const int j = (int)(e >> kCodeBits);
                 const double hij = uni ? K.h_u : pair_h(K, hi, S.h[j]);
-                if (exact(j, e & ((1u << kCodeBits) - 1u), hij)) nbl[(size_t)cnt++ * n + i] = e;
+                if (exact(j, e & ((1u << kCodeBits) - 1u), hij)) {
+                    if (cnt != k) nbl[(size_t)cnt * n + i] = e;     // entries before a rejected one stay in place
+                    ++cnt;
+                }
             }
         }
     }
     if (!staged) for_candidates_rows<DIM, false>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
     if (nbc) nbc[i] = cnt;
+    if (uni) sigma *= wnorm_u;
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     const double w = __dsub_rn(rho, K.rho0);
     vr[i] = make_double4_32a(vi[0], vi[1], vi[2], w);
