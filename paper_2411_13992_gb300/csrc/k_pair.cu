@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
                                                      Grid G, Consts<double> K, double4_32a* __restrict__ vr,
                                                      const float4* __restrict__ pos4,
                                                      const int32_t* __restrict__ cell_of, uint32_t* __restrict__ nbl,
-                                                     int32_t* __restrict__ nbc, int cap, double* __restrict__ inv_rho)
+                                                     int32_t* __restrict__ nbc, int cap, double* __restrict__ vol)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -177,19 +177,19 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     double rho = __ddiv_rn(__dmul_rn(K.rho0, sigma), S.s0[i]);
     const double w = __dsub_rn(rho, K.rho0);
     vr[i] = make_double4_32a(vi[0], vi[1], vi[2], w);
-    // 1/rho_j for the force pass, once per particle instead of once per pair
-    // (the force pass's own expression: rho0 + w, then the division)
-    if (inv_rho) inv_rho[i] = 1.0 / (K.rho0 + w);
+    // V_i = m_i / rho_i for the force pass, once per particle instead of once
+    // per pair
+    if (vol) vol[i] = S.m[i] / (K.rho0 + w);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, const int32_t* __restrict__ start,
+__global__ void __launch_bounds__(256, 2) k_forces_f64(int n, StateSet<double> S, const int32_t* __restrict__ start,
                                                     Grid G, Consts<double> K, const double4_32a* __restrict__ vr,
                                                     const uint32_t* __restrict__ nbl, const int32_t* __restrict__ nbc,
                                                     int cap, const double* __restrict__ dt_ptr, int kick_on,
                                                     int write_ad, double* __restrict__ Rout,
                                                     double* __restrict__ chi_out, double* __restrict__ partials,
-                                                    const double* __restrict__ inv_rho)
+                                                    const double* __restrict__ vol)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part[kNPart];
@@ -215,16 +215,33 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
                                  K.inv_h_u;
         // the cell of i (as the sort computed it from these positions)
         const int ci[3] = {cell_coord(G, xi[0], 0), cell_coord(G, xi[1], 1), DIM == 3 ? cell_coord(G, xi[2], 2) : 0};
-        const PairI64 I = pair_i64(K, me.w, inv_rho_i);
+        // W'/r = C t^3 at uniform resolution (t = 1 - r / 2h): C leaves the sums
+        const double C = uni ? dwrnorm_u : 1.0;
+        const double half_inv_h = 0.5 * K.inv_h_u;
+        const PairI64 I = pair_i64(K, me.w, inv_rho_i, C);
         // a neighbour j (0 < r < 2 h_ij) at rv = x_i - x_j, r2 = |rv|^2
         auto body = [&](int j, const double* rv, double r2) {
             const double inv_r = rsqrt(r2);
             const double r = r2 * inv_r;
-            const double dwr = uni ? wendland_dWr_scaled<DIM>(r, K.inv_h_u, dwrnorm_u)
-                                   : wendland_dW<DIM, double>(r, 1.0 / pair_h(K, hi, S.h[j])) * inv_r;
+            double g;
+            if (uni) {
+                const double t = fma(-half_inv_h, r, 1.0);
+                g = t * t * t;
+            } else {
+                g = wendland_dW<DIM, double>(r, 1.0 / pair_h(K, hi, S.h[j])) * inv_r;
+            }
             const double4_32a oj = vr[j];
             const double vj[3] = {oj.x, oj.y, oj.z};
-            pair_force64<DIM>(K, I, rv, inv_r, dwr, vi, vj, oj.w, S.m[j], inv_rho[j], acc_a, acc_R);
+            double w_j = oj.w, V_j = vol[j];
+            const bool wall = is_wall(w_j);
+            if (__any_sync(__activemask(), wall)) {
+                // a wall stands in with rho_j = rho_i: w_j = w_i, V_j = m_j / rho_i
+                if (wall) {
+                    w_j = me.w;
+                    V_j = S.m[j] * inv_rho_i;
+                }
+            }
+            pair_force64<DIM>(K, I, rv, inv_r, g, vi, vj, w_j, V_j, acc_a, acc_R);
         };
         const int cnt = nbl ? nbc[i] : cap + 1;
         if (cnt <= cap) {
@@ -292,7 +309,7 @@ __global__ void __launch_bounds__(256) k_forces_f64(int n, StateSet<double> S, c
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             a[d] = K.g[d] + acc_a[d].value();
-            R[d] = acc_R[d].value();
+            R[d] = C * acc_R[d].value();
             R2 += R[d] * R[d];
         }
         const double htv = K.tv_h_particle ? hi : K.h_min;
@@ -457,7 +474,7 @@ int pair_blocks(int prec, int n, int sms) { return nblk(n, pair_threads(prec, n,
 
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st, double* inv_rho)
+                           cudaStream_t st, double* vol)
 {
     const int T = pair_threads(prec, n, G.sms);
     if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st);
@@ -466,17 +483,17 @@ cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* sta
     const int cap = nbl_capacity(dim);
     if (dim == 2)
         k_density_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap,
-                                                   inv_rho);
+                                                   vol);
     else
         k_density_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (double4_32a*)vr, pos4, cell_of, nbl, nbc, cap,
-                                                   inv_rho);
+                                                   vol);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
-                          void* Rout, void* chi, double* partials, cudaStream_t st, const double* inv_rho)
+                          void* Rout, void* chi, double* partials, cudaStream_t st, const double* vol)
 {
     const int T = pair_threads(prec, n, G.sms);
     if (prec == 32)
@@ -487,10 +504,10 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
     const int cap = nbl_capacity(dim);
     if (dim == 2)
         k_forces_f64<2><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
-                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, inv_rho);
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, vol);
     else
         k_forces_f64<3><<<nblk(n, T), T, 0, st>>>(n, s, start, G, k, (const double4_32a*)vr, nbl, nbc, cap, dt,
-                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, inv_rho);
+                                                  kick_on, write_ad, (double*)Rout, (double*)chi, partials, vol);
     return cudaGetLastError();
 }
 

@@ -55,11 +55,11 @@ int pair_blocks(int prec, int n, int sms);
 // writes the neighbour list the dual-criteria integrator uses.
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st, double* inv_rho = nullptr);
+                           cudaStream_t st, double* vol = nullptr);
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
-                          void* Rout, void* chi, double* partials, cudaStream_t st, const double* inv_rho = nullptr);
+                          void* Rout, void* chi, double* partials, cudaStream_t st, const double* vol = nullptr);
 
 // k_pair32.cu
 int nbl_capacity(int dim);

@@ -34,22 +34,26 @@ __device__ __forceinline__ Real tv_limiter(const Consts<Real>& K, Real s)
 }
 
 // Per-particle values of i shared by all pairs of i in the FP64 force pass.
+// C is a constant factor of W'/r that the pass takes out of the pair sums
+// (-5 a_D h^-(D+2) at uniform resolution, where W'/r = C t^3; else 1).
 struct PairI64 {
     double w;          // rho_i - rho0
     double inv_rho;    // 1 / rho_i
-    double rho_half;   // rho0 + w / 2, so that rho_bar = rho_half + w_j / 2
-    double m2_ir;      // -2 / rho_i
-    double eta_ir;     // 2 eta / rho_i
+    double hp;         // p_i / 2 = (c^2 / 2) w_i
+    double crho;       // (c/2)(rho0 + w_i / 2): (c/2) rho_bar = crho + (c/4) w_j
+    double m2_ir;      // -2 C / rho_i
+    double eta_ir;     // 2 eta C / rho_i
 };
 
-__device__ __forceinline__ PairI64 pair_i64(const Consts<double>& K, double w, double inv_rho)
+__device__ __forceinline__ PairI64 pair_i64(const Consts<double>& K, double w, double inv_rho, double C)
 {
     PairI64 I;
     I.w = w;
     I.inv_rho = inv_rho;
-    I.rho_half = K.rho0 + 0.5 * w;
-    I.m2_ir = -2.0 * inv_rho;
-    I.eta_ir = K.two_eta * inv_rho;
+    I.hp = (0.5 * K.c2) * w;
+    I.crho = (0.5 * K.c) * (K.rho0 + 0.5 * w);
+    I.m2_ir = (-2.0 * C) * inv_rho;
+    I.eta_ir = (K.two_eta * C) * inv_rho;
     return I;
 }
 
@@ -64,24 +68,27 @@ __device__ __forceinline__ double clamp01(double x)
     return x;
 }
 
+// w = +inf marks a wall particle in the velocity record (a bit test: no
+// FP64 comparison).
+__device__ __forceinline__ bool is_wall(double w)
+{
+    return (__double_as_longlong(w) & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL;
+}
+
 // Contribution of neighbour j to a_i and R_i in the FP64 form: Eq. 3
 // (pressure, with P* of Eq. 5-6), Eq. 7 (viscous) and the residual of
-// Eq. 14, arranged for the FP64 pipe (1/64 of the FP32 rate here): the wall test
-// and the limiter's clamp on the integer ALU, P* from the density
-// deviations (p_i + p_j = c^2 (w_i + w_j), rho_bar = rho0 + (w_i + w_j)/2),
-// and one product m_j W'/(r rho_j) = V_j W'/r that the pressure, viscous and
-// residual terms share.  rv = x_i - x_j, inv_r = 1/r, dwr = W'(r, h_ij)/r,
-// w_j = rho_j - rho0 (+inf: a wall, which stands in with w_i),
-// inv_rho_jd = 1/rho_j (unused for a wall).
+// Eq. 14, arranged for the FP64 pipe (1/64 of the FP32 rate here): P* from
+// the density deviations (p_i + p_j = c^2 (w_i + w_j), rho_bar = rho0 +
+// (w_i + w_j)/2), the limiter's clamp on the integer ALU, and one product
+// V_j g that the pressure, viscous and residual terms share.  rv = x_i -
+// x_j, inv_r = 1/r, g = W'(r, h_ij) / (r C); w_j = rho_j - rho0 and V_j =
+// m_j / rho_j, for a wall neighbour w_i and m_j / rho_i (the caller
+// substitutes them).  acc_R collects R_i / C.
 template <int DIM>
 __device__ __forceinline__ void pair_force64(const Consts<double>& K, const PairI64& I, const double* rv,
-                                             double inv_r, double dwr, const double* vi, const double* vj,
-                                             double w_j, double m_j, double inv_rho_jd, PlainD* acc_a,
-                                             PlainD* acc_R)
+                                             double inv_r, double g, const double* vi, const double* vj,
+                                             double w_j, double V_j, PlainD* acc_a, PlainD* acc_R)
 {
-    const bool wall = (__double_as_longlong(w_j) & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL;
-    const double wj = wall ? I.w : w_j;
-    const double inv_rho_j = wall ? I.inv_rho : inv_rho_jd;
     double dv[3] = {0.0, 0.0, 0.0};
     double dvr = 0.0;
 #pragma unroll
@@ -91,10 +98,10 @@ __device__ __forceinline__ void pair_force64(const Consts<double>& K, const Pair
     }
     const double du = -dvr * inv_r;                                   // U_l - U_r
     const double beta = clamp01((K.beta_slope * K.inv_c) * du);
-    const double half_psum = (0.5 * K.c2) * (I.w + wj);              // (p_i + p_j) / 2
-    const double rhobar = fma(0.5, wj, I.rho_half);
-    const double pstar = fma((0.5 * K.c) * (beta * du), rhobar, half_psum);
-    const double vw = (m_j * inv_rho_j) * dwr;                        // V_j W'/r
+    const double hpsum = fma(0.5 * K.c2, w_j, I.hp);                   // (p_i + p_j) / 2
+    const double crhobar = fma(0.25 * K.c, w_j, I.crho);               // (c/2) rho_bar
+    const double pstar = fma(beta * du, crhobar, hpsum);
+    const double vw = V_j * g;                                        // V_j W'/(r C)
     const double cpw = I.m2_ir * (vw * pstar);                        // -2 m_j P* / (rho_i rho_j) W'/r
     const double cv = I.eta_ir * vw;                                  // 2 eta m_j / (rho_i rho_j) W'/r
 #pragma unroll

@@ -58,7 +58,7 @@ struct sph_ctx {
     float* mf;
     uint32_t* nbl;      // neighbour lists of the density pass [cap][n], transposed
     int32_t* nbc;       // neighbour count per particle (with nbl)
-    double* inv_rho;    // FP64 form: 1/rho per particle, written by the density pass for the force pass
+    double* vol;        // FP64 form: V = m/rho per particle, written by the density pass for the force pass
     void* anu;          // dual integrator: viscous acceleration held for an advection step
     double* du;         // dual integrator: device state (DU_*)
     int dual_est;       // dual integrator: substeps to launch before the first check
@@ -266,7 +266,7 @@ size_t carve(sph_ctx* c, char* base)
     const bool lists = !c->density_only;   // both forms: the force pass walks the density pass's list
     c->nbl = lists ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
     c->nbc = lists ? W.take<int32_t>(n) : nullptr;
-    c->inv_rho = lists && c->prec == 64 ? W.take<double>(n) : nullptr;
+    c->vol = lists && c->prec == 64 ? W.take<double>(n) : nullptr;
     c->anu = dual ? W.take<char>(D * n * rs) : nullptr;
     c->du = dual ? W.take<double>(DU_COUNT) : nullptr;
     c->R = c->density_only ? nullptr : W.take<char>(D * n * rs);
@@ -380,7 +380,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int n = (int)c->n;
     if (!pairs) {
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->inv_rho));
+                              c->nbl, c->nbc, c->st, c->vol));
         SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->G.sms, c->st));
         SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
                                count_step, c->st));
@@ -390,12 +390,12 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int write_ad = 1;
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->nbl,
-                          c->nbc, c->st, c->inv_rho));
+                          c->nbc, c->st, c->vol));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_FORCES, 0);
     SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->mf, c->vr, c->pos4, c->cell,
                          c->nbl, c->nbc, c->dt, kick_on, write_ad, c->R, c->chi, c->partials, c->st,
-                         c->inv_rho));
+                         c->vol));
     SPH_MARK(SPH_K_FORCES, 1);
     SPH_MARK(SPH_K_FINALIZE, 0);
     SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
@@ -439,7 +439,7 @@ sph_status run_dual_step(sph_ctx* c)
     SPH_TRY(run_sort(c, 2, 0));
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                          c->nbl, c->nbc, c->st, c->inv_rho));
+                          c->nbl, c->nbc, c->st, c->vol));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_ADVECT, 0);
     SPH_CU(launch_dual_begin(c->P, c->diag, c->du, c->st));
@@ -991,7 +991,7 @@ sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr
         // density pass now (a and dr travel with the sort)
         SPH_TRY(run_sort(c, 0, 1));
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->inv_rho));
+                              c->nbl, c->nbc, c->st, c->vol));
         ++c->launches;
         c->cells_pending = 0;
     }
