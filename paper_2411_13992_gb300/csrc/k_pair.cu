@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
     const float lim_u = (float)two_hu;
     const float lim2_u = lim_u * lim_u * 1.0001f;
     const double wnorm_u = kernel_norm<DIM, double>() * pow_dim<DIM, double>(K.inv_h_u);
+    const double half_inv_hu = 0.5 * K.inv_h_u, two_inv_hu = 2.0 * K.inv_h_u;
     // sigma; at uniform resolution the sum of W / (a_D h^-D), the constant
     // applied once at the end
     double sigma = 0.0;
@@ -105,10 +106,10 @@ __global__ void __launch_bounds__(256) k_density_f64(int n, StateSet<double> S, 
               (unsigned long long)__double_as_longlong(uni ? two_hu : 2.0 * hij)))
             return false;
         if (uni) {
-            const double q = r * K.inv_h_u;
-            const double t = 1.0 - 0.5 * q;
+            // t = 1 - q/2 and 2q + 1 with q = r/h, each one fused operation
+            const double t = fma(-half_inv_hu, r, 1.0);
             const double t2 = t * t;
-            sigma = fma(t2 * t2, 2.0 * q + 1.0, sigma);
+            sigma = fma(t2 * t2, fma(two_inv_hu, r, 1.0), sigma);
         } else {
             sigma += wendland_W<DIM, double>(r, 1.0 / hij);
         }
