@@ -77,7 +77,7 @@ __device__ __forceinline__ bool is_wall(double w)
 
 // Contribution of neighbour j to a_i and R_i in the FP64 form: Eq. 3
 // (pressure, with P* of Eq. 5-6), Eq. 7 (viscous) and the residual of
-// Eq. 14, arranged for the FP64 pipe (1/64 of the FP32 rate here): P* from
+// Eq. 14, arranged for the FP64 pipe (1/74 of the FP32 rate here): P* from
 // the density deviations (p_i + p_j = c^2 (w_i + w_j), rho_bar = rho0 +
 // (w_i + w_j)/2), the limiter's clamp on the integer ALU, and one product
 // V_j g that the pressure, viscous and residual terms share.  rv = x_i -
@@ -122,7 +122,7 @@ __device__ __forceinline__ void pair_force64(const Consts<double>& K, const Pair
 // order.  With FIRST the flags are counted with a ballot and the maxima of
 // the non-negative squares are integer maxima of their bit patterns (a NaN
 // counts as 0, as fmax ignores it), which keeps both off the FP64 pipe
-// (1/64 of the FP32 rate on this part).  sums = false (the same for every
+// (1/74 of the FP32 rate on this part).  sums = false (the same for every
 // thread of the grid) when the caller's sums are all zero: they are skipped.
 template <bool FIRST>
 __device__ __forceinline__ void block_partials(double* vals, double* out_block, bool sums = true)
