@@ -225,9 +225,10 @@ __device__ __forceinline__ int trunc_nonneg(double t)
 
 __device__ __forceinline__ int cell_coord(const Grid& G, double x, int d)
 {
-    // x - lo is x itself when lo = 0 (bit for bit), one FP64 operation fewer;
-    // the truncation (toward zero, then clamped) on the integer ALU
-    const double t = G.lo[d] == 0.0 ? x : __dsub_rn(x, G.lo[d]);
+    // x - lo is x itself when lo = 0 (bit for bit), one FP64 operation fewer
+    // (lo = +-0 read from its bit pattern); the truncation (toward zero, then
+    // clamped) on the integer ALU
+    const double t = (__double_as_longlong(G.lo[d]) << 1) == 0 ? x : __dsub_rn(x, G.lo[d]);
     const int c = trunc_nonneg(t * G.inv_edge[d]);
     return min(max(c, 0), G.nc[d] - 1);
 }

@@ -16,6 +16,36 @@
 
 namespace sphtv {
 
+// A non-negative int as a double, exactly, on the integer ALU: the leading
+// one sets the binary64 exponent, the bits below it the fraction.
+__device__ __forceinline__ double i2d_exact(int c)
+{
+    if (c <= 0) return 0.0;                   // callers pass cell coordinates >= 0
+    const int e = 31 - __clz(c);
+    const unsigned long long frac = ((unsigned long long)c << (52 - e)) & 0xfffffffffffffULL;
+    return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | frac));
+}
+
+// A double rounded to the nearest float (ties to even), as the hardware
+// conversion rounds it, on the integer ALU for results that are normal
+// floats: the 52-bit fraction is cut to 23 bits and rounded up when the cut
+// part is above half an ulp, or exactly half with an odd last kept bit (a
+// carry out of the fraction raises the exponent, and past the largest float
+// gives infinity, as rounding does).  Zeros, subnormal results, infinities
+// and NaN take the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ff) - 1023;
+    if (E < -126 || E > 127) return (float)x;
+    const unsigned long long frac = b & 0xfffffffffffffULL;
+    const unsigned keep = (unsigned)(frac >> 29);
+    const unsigned long long cut = frac & 0x1fffffffULL;               // the 29 bits cut off
+    const unsigned up = (cut > 0x10000000ULL || (cut == 0x10000000ULL && (keep & 1u))) ? 1u : 0u;
+    const unsigned f = (((unsigned)(E + 127) << 23) + keep + up) | ((unsigned)(b >> 32) & 0x80000000u);
+    return __uint_as_float(f);
+}
+
 template <typename Real>
 __device__ __forceinline__ Real kick(Real v, double hdt, Real a);
 
@@ -28,7 +58,7 @@ __device__ __forceinline__ double kick<double>(double v, double hdt, double a)
 template <>
 __device__ __forceinline__ float kick<float>(float v, double hdt, float a)
 {
-    return __fadd_rn(v, __fmul_rn((float)hdt, a));
+    return __fadd_rn(v, __fmul_rn(d2f_rn(hdt), a));
 }
 
 // FP64 value of a velocity or displacement component (exact either way).
@@ -252,11 +282,14 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
         int c[3];
         cell_decode(G, kk, c);
         float o[3] = {0.f, 0.f, 0.f};
+        // the conversions on the integer ALU (the same values as the hardware
+        // conversions, which run on the FP64 pipe)
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) o[d] = (float)(xs[d] - (G.lo[d] + (double)c[d] * G.edge[d]));
-        pos4[k] = make_float4(o[0], o[1], o[2], uniform_h ? (float)m : (float)h);
+        for (int d = 0; d < DIM; ++d) o[d] = d2f_rn(xs[d] - (G.lo[d] + i2d_exact(c[d]) * G.edge[d]));
+        const float m_f = d2f_rn(m);
+        pos4[k] = make_float4(o[0], o[1], o[2], uniform_h ? m_f : d2f_rn(h));
         cell_out[k] = kk;
-        mf[k] = (float)m;
+        mf[k] = m_f;
     }
 }
 
