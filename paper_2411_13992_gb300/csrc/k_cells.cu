@@ -65,6 +65,14 @@ __device__ __forceinline__ float kick<float>(float v, double hdt, float a)
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(float x) { return f2d_exact(x); }
 
+// -1 for x < lo, +1 for x >= hi, else 0: the periodic wrap of axis d, as
+// integer comparisons of order keys (dkey).
+__device__ __forceinline__ int wrap_side(const Grid& G, double x, int d)
+{
+    const long long kx = dkey(x);
+    return kx < dkey(G.lo[d]) ? -1 : (kx >= dkey(G.hi[d]) ? 1 : 0);
+}
+
 template <typename Real, int DIM>
 __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restrict__ dt_ptr, int drift, Grid G,
                                  int32_t* __restrict__ key, int32_t* __restrict__ count, uint32_t* err)
@@ -81,12 +89,11 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             if (!G.periodic[d]) continue;
-            double xn = xs[d];
-            const long long kx = dkey(xn);
-            if (kx < dkey(G.lo[d])) xn = __dadd_rn(xn, G.L[d]);
-            else if (kx >= dkey(G.hi[d])) xn = __dsub_rn(xn, G.L[d]);
-            if (xn != xs[d]) S.x[(size_t)d * n + i] = xn;
-            xs[d] = xn;
+            const int w = wrap_side(G, xs[d], d);
+            if (__any_sync(__activemask(), w != 0) && w != 0) {
+                xs[d] = w < 0 ? __dadd_rn(xs[d], G.L[d]) : __dsub_rn(xs[d], G.L[d]);
+                S.x[(size_t)d * n + i] = xs[d];
+            }
         }
     } else if (drift == 1 && S.kind[i] == 0) {
         const double dt = *dt_ptr;
@@ -98,10 +105,11 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
             S.v[o] = vh;
             double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(S.dr[o]));
             if (G.periodic[d]) {
-                // xn < lo, xn >= hi as integer comparisons (dkey)
-                const long long kx = dkey(xn);
-                if (kx < dkey(G.lo[d])) xn = __dadd_rn(xn, G.L[d]);
-                else if (kx >= dkey(G.hi[d])) xn = __dsub_rn(xn, G.L[d]);
+                // the wrap only in warps where a particle left the box (the
+                // FP64 operation would otherwise be issued for every warp)
+                const int w = wrap_side(G, xn, d);
+                if (__any_sync(__activemask(), w != 0) && w != 0)
+                    xn = w < 0 ? __dadd_rn(xn, G.L[d]) : __dsub_rn(xn, G.L[d]);
             }
             xs[d] = xn;
             S.x[o] = xn;
