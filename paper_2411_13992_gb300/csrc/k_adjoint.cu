@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "pair_physics.cuh"
+#include "pair_walk.cuh"
 
 namespace sphtv {
 
@@ -52,27 +53,45 @@ template <typename Real, int DIM, typename F>
 __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Consts<Real>& K, const Tape<Real>& T,
                                           F& f)
 {
-    const int SR = G.R, zr = DIM == 3 ? SR : 0;
-    int c[3];
-    if constexpr (sizeof(Real) == 8) {
-        for (int d = 0; d < 3; ++d) c[d] = d < DIM ? cell_coord(G, T.x[(size_t)d * n + k], d) : 0;
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 form: the clipped row walk of the forward density pass, with
+        // its arithmetic for r^2, so the pairs are exactly the forward's
+        // (same order as the cell scan below)
+        const float4 pk = T.pos4[k];
+        const float ok[3] = {pk.x, pk.y, pk.z};
+        const float hk = (float)T.h[k];
+        const float reach = K.uniform_h ? 2.f * K.h_u : 2.f * pair_h(K, hk, K.h_u);
+        auto g = [&](int j, uint32_t, const float4&, float r2, float rx, float ry, float rz) {
+            float lim;
+            if (K.uniform_h) lim = K.four_h2_u;
+            else {
+                const float hh = pair_h(K, hk, (float)T.h[j]);
+                lim = 4.f * hh * hh;
+            }
+            if (!(r2 < lim) || !(r2 > 0.f)) return;
+            const Real rv[3] = {rx, ry, rz};
+            f(j, rv, sqrtf(r2));
+        };
+        for_candidates_rows<DIM, false>(ok, reach, T.cell[k], G, T.start, T.cell, T.pos4, g);
     } else {
-        cell_decode(G, T.cell[k], c);
-    }
-    for (int dz = -zr; dz <= zr; ++dz) {
-        int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
-        if (cz < 0) continue;
-        for (int dy = -SR; dy <= SR; ++dy) {
-            int cy = cell_step(G, c[1], dy, 1);
-            if (cy < 0) continue;
-            for (int dx = -SR; dx <= SR; ++dx) {
-                int cx = cell_step(G, c[0], dx, 0);
-                if (cx < 0) continue;
-                const int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
-                for (int j = T.start[cell]; j < T.start[cell + 1]; ++j) {
-                    if (j == k) continue;
-                    Real rv[3] = {0, 0, 0};
-                    if constexpr (sizeof(Real) == 8) {
+        // FP64 form: the exact test of the forward pass (minimum image,
+        // sqrt(r^2) < 2 h_kj)
+        const int SR = G.R, zr = DIM == 3 ? SR : 0;
+        int c[3];
+        for (int d = 0; d < 3; ++d) c[d] = d < DIM ? cell_coord(G, T.x[(size_t)d * n + k], d) : 0;
+        for (int dz = -zr; dz <= zr; ++dz) {
+            int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+            if (cz < 0) continue;
+            for (int dy = -SR; dy <= SR; ++dy) {
+                int cy = cell_step(G, c[1], dy, 1);
+                if (cy < 0) continue;
+                for (int dx = -SR; dx <= SR; ++dx) {
+                    int cx = cell_step(G, c[0], dx, 0);
+                    if (cx < 0) continue;
+                    const int cell = cx + G.nc[0] * (cy + G.nc[1] * cz);
+                    for (int j = T.start[cell]; j < T.start[cell + 1]; ++j) {
+                        if (j == k) continue;
+                        Real rv[3] = {0, 0, 0};
                         double r2 = 0.0;
                         for (int d = 0; d < DIM; ++d) {
                             rv[d] = min_image(G, T.x[(size_t)d * n + k], T.x[(size_t)d * n + j], d);
@@ -82,23 +101,6 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
                         const double hij = pair_h(K, T.h[k], T.h[j]);
                         if (!(r < 2.0 * hij) || r == 0.0) continue;
                         f(j, rv, (Real)r);
-                    } else {
-                        const float4 pk = T.pos4[k], pj = T.pos4[j];
-                        rv[0] = (pk.x - pj.x) + (-(float)dx * G.edgef[0]);
-                        rv[1] = (pk.y - pj.y) + (-(float)dy * G.edgef[1]);
-                        float r2 = rv[0] * rv[0] + rv[1] * rv[1];
-                        if (DIM == 3) {
-                            rv[2] = (pk.z - pj.z) + (-(float)dz * G.edgef[2]);
-                            r2 += rv[2] * rv[2];
-                        }
-                        float lim;
-                        if (K.uniform_h) lim = K.four_h2_u;
-                        else {
-                            const float hh = pair_h(K, (float)T.h[k], (float)T.h[j]);
-                            lim = 4.f * hh * hh;
-                        }
-                        if (!(r2 < lim) || !(r2 > 0.f)) continue;
-                        f(j, rv, sqrtf(r2));
                     }
                 }
             }
