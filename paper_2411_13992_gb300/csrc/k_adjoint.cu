@@ -48,7 +48,9 @@ struct Tape {
 };
 
 // Visit the neighbours j != k of particle k with 0 < r < 2 h_kj, decided
-// exactly as the forward pass decided them: f(j, rv[3] = x_k - x_j, r).
+// exactly as the forward pass decided them: f(j, rv[3] = x_k - x_j, r, 1/r)
+// (FP32 form: 1/r from rsqrt and r = r^2/r, as the forward force pass takes
+// them; FP64 form: r = sqrt(r^2), 1/r = 1/r).
 template <typename Real, int DIM, typename F>
 __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Consts<Real>& K, const Tape<Real>& T,
                                           F& f)
@@ -70,7 +72,8 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
             }
             if (!(r2 < lim) || !(r2 > 0.f)) return;
             const Real rv[3] = {rx, ry, rz};
-            f(j, rv, sqrtf(r2));
+            const float inv_r = rsqrtf(r2);
+            f(j, rv, r2 * inv_r, inv_r);
         };
         for_candidates_rows<DIM, false>(ok, reach, T.cell[k], G, T.start, T.cell, T.pos4, g);
     } else {
@@ -100,7 +103,7 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
                         const double r = sqrt(r2);
                         const double hij = pair_h(K, T.h[k], T.h[j]);
                         if (!(r < 2.0 * hij) || r == 0.0) continue;
-                        f(j, rv, (Real)r);
+                        f(j, rv, (Real)r, Real(1) / (Real)r);
                     }
                 }
             }
@@ -164,6 +167,11 @@ __device__ __forceinline__ void pair_adjoint(const Consts<Real>& K, const Real* 
 #pragma unroll
     for (int d = 0; d < DIM; ++d) rb[d] = (ub[d] - uu * u[d]) * inv_r + radial * u[d];
 }
+
+// 1/x: rcp.approx in the FP32 form (as its forward pass takes reciprocals),
+// the correctly rounded division in the FP64 form.
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 template <typename Real>
 __device__ __forceinline__ Real inv_pair_h(const Consts<Real>& K, const Tape<Real>& T, int k, int j)
@@ -238,7 +246,7 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
         }
         Acc ax[DIM], av[DIM], arho;
         double eta_acc = 0.0;
-        auto pair = [&](int j, const Real* rv, Real r) {
+        auto pair = [&](int j, const Real* rv, Real r, Real inv_r) {
             const Real inv_h = inv_pair_h(K, T, k, j);
             const Real w = wendland_dW<DIM, Real>(r, inv_h);
             const Real w2 = wendland_d2W<DIM, Real>(r, inv_h);
@@ -246,9 +254,8 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
             const Real vj[3] = {mj.x, mj.y, mj.z};
             const bool wall = isinf(mj.w);
             const Real rho_j = wall ? rho_k : K.rho0 + mj.w;
-            const Real inv_rho_j = wall ? inv_rho_k : Real(1) / rho_j;
+            const Real inv_rho_j = wall ? inv_rho_k : recip(rho_j);
             const Real p_j = wall ? p_k : K.c2 * mj.w;
-            const Real inv_r = Real(1) / r;
             Real rb[3], dvb[3], rib, rjb, eb;
             // k's own sums (k as i)
             pair_adjoint<Real, DIM>(K, rv, r, inv_r, w, w2, vk, rho_k, inv_rho_k, p_k, vj, rho_j, inv_rho_j, p_j,
@@ -312,11 +319,11 @@ __global__ void __launch_bounds__(128) k_adj_density(int n, Tape<Real> T, Grid G
     }
     const Real sk = sigb[k];
     Acc acc[DIM];
-    auto pair = [&](int j, const Real* rv, Real r) {
+    auto pair = [&](int j, const Real* rv, Real r, Real inv_r) {
         const Real inv_h = inv_pair_h(K, T, k, j);
         const Real w = wendland_dW<DIM, Real>(r, inv_h);
         const Real sj = T.kind[j] ? Real(0) : sigb[j];
-        const Real g = (sk + sj) * w / r;
+        const Real g = sizeof(Real) == 4 ? (sk + sj) * w * inv_r : (sk + sj) * w / r;
         for (int d = 0; d < DIM; ++d) acc[d].add(g * rv[d]);
     };
     adj_visit<Real, DIM>(n, k, G, K, T, pair);
