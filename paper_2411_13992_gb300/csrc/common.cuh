@@ -101,26 +101,6 @@ __device__ __forceinline__ Real wendland_W(Real r, Real inv_h)
     return kernel_norm<DIM, Real>() * pow_dim<DIM, Real>(inv_h) * (t2 * t2) * (Real(2) * q + Real(1));
 }
 
-// W(r, h) for r < 2h with a_D h^-D given (wnorm = kernel_norm * pow_dim(1/h),
-// computed in that order): the same value as wendland_W.
-template <int DIM>
-__device__ __forceinline__ double wendland_W_scaled(double r, double inv_h, double wnorm)
-{
-    double q = r * inv_h;
-    double t = 1.0 - 0.5 * q;
-    double t2 = t * t;
-    return wnorm * (t2 * t2) * (2.0 * q + 1.0);
-}
-
-// W'(r)/r for r < 2h, given dwrnorm = -5 a_D h^-(D+2): W' = a_D h^-(D+1)
-// (-5 q) t^3 with q = r/h, t = 1 - q/2, and q / r = 1/h.
-template <int DIM>
-__device__ __forceinline__ double wendland_dWr_scaled(double r, double inv_h, double dwrnorm)
-{
-    double t = 1.0 - 0.5 * (r * inv_h);
-    return dwrnorm * (t * t * t);
-}
-
 // dW/dr (r, h) for r < 2h.
 template <int DIM, typename Real>
 __device__ __forceinline__ Real wendland_dW(Real r, Real inv_h)
