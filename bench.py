@@ -428,11 +428,21 @@ def run_native(args):
         "candidates_per_particle": CANDIDATES_PER_PARTICLE, "flops_per_candidate": FLOPS_PER_CANDIDATE,
         "note": "implementation rate: the neighbour search's candidate tests added to the algorithmic flops; "
                 "not the roofline figure"}
+    # what binds the two FP32 pair kernels, from the committed ncu summary
+    # (96^3, one launch each): instruction issue, not the FMA pipe or HBM
+    roof_d["binding"] = {"limiter": "instruction issue", "issue_active": 0.748, "lanes_active_per_warp_instr": 19.1,
+                         "fma_pipe": 0.313, "dram_throughput": 0.095,
+                         "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
+    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.779, "lanes_active_per_warp_instr": 31.9,
+                         "fma_pipe": 0.507, "dram_throughput": 0.119,
+                         "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
     f64_ms, f64_cnt = prof64["forces"]
     f64_tflops = pairs * FLOPS_PER_PAIR_FP64 / (f64_ms / max(f64_cnt, 1) * 1e-3) / 1e12
     roof_f["fp64_forces"] = {"achieved": f64_tflops, "peak": dfma_tflops, "frac": f64_tflops / dfma_tflops,
                              "flops_per_pair": FLOPS_PER_PAIR_FP64,
-                             "peak_source": "measured: FP64 FMA microbenchmark (sph_fma_peak)"}
+                             "peak_source": "measured: FP64 FMA microbenchmark (sph_fma_peak)",
+                             "binding": {"limiter": "FP64 pipe", "fp64_pipe_active": 0.877,
+                                         "source": "profiles/fp64_pair_kernels_tgv3d_96_ncu.md"}}
     dominant = prof["density"][0] >= prof["forces"][0]
     roof, roof_other = (roof_d, roof_f) if dominant else (roof_f, roof_d)
     kernels = {k: {"ms_per_step": v[0] / max(v[1], 1), "share": v[0] / max(sum(t[0] for t in prof.values()), 1e-9)}
