@@ -80,7 +80,8 @@ def test_adjoint_matches_the_oracle_adjoint(kind, prec, tol):
     assert ex <= tol and ev <= tol and ee <= tol, (ex, ev, ee)
 
 
-def test_adjoint_with_unlimited_correction_and_variable_resolution():
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-4)])
+def test_adjoint_with_unlimited_correction_and_variable_resolution(prec, tol):
     c = cases.cylinder2d(D=1.0, res=10, box=(3.0, 2.0), center=(1.0, 1.0), refine=(0.6, 2.4, 0.4, 1.6),
                          band_dp=2.0, jitter_dp=0.05)
     opts = {"tv_mode": oracle.TV_UNLIMITED}
@@ -90,11 +91,13 @@ def test_adjoint_with_unlimited_correction_and_variable_resolution():
     wts = _weights(c, np.random.default_rng(5))
     states = oracle.rollout(P, c, c["x"], c["v"], s0, dt, 2)
     xr, vr, er = oracle.rollout_adjoint(P, c, states, s0, dt, wts)
-    xb, vb, eb = _library_gradients(c, 64, dt, 2, wts, **opts)
+    xb, vb, eb = _library_gradients(c, prec, dt, 2, wts, **opts)
     fl = c["kind"] == 0
-    assert normwise(xb[fl], xr[fl]) <= 1e-12
-    assert normwise(vb[fl], vr[fl]) <= 1e-12
-    assert abs(eb - er) <= 1e-12 * abs(er)
+    ex, ev = normwise(xb[fl], xr[fl]), normwise(vb[fl], vr[fl])
+    print(prec, "x %.2e v %.2e eta %.2e" % (ex, ev, abs(eb - er) / abs(er)))
+    assert ex <= tol
+    assert ev <= tol
+    assert abs(eb - er) <= tol * abs(er)
 
 
 def _ke_rollout_fp64(c, dt, nsteps, v0, nu):
