@@ -256,11 +256,15 @@ __global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, cons
 // --------------------------------------------------------------- permute
 
 // pos4 = {offset from the cell origin, h} (uniform resolution:
-// {offset, m}, since h is then a constant), mf = m in FP32, cell_out = key.
+// {offset, m}, since h is then a constant), mf = m in FP32, cell_out = key;
+// pos4c (when given: the FP32 form at uniform resolution) = {offset, bits of
+// the cell index}, which the FP32 density walk reads instead of pos4 and
+// cell_out.
 template <typename Real, int DIM, bool CARRY_AD, bool F32POS>
 __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real> src, StateSet<Real> dst,
                           const int32_t* __restrict__ key, Grid G, float4* __restrict__ pos4,
-                          int32_t* __restrict__ cell_out, float* __restrict__ mf, int uniform_h)
+                          int32_t* __restrict__ cell_out, float* __restrict__ mf, int uniform_h,
+                          float4* __restrict__ pos4c)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -296,6 +300,7 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
         for (int d = 0; d < DIM; ++d) o[d] = d2f_rn(xs[d] - (G.lo[d] + i2d_exact(c[d]) * G.edge[d]));
         const float m_f = d2f_rn(m);
         pos4[k] = make_float4(o[0], o[1], o[2], uniform_h ? m_f : d2f_rn(h));
+        if (pos4c) pos4c[k] = make_float4(o[0], o[1], o[2], __int_as_float(kk));
         cell_out[k] = kk;
         mf[k] = m_f;
     }
@@ -334,27 +339,34 @@ cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int
 
 template <typename Real>
 static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
-                      const Grid& G, float4* pos4, int32_t* cell, float* mf, int uh, int carry_ad, cudaStream_t st)
+                      const Grid& G, float4* pos4, int32_t* cell, float* mf, int uh, int carry_ad, cudaStream_t st,
+                      float4* pos4c)
 {
     const int T = 256;
     auto s = *(StateSet<Real>*)src;
     auto d = *(StateSet<Real>*)dst;
     constexpr bool F32 = true;   // both forms: the density passes walk the FP32 cell-relative positions
     if (dim == 2) {
-        if (carry_ad) k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
-        else k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
+        if (carry_ad)
+            k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+        else
+            k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
     } else {
-        if (carry_ad) k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
-        else k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh);
+        if (carry_ad)
+            k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+        else
+            k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
     }
 }
 
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                            const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
-                           cudaStream_t st)
+                           cudaStream_t st, float4* pos4c)
 {
-    if (prec == 64) permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st);
-    else permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st);
+    if (prec == 64)
+        permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c);
+    else
+        permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c);
     return cudaGetLastError();
 }
 

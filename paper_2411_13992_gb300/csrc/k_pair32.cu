@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
                                                       const int32_t* __restrict__ cell_of,
                                                       const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                       StateSet<float> S, float4* __restrict__ vr,
-                                                      uint32_t* __restrict__ nbl, int32_t* __restrict__ nbc, int cap)
+                                                      uint32_t* __restrict__ nbl, int32_t* __restrict__ nbc, int cap,
+                                                      const float4* __restrict__ pos4c)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -125,7 +126,11 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     };
     // reach: the largest support radius 2 h_ij of any pair of i (h_j <= h_max)
     const float reach = UNIFORM ? 2.f * K.h_u : 2.f * pair_h(K, hi, K.h_u);
-    for_candidates_rows<DIM>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
+    // at uniform resolution the walk reads the copy of the offsets that
+    // carries each candidate's cell index in w (one load per candidate
+    // instead of two)
+    if (UNIFORM) for_candidates_rows<DIM, true, true>(oi, reach, cell_i, G, start, cell_of, pos4c, visit);
+    else for_candidates_rows<DIM>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
     const float w = K.rho0 * (sigma.value() - s0) / s0;
@@ -297,11 +302,11 @@ int nbl_capacity(int dim) { return dim == 3 ? 128 : 96; }
 template <int DIM, typename Acc, bool U>
 static void density_t(int n, const float4* pos4, const int32_t* cell_of, const int32_t* start, const Grid& G,
                       const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl, int32_t* nbc,
-                      cudaStream_t st)
+                      cudaStream_t st, const float4* pos4c)
 {
     const int T = pair_threads(32, n, G.sms);
     k_density32<DIM, Acc, U><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, K, S, vr, nbl, nbc,
-                                                       nbl_capacity(DIM));
+                                                       nbl_capacity(DIM), pos4c);
 }
 
 template <int DIM, typename Acc, bool U>
@@ -338,11 +343,12 @@ static void forces_t(int n, const float4* pos4, const int32_t* cell_of, const in
 
 cudaError_t launch_density32(int dim, int n, void* Sv, const int32_t* start, const Grid& G, const void* Kv, void* vr,
                              const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                             cudaStream_t st)
+                             cudaStream_t st, const float4* pos4c)
 {
     const StateSet<float> S = *(StateSet<float>*)Sv;
     const Consts<float>& K = *(const Consts<float>*)Kv;
-    SPH_DISPATCH32(density_t, n, pos4, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
+    if (K.uniform_h && !pos4c) return cudaErrorInvalidValue;   // the uniform walk reads the cell-tagged copy
+    SPH_DISPATCH32(density_t, n, pos4, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st, pos4c);
     return cudaGetLastError();
 }
 

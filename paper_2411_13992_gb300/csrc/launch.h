@@ -46,7 +46,7 @@ cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int
                                  int64_t* launches);
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                            const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
-                           cudaStream_t st);
+                           cudaStream_t st, float4* pos4c = nullptr);
 
 // k_pair.cu (FP64 form; FP32 calls are forwarded to k_pair32.cu)
 int pair_threads(int prec, int n, int sms);
@@ -55,7 +55,7 @@ int pair_blocks(int prec, int n, int sms);
 // writes the neighbour list the dual-criteria integrator uses.
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st, double* vol = nullptr);
+                           cudaStream_t st, double* vol = nullptr, const float4* pos4c = nullptr);
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
@@ -65,7 +65,7 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
 int nbl_capacity(int dim);
 cudaError_t launch_density32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K, void* vr,
                              const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                             cudaStream_t st);
+                             cudaStream_t st, const float4* pos4c);
 cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                             const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                             const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,

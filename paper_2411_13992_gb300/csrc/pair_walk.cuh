@@ -1,9 +1,11 @@
 // pair_walk.cuh -- candidate walks over the 5^D cells around a particle's
 // cell, on cell-relative FP32 positions (pos4 = {offset from the cell
-// origin, m or h}).  Both visit the candidates in the same order: cells by
-// (dz, dy, dx) ascending (periodic images in the order of the stencil step),
-// particles by index within a cell.  Used by the FP32 pair passes and, as a
-// prefilter in front of the exact FP64 test, by the FP64 density pass.
+// origin, m or h}; at uniform resolution the FP32 density pass walks a copy
+// with the bits of the cell index in w).  Both visit the candidates in the
+// same order: cells by (dz, dy, dx) ascending (periodic images in the order
+// of the stencil step), particles by index within a cell.  Used by the FP32
+// pair passes and, as a prefilter in front of the exact FP64 test, by the
+// FP64 density pass.
 #pragma once
 
 #include "common.cuh"
@@ -70,8 +72,11 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 // row is cut to the cells within the remaining half-chord; every margin is
 // 1e-3 of a cell edge, far above FP32 rounding, so every candidate that the
 // full stencil would accept is still visited, in the same order.  About 2/3
-// of the 5^3 cells remain in 3-D.
-template <int DIM, bool TWO = true, typename F>
+// of the 5^3 cells remain in 3-D.  CELL_IN_W: the cell index of each
+// candidate is read from the bits of pos4.w (the copy with the cell index
+// that the permute writes at uniform resolution) instead of a separate load
+// from cell_of.
+template <int DIM, bool TWO = true, bool CELL_IN_W = false, typename F>
 __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach, int cell_i, const Grid& G,
                                                     const int32_t* __restrict__ start,
                                                     const int32_t* __restrict__ cell_of,
@@ -146,14 +151,20 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                     }
                     f(j, code_row + (uint32_t)dx, pj, r2, rxy.x, rxy.y, rz_);
                 };
+                auto cell_at = [&](int j, const float4& pj) {
+                    return CELL_IN_W ? __float_as_int(pj.w) : cell_of[j];
+                };
                 int j = start[cell];
                 for (; TWO && j + 1 < jend; j += 2) {
                     const float4 p0 = pos4[j], p1 = pos4[j + 1];
-                    const int d0 = cell_of[j] - kr, d1 = cell_of[j + 1] - kr;
+                    const int d0 = cell_at(j, p0) - kr, d1 = cell_at(j + 1, p1) - kr;
                     one(j, p0, d0);
                     one(j + 1, p1, d1);
                 }
-                for (; j < jend; ++j) one(j, pos4[j], cell_of[j] - kr);
+                for (; j < jend; ++j) {
+                    const float4 pj = pos4[j];
+                    one(j, pj, cell_at(j, pj) - kr);
+                }
             }
         }
     }

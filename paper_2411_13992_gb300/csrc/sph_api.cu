@@ -54,6 +54,7 @@ struct sph_ctx {
     int32_t *key, *perm_tmp, *perm, *count, *cursor, *start, *scan_tmp;
     void* vr;
     float4* pos4;
+    float4* pos4c;      // FP32 form, uniform h: pos4 with the cell index bits in w
     int32_t* cell;
     float* mf;
     uint32_t* nbl;      // neighbour lists of the density pass [cap][n], transposed
@@ -261,6 +262,7 @@ size_t carve(sph_ctx* c, char* base)
     c->scan_tmp = W.take<int32_t>(scan_temp_elems((int)nc1));
     c->vr = W.take<char>(n * 4 * rs);
     c->pos4 = W.take<float4>(n);     // both forms: FP32 cell-relative positions for the candidate walks
+    c->pos4c = c->prec == 32 && c->P.h_min == c->P.h_max ? W.take<float4>(n) : nullptr;
     c->cell = W.take<int32_t>(n);
     c->mf = W.take<float>(n);
     const bool lists = !c->density_only;   // both forms: the force pass walks the density pass's list
@@ -365,7 +367,7 @@ sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
     SPH_MARK(SPH_K_ORDER, 1);
     SPH_MARK(SPH_K_PERMUTE, 0);
     SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
-                          c->mf, c->K32.uniform_h, carry_ad, c->st));
+                          c->mf, c->K32.uniform_h, carry_ad, c->st, c->pos4c));
     ++c->launches;
     SPH_MARK(SPH_K_PERMUTE, 1);
     c->cur = 1 - c->cur;
@@ -380,7 +382,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int n = (int)c->n;
     if (!pairs) {
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->vol));
+                              c->nbl, c->nbc, c->st, c->vol, c->pos4c));
         SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->G.sms, c->st));
         SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
                                count_step, c->st));
@@ -390,7 +392,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int write_ad = 1;
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->nbl,
-                          c->nbc, c->st, c->vol));
+                          c->nbc, c->st, c->vol, c->pos4c));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_FORCES, 0);
     SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->mf, c->vr, c->pos4, c->cell,
@@ -439,7 +441,7 @@ sph_status run_dual_step(sph_ctx* c)
     SPH_TRY(run_sort(c, 2, 0));
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                          c->nbl, c->nbc, c->st, c->vol));
+                          c->nbl, c->nbc, c->st, c->vol, c->pos4c));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_ADVECT, 0);
     SPH_CU(launch_dual_begin(c->P, c->diag, c->du, c->st));
@@ -991,7 +993,7 @@ sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr
         // density pass now (a and dr travel with the sort)
         SPH_TRY(run_sort(c, 0, 1));
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->vol));
+                              c->nbl, c->nbc, c->st, c->vol, c->pos4c));
         ++c->launches;
         c->cells_pending = 0;
     }
