@@ -430,11 +430,11 @@ def run_native(args):
                 "not the roofline figure"}
     # what binds the two FP32 pair kernels, from the committed ncu summary
     # (96^3, one launch each): instruction issue, not the FMA pipe or HBM
-    roof_d["binding"] = {"limiter": "instruction issue", "issue_active": 0.748, "lanes_active_per_warp_instr": 19.1,
-                         "fma_pipe": 0.313, "dram_throughput": 0.095,
+    roof_d["binding"] = {"limiter": "instruction issue", "issue_active": 0.769, "lanes_active_per_warp_instr": 19.0,
+                         "fma_pipe": 0.326, "dram_throughput": 0.108,
                          "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
-    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.779, "lanes_active_per_warp_instr": 31.9,
-                         "fma_pipe": 0.507, "dram_throughput": 0.119,
+    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.784, "lanes_active_per_warp_instr": 31.9,
+                         "fma_pipe": 0.510, "dram_throughput": 0.120,
                          "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
     f64_ms, f64_cnt = prof64["forces"]
     f64_tflops = pairs * FLOPS_PER_PAIR_FP64 / (f64_ms / max(f64_cnt, 1) * 1e-3) / 1e12
