@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
 // ------------------------------------------------------------------ forces
 
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32, 10) k_forces32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __restrict__ pos4,
                                                      const int32_t* __restrict__ cell_of,
                                                      const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                      StateSet<float> S, const float* __restrict__ mf,
