@@ -433,8 +433,8 @@ def run_native(args):
     roof_d["binding"] = {"limiter": "instruction issue", "issue_active": 0.769, "lanes_active_per_warp_instr": 19.0,
                          "fma_pipe": 0.326, "dram_throughput": 0.108,
                          "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
-    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.784, "lanes_active_per_warp_instr": 31.9,
-                         "fma_pipe": 0.510, "dram_throughput": 0.120,
+    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.814, "lanes_active_per_warp_instr": 31.9,
+                         "fma_pipe": 0.549, "dram_throughput": 0.134,
                          "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
     f64_ms, f64_cnt = prof64["forces"]
     f64_tflops = pairs * FLOPS_PER_PAIR_FP64 / (f64_ms / max(f64_cnt, 1) * 1e-3) / 1e12
