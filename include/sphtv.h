@@ -166,8 +166,9 @@ SPH_API sph_status sph_default_params(sph_params* p);
  * The cell grid follows from dim, lo, L, periodic and h_max: along each
  * axis floor(L / h_max) cells of edge >= h_max, so the neighbours of a
  * particle lie in the 5^D cells around its own (at least 5 cells along
- * periodic axes, else SPH_ERR_ARG).  Returns SPH_ERR_ARG on invalid
- * parameters. */
+ * periodic axes, else SPH_ERR_ARG).  The grid may have at most 2^20 cells
+ * along an axis and 2^30 cells in all (else SPH_ERR_ARG, before anything is
+ * sized or enqueued).  Returns SPH_ERR_ARG on invalid parameters. */
 SPH_API sph_status sph_query_workspace(const sph_params* p, int64_t n, size_t* bytes);
 
 /* Create a context on the current CUDA device.  workspace: device memory
@@ -347,9 +348,12 @@ SPH_API sph_status sph_force_pass_adjoint(sph_ctx* ctx, const double* x, const d
  * Its scratch is one fixed array in device memory inside the library,
  * 24 MiB on every GPU that loads it, held until the process exits; n above
  * SPH_NOALLOC_MAX_PARTICLES or a cell grid above SPH_NOALLOC_MAX_CELLS cells
- * returns SPH_ERR_WORKSPACE before any work is enqueued.  The first call on
- * each device looks up the scratch's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one
+ * returns SPH_ERR_WORKSPACE before any work is enqueued.  A call made
+ * outside stream capture looks up the scratch's device address on the
+ * current device (cudaGetSymbolAddress) and remembers it; a call made while
+ * the stream is being captured uses the remembered address, so make a first
+ * call on each device before any capture (otherwise SPH_ERR_STATE).  After a
+ * device reset, make a call outside capture before capturing again.  All calls share the one
  * scratch: the call clears the counters it sums into, but two calls whose
  * work overlaps on the GPU (different streams, or different host threads)
  * race on it and must be serialised by the caller.  Device-side input checks

@@ -109,6 +109,9 @@ struct sph_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+// Largest cell grid (product over the axes) a context accepts: cell indices
+// and the scan of the cell counts are int.
+constexpr int64_t kMaxCells = (int64_t)1 << 30;
 
 struct Carver {
     char* base;
@@ -137,11 +140,17 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
     if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
     if (p->integrator == SPH_INT_DUAL && (p->fixed_dt != 0.0 || p->adjoint_steps != 0)) return SPH_ERR_ARG;
+    // the cell grid: each axis and the product of all axes bounded, so that
+    // cell indices, the count and start arrays and the workspace size stay
+    // within int (the product is taken in int64 before anything is sized)
+    int64_t ncell = 1;
     for (int d = 0; d < p->dim; ++d) {
-        if (!(p->L[d] > 0) || !std::isfinite(p->lo[d])) return SPH_ERR_ARG;
+        if (!(p->L[d] > 0) || !std::isfinite(p->lo[d]) || !std::isfinite(p->L[d])) return SPH_ERR_ARG;
         double nc = std::floor(p->L[d] * kStencilR / (2.0 * p->h_max));
         if (p->periodic[d] && nc < 2 * kStencilR + 1) return SPH_ERR_ARG;
-        if (nc > 1 << 20) return SPH_ERR_ARG;
+        if (!(nc <= (double)(1 << 20))) return SPH_ERR_ARG;
+        ncell *= nc < 1 ? 1 : (int64_t)nc;
+        if (ncell > kMaxCells) return SPH_ERR_ARG;
     }
     return SPH_OK;
 }
@@ -1256,17 +1265,35 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch on the current device; looked up once per
-// device (the first call on a device does this).
-sph_status noalloc_scratch(void** out)
+// Device address of the scratch on the current device.  Outside stream
+// capture every call looks it up again (cheap once the library's device code
+// is loaded), so an address cached before a device reset -- after which the
+// device code is loaded anew, possibly elsewhere -- is never used.  During a
+// capture the lookup (which may load the device code) is not made: the
+// address of the last call outside capture on this device is used, and a
+// capture with no earlier call on the device is refused (SPH_ERR_STATE).
+sph_status noalloc_scratch(cudaStream_t st, void** out)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPH_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SPH_ERR_CUDA;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SPH_ERR_CUDA;
+        }
         g_noalloc_addr[dev] = p;
+    } else if (!g_noalloc_addr[dev]) {
+        return SPH_ERR_STATE;
     }
     *out = g_noalloc_addr[dev];
     return SPH_OK;
@@ -1285,7 +1312,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     const Grid G = make_grid(p);
     if (G.ncell > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_WORKSPACE;
     void* base = nullptr;
-    s = noalloc_scratch(&base);
+    s = noalloc_scratch((cudaStream_t)stream, &base);
     if (s != SPH_OK) return s;
 
     // Lay out a context-like view over the scratch (host struct only).

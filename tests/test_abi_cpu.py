@@ -147,3 +147,26 @@ def test_particle_count_limit_is_two_to_the_25(lib):
     with pytest.raises(sph.SphError) as e:
         sph.sph_query_workspace(p, 2 ** 25 + 1)
     assert e.value.status == 1
+
+
+def test_cell_grid_product_is_bounded_before_anything_is_sized(lib):
+    """A grid whose axes are each within 2^20 cells but whose product exceeds
+    2^30 (here 2^16 x 2^16 = 2^32, which would wrap an int cell count to 0) is
+    refused by the host check of every entry that sizes or fills a grid,
+    before any pointer is touched or any work is enqueued."""
+    c = cases.tgv2d(20)
+    p = sph.params_from_case(c, 64)
+    p.periodic[0] = p.periodic[1] = 0
+    p.L[0] = p.L[1] = 65536 * p.h_max            # floor(L / h_max) = 2^16 cells per axis
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_query_workspace(p, c["n"])
+    assert e.value.status == 1
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_create(p, c["n"], 0x100000, 1 << 40, 0)      # never dereferenced
+    assert e.value.status == 1
+    bogus = ctypes.c_void_p(0x100000)                        # never dereferenced
+    st = lib.sph_density_noalloc(ctypes.byref(p), 1000, bogus, bogus, bogus, None, None, bogus, None)
+    assert st == 1
+    # one cell fewer than the bound along the second axis is accepted
+    p.L[1] = 16383 * p.h_max                                 # 2^16 x (2^14 - 1) < 2^30 cells
+    assert sph.sph_query_workspace(p, c["n"]) > 0

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2411_13992_gb300 as sph
 from paper_2411_13992_gb300 import cases
 
@@ -22,9 +23,9 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
 
 
-def _workspace_rho(case):
+def _workspace_rho(case, sigma0=None):
     sim = sph.Simulation(case, precision=64)
-    sim.set_state()
+    sim.set_state(sigma0=sigma0)
     sim.build_cells()
     sim.sync()
     rho = sim.get_state()["rho"]
@@ -63,6 +64,53 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     case = cases.tgv2d(257)                      # 66,049 > 65,536 particles
     assert case["n"] > sph.NOALLOC_MAX_PARTICLES
     p = sph.params_from_case(case, 64)
+    x, h, m, kind = _device_inputs(case)
+    rho = torch.zeros(case["n"], dtype=torch.float64, device=x.device)
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_density_noalloc(p, case["n"], x, h, m, kind, None, rho, torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == 3                   # SPH_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert float(rho.abs().max()) == 0.0         # nothing was written
+
+
+def _small_cylinder():
+    """The variable-resolution layout (h ratio 2 with a blend, walls) at a
+    size the scratch holds: a 12 x 8 periodic box, D = 1."""
+    return cases.cylinder2d(res=6, box=(12.0, 8.0), center=(4.0, 4.0), refine=(3.0, 9.0, 2.5, 5.5))
+
+
+def test_noalloc_with_given_sigma0_and_variable_resolution():
+    """sigma0 passed in (not the lattice sums the call would compute) and
+    per-particle h (the variable-resolution walk), on two calls in a row."""
+    stream = torch.cuda.current_stream()
+    for case in (_small_cylinder(), cases.tgv2d(64)):
+        assert case["n"] <= sph.NOALLOC_MAX_PARTICLES
+        # a sigma0 that differs from the lattice sums, so that using the
+        # wrong one shows: the lattice sums scaled by a seeded factor
+        s0 = oracle.sigma0_for(case, 2) * (1.0 + 0.01 * cases.uniform(np.arange(case["n"]), 0, 7))
+        ref = _workspace_rho(case, sigma0=s0)
+        p = sph.params_from_case(case, 64)
+        x, h, m, kind = _device_inputs(case)
+        s0_dev = torch.from_numpy(s0).to(x.device)
+        rho = torch.empty(case["n"], dtype=torch.float64, device=x.device)
+        for _ in range(2):
+            rho.fill_(float("nan"))
+            sph.sph_density_noalloc(p, case["n"], x, h, m, kind, s0_dev, rho, stream.cuda_stream)
+            torch.cuda.synchronize()
+            got = rho.cpu().numpy()
+            assert np.isfinite(got).all()
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err <= TOL64, (case["name"], err)
+
+
+def test_noalloc_rejects_cell_grids_beyond_its_scratch():
+    """Few particles, but a non-periodic box whose cell grid (257 x 257 cells)
+    exceeds the scratch's SPH_NOALLOC_MAX_CELLS: refused, nothing written."""
+    case = cases.tgv2d(20)
+    p = sph.params_from_case(case, 64)
+    p.periodic[0] = p.periodic[1] = 0
+    p.L[0] = p.L[1] = 257.5 * p.h_max
+    assert case["n"] <= sph.NOALLOC_MAX_PARTICLES
     x, h, m, kind = _device_inputs(case)
     rho = torch.zeros(case["n"], dtype=torch.float64, device=x.device)
     with pytest.raises(sph.SphError) as e:
