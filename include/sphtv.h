@@ -136,6 +136,11 @@ typedef struct sph_params {
                                time from a captured CUDA graph on a library-owned stream,
                                ordered after and before the context's stream by events
                                (same results, fewer launches); 0: always launch directly */
+    int32_t pair_tiles;     /* FP32 form at uniform resolution (h_min == h_max): 1 (default)
+                               runs the density pass on cell-blocked shared-memory tiles
+                               (a block of cells and the two cells around it staged per
+                               thread block); 0 walks the cell rows in global memory.  Both
+                               give the same results bit for bit; ignored otherwise */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -158,7 +163,7 @@ typedef struct sph_ctx sph_ctx;
 
 /* Fill *p with the paper's constants: riemann_eta 3, tv_xi -0.2, tv_C 1e3,
  * tv_thresh 5e-4, cfl_ad 0.25, cfl_ac 0.6, tv_mode limited, tv_h h_min,
- * h_pair mean, kahan on, graphs on, precision 64, dim 2, rho0 1.  Returns
+ * h_pair mean, kahan on, graphs on, pair_tiles on, precision 64, dim 2, rho0 1.  Returns
  * SPH_ERR_ARG on NULL. */
 SPH_API sph_status sph_default_params(sph_params* p);
 

@@ -61,6 +61,7 @@ class SphParams(ctypes.Structure):
         ("fixed_dt", ctypes.c_double),
         ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32),
         ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("graphs", ctypes.c_int32),
+        ("pair_tiles", ctypes.c_int32),
     ]
 
 

@@ -475,10 +475,10 @@ int pair_blocks(int prec, int n, int sms) { return nblk(n, pair_threads(prec, n,
 
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st, double* vol, const float4* pos4c)
+                           cudaStream_t st, double* vol, const float4* pos4c, int tiles)
 {
     const int T = pair_threads(prec, n, G.sms);
-    if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st, pos4c);
+    if (prec == 32) return launch_density32(dim, n, S, start, G, K, vr, pos4, cell_of, nbl, nbc, st, pos4c, tiles);
     auto s = *(StateSet<double>*)S;
     auto k = *(const Consts<double>*)K;
     const int cap = nbl_capacity(dim);

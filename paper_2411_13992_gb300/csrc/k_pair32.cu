@@ -137,6 +137,271 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     vr[i] = make_float4(vi[0], vi[1], vi[2], w);
 }
 
+// ------------------------------------------------- density on cell-blocked tiles
+//
+// The same density pass at uniform resolution, one thread block per block of
+// B0 x B1 (x B2) home cells.  The block first stages the offsets of every
+// particle in the home cells and the R = 2 cells around them (the halo,
+// H = B + 2R cells per axis, periodic images resolved) into shared memory,
+// in halo x-major order, with the halo x index of each particle's cell in w.
+// Then each thread walks its home particle's clipped 5^D stencil row by row
+// over that tile: each (dy, dz) row of the stencil is one contiguous run of
+// the tile (no periodic split, no per-row global loads), and the x step of a
+// candidate is the difference of the halo x indices.  The visit order is the
+// row walk's (rows by (dz, dy), cells by dx, particles by index within a
+// cell) and the arithmetic is the same, so sigma and the neighbour list are
+// bit for bit those of k_density32.  A block whose halo holds more particles
+// than the tile takes the row walk over global memory instead.
+
+template <int DIM> struct TileShape;
+template <> struct TileShape<3> { static constexpr int B0 = 4, B1 = 4, B2 = 4, T = 160; };
+template <> struct TileShape<2> { static constexpr int B0 = 8, B1 = 8, B2 = 1, T = 128; };
+
+template <int DIM> struct TileDims {
+    using S = TileShape<DIM>;
+    static constexpr int R = kStencilR;
+    static constexpr int H0 = S::B0 + 2 * R, H1 = S::B1 + 2 * R, H2 = DIM == 3 ? S::B2 + 2 * R : 1;
+    static constexpr int NHC = H0 * H1 * H2;        // halo cells
+    static constexpr int NHR = H1 * H2;             // halo rows along x
+    static constexpr int NHOME = S::B1 * S::B2;     // home rows along x
+};
+
+// Coordinate of halo cell v (relative to the grid origin) along axis d:
+// wrapped on periodic axes, -1 outside a non-periodic axis.
+__device__ __forceinline__ int halo_coord(const Grid& G, int v, int d)
+{
+    const int nc = G.nc[d];
+    if (G.periodic[d]) return ((v % nc) + nc) % nc;
+    return (v >= 0 && v < nc) ? v : -1;
+}
+
+// In-place exclusive scan of a[0, len) by the T threads of the block, total
+// in a[len].  s_warp holds T/32 + 1 ints.
+template <int T>
+__device__ __forceinline__ void block_exclusive_scan(int* a, int len, int* s_warp)
+{
+    static_assert(T % 32 == 0, "whole warps");
+    const int ipt = (len + T - 1) / T;
+    const int b = threadIdx.x * ipt;
+    int sum = 0;
+    for (int k = 0; k < ipt; ++k)
+        if (b + k < len) sum += a[b + k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < T / 32; ++k) {
+            const int t = s_warp[k];
+            s_warp[k] = acc;
+            acc += t;
+        }
+        s_warp[T / 32] = acc;
+    }
+    __syncthreads();
+    int run = s_warp[w] + x - sum;
+    for (int k = 0; k < ipt; ++k)
+        if (b + k < len) {
+            const int t = a[b + k];
+            a[b + k] = run;
+            run += t;
+        }
+    if (threadIdx.x == 0) a[len] = s_warp[T / 32];
+    __syncthreads();
+}
+
+// Bytes of dynamic shared memory of the tile kernel for a tile of cap particles.
+template <int DIM>
+constexpr size_t tile_smem_bytes(int cap)
+{
+    return (size_t)cap * (sizeof(float4) + sizeof(int)) + (size_t)(2 * TileDims<DIM>::NHC + 1) * sizeof(int);
+}
+
+template <int DIM, typename Acc>
+__global__ void __launch_bounds__(TileShape<DIM>::T) k_density32_tile(
+    int n, const float4* __restrict__ pos4c, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ start,
+    Grid G, Consts<float> K, StateSet<float> S, float4* __restrict__ vr, uint32_t* __restrict__ nbl,
+    int32_t* __restrict__ nbc, int cap, int nb0, int nb1, int tile_cap)
+{
+    using TD = TileDims<DIM>;
+    using SH = TileShape<DIM>;
+    constexpr int T = SH::T, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
+    constexpr int Rz = DIM == 3 ? R : 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_pos = (float4*)smem;                   // [tile_cap] offsets, w = halo x index of the cell
+    int* s_gid = (int*)(s_pos + tile_cap);           // [tile_cap] global particle index
+    int* s_ts = s_gid + tile_cap;                    // [NHC + 1] tile start of each halo cell
+    int* s_gs = s_ts + NHC + 1;                      // [NHC] global start of each halo cell
+    __shared__ int s_warp[T / 32 + 1];
+    __shared__ int s_home[TD::NHOME + 1];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = blockIdx.x;
+    const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+    const int cx0 = bx * SH::B0, cy0 = by * SH::B1, cz0 = bz * SH::B2;
+    const int bxn = min(SH::B0, G.nc[0] - cx0), byn = min(SH::B1, G.nc[1] - cy0);
+    const int bzn = DIM == 3 ? min(SH::B2, G.nc[2] - cz0) : 1;
+
+    // 1. counts and global starts of the halo cells
+    for (int c = tid; c < NHC; c += T) {
+        const int hx = c % H0, hy = (c / H0) % H1, hz = c / (H0 * H1);
+        const int gx = halo_coord(G, cx0 + hx - R, 0), gy = halo_coord(G, cy0 + hy - R, 1);
+        const int gz = DIM == 3 ? halo_coord(G, cz0 + hz - R, 2) : 0;
+        int cnt = 0, gs = 0;
+        if (gx >= 0 && gy >= 0 && gz >= 0) {
+            const int g = gx + G.nc[0] * (gy + G.nc[1] * gz);
+            gs = start[g];
+            cnt = start[g + 1] - gs;
+        }
+        s_gs[c] = gs;
+        s_ts[c] = cnt;
+    }
+    __syncthreads();
+    block_exclusive_scan<T>(s_ts, NHC, s_warp);
+    const bool fits = s_ts[NHC] <= tile_cap;
+
+    // 2. stage the tile: one warp per halo row, the particles of a row being
+    // one or two contiguous runs of the cell-sorted offsets
+    if (fits) {
+        for (int r = warp; r < TD::NHR; r += T / 32) {
+            const int c0 = r * H0;
+            const int t1 = s_ts[c0 + H0];
+            for (int t = s_ts[c0] + lane; t < t1; t += 32) {
+                int lo = 0, hi = H0 - 1;           // the cell of t: last k with s_ts[c0 + k] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_ts[c0 + mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int c = c0 + lo;
+                const int g = s_gs[c] + (t - s_ts[c]);
+                float4 p = pos4c[g];
+                p.w = __int_as_float(lo);
+                s_pos[t] = p;
+                s_gid[t] = g;
+            }
+        }
+    }
+    // home rows: prefix counts of the home particles, row by row
+    if (tid == 0) {
+        int acc = 0;
+        for (int k = 0; k < byn * bzn; ++k) {
+            const int hy = R + k % byn, hz = Rz + k / byn;
+            const int c = (hy + H1 * hz) * H0 + R;
+            s_home[k] = acc;
+            acc += s_ts[c + bxn] - s_ts[c];
+        }
+        s_home[byn * bzn] = acc;
+    }
+    __syncthreads();
+    const int nhome = s_home[byn * bzn];
+
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    const float inv_ex = 1.f / ex;
+    const float reach = 2.f * K.h_u;
+    const float reach2 = reach * reach;
+    for (int t = tid; t < nhome; t += T) {
+        int k = 0;
+        while (s_home[k + 1] <= t) ++k;
+        const int hy_i = R + k % byn, hz_i = Rz + k / byn;
+        const int c_row = (hy_i + H1 * hz_i) * H0 + R;
+        const int i = s_gs[c_row] + (t - s_home[k]);      // home rows are contiguous in the global order
+        const int8_t kind = S.kind[i];
+        const float s0 = (float)S.s0[i];
+        float vi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
+        if (kind) {
+            vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
+            nbc[i] = 0;
+            continue;
+        }
+        Acc sigma;
+        int cnt = 0;
+        uint32_t* lp = nbl + i;
+        auto accept = [&](float r2, uint32_t entry) {
+            sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), K.inv_h_u));
+            if (r2 > 0.f) {
+                if (cnt < cap) {
+                    *lp = entry;
+                    lp += n;
+                }
+                ++cnt;
+            }
+        };
+        if (fits) {
+            const int s = s_ts[c_row] + (t - s_home[k]);
+            const float4 pi = s_pos[s];
+            const float oi[3] = {pi.x, pi.y, pi.z};
+            const int hx_i = __float_as_int(pi.w);
+            for (int dz = -Rz; dz <= Rz; ++dz) {
+                float rz = 0.f;
+                if (DIM == 3) {
+                    rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
+                    rz = fmaxf(rz - 1e-3f * ez, 0.f);
+                }
+                const float wz2 = reach2 - rz * rz;
+                if (wz2 <= 0.f) continue;
+                const float shz = -(float)dz * ez;
+                for (int dy = -R; dy <= R; ++dy) {
+                    float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
+                    ry = fmaxf(ry - 1e-3f * ey, 0.f);
+                    const float w2 = wz2 - ry * ry;
+                    if (w2 <= 0.f) continue;
+                    const float w = sqrtf(w2) + 1e-3f * ex;
+                    const int dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
+                    const int dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
+                    if (dxlo > dxhi) continue;
+                    const float shy = -(float)dy * ey;
+                    const int rowc = (hy_i + dy + H1 * (hz_i + dz)) * H0 + hx_i;
+                    const int tend = s_ts[rowc + dxhi + 1];
+                    const uint32_t code_row =
+                        (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R)) - (uint32_t)hx_i;
+                    auto one = [&](int tj, const float4& pj) {
+                        const int hxj = __float_as_int(pj.w);
+                        const float shx = -(float)(hxj - hx_i) * ex;
+                        const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
+                                                                 make_float2(oi[0], oi[1])),
+                                                      make_float2(shx, shy));
+                        const float2 q = __fmul2_rn(rxy, rxy);
+                        float r2 = q.x + q.y;
+                        if (DIM == 3) {
+                            const float rz_ = (oi[2] - pj.z) + shz;
+                            r2 = fmaf(rz_, rz_, r2);
+                        }
+                        if (r2 < K.four_h2_u)
+                            accept(r2, ((uint32_t)s_gid[tj] << kCodeBits) | (code_row + (uint32_t)hxj));
+                    };
+                    int tj = s_ts[rowc + dxlo];
+                    for (; tj + 1 < tend; tj += 2) {
+                        const float4 p0 = s_pos[tj], p1 = s_pos[tj + 1];
+                        one(tj, p0);
+                        one(tj + 1, p1);
+                    }
+                    if (tj < tend) one(tj, s_pos[tj]);
+                }
+            }
+        } else {
+            // the halo does not fit the tile: the row walk over global memory
+            const float4 pi = pos4c[i];
+            const float oi[3] = {pi.x, pi.y, pi.z};
+            auto visit = [&](int j, uint32_t code, const float4&, float r2, float, float, float) {
+                if (r2 < K.four_h2_u) accept(r2, ((uint32_t)j << kCodeBits) | code);
+            };
+            for_candidates_rows<DIM, true, true>(oi, reach, cell_of[i], G, start, cell_of, pos4c, visit);
+        }
+        nbc[i] = cnt;
+        const float w = K.rho0 * (sigma.value() - s0) / s0;
+        vr[i] = make_float4(vi[0], vi[1], vi[2], w);
+    }
+}
+
 // ------------------------------------------------------------------ forces
 
 template <int DIM, typename Acc, bool UNIFORM>
@@ -309,6 +574,37 @@ static void density_t(int n, const float4* pos4, const int32_t* cell_of, const i
                                                        nbl_capacity(DIM), pos4c);
 }
 
+// Particles the tile holds: the expected halo population (particles per
+// cell x halo cells) with a margin, in whole warps, between 256 and 4096.
+template <int DIM>
+static int tile_capacity(int n, const Grid& G)
+{
+    const double per_cell = (double)n / (double)G.ncell;
+    int cap = (int)(1.4 * per_cell * TileDims<DIM>::NHC) + 64;
+    cap = (cap + 31) / 32 * 32;
+    return cap < 256 ? 256 : (cap > 4096 ? 4096 : cap);
+}
+
+template <int DIM, typename Acc>
+static cudaError_t density_tile_t(int n, const float4* pos4c, const int32_t* cell_of, const int32_t* start,
+                                  const Grid& G, const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl,
+                                  int32_t* nbc, cudaStream_t st)
+{
+    using SH = TileShape<DIM>;
+    const int nb0 = (G.nc[0] + SH::B0 - 1) / SH::B0, nb1 = (G.nc[1] + SH::B1 - 1) / SH::B1;
+    const int nb2 = DIM == 3 ? (G.nc[2] + SH::B2 - 1) / SH::B2 : 1;
+    const int cap = tile_capacity<DIM>(n, G);
+    const size_t smem = tile_smem_bytes<DIM>(cap);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_density32_tile<DIM, Acc>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_density32_tile<DIM, Acc><<<nb0 * nb1 * nb2, SH::T, smem, st>>>(n, pos4c, cell_of, start, G, K, S, vr, nbl, nbc,
+                                                                     nbl_capacity(DIM), nb0, nb1, cap);
+    return cudaGetLastError();
+}
+
 template <int DIM, typename Acc, bool U>
 static void forces_t(int n, const float4* pos4, const int32_t* cell_of, const int32_t* start, const Grid& G,
                      const Consts<float>& K, StateSet<float> S, const float* mf, const float4* vr,
@@ -343,11 +639,17 @@ static void forces_t(int n, const float4* pos4, const int32_t* cell_of, const in
 
 cudaError_t launch_density32(int dim, int n, void* Sv, const int32_t* start, const Grid& G, const void* Kv, void* vr,
                              const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                             cudaStream_t st, const float4* pos4c)
+                             cudaStream_t st, const float4* pos4c, int tiles)
 {
     const StateSet<float> S = *(StateSet<float>*)Sv;
     const Consts<float>& K = *(const Consts<float>*)Kv;
     if (K.uniform_h && !pos4c) return cudaErrorInvalidValue;   // the uniform walk reads the cell-tagged copy
+    if (K.uniform_h && tiles) {
+        if (K.kahan) return dim == 2 ? density_tile_t<2, KSum>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st)
+                                     : density_tile_t<3, KSum>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
+        return dim == 2 ? density_tile_t<2, PlainF>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st)
+                        : density_tile_t<3, PlainF>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
+    }
     SPH_DISPATCH32(density_t, n, pos4, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st, pos4c);
     return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ int pair_blocks(int prec, int n, int sms);
 // writes the neighbour list the dual-criteria integrator uses.
 cudaError_t launch_density(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                            void* vr, const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                           cudaStream_t st, double* vol = nullptr, const float4* pos4c = nullptr);
+                           cudaStream_t st, double* vol = nullptr, const float4* pos4c = nullptr, int tiles = 0);
 cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                           const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                           const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,
@@ -63,9 +63,11 @@ cudaError_t launch_forces(int prec, int dim, int n, void* S, const int32_t* star
 
 // k_pair32.cu
 int nbl_capacity(int dim);
+// tiles: at uniform resolution, the pass on cell-blocked shared-memory tiles
+// (same results bit for bit as the row walk over global memory, tiles = 0)
 cudaError_t launch_density32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K, void* vr,
                              const float4* pos4, const int32_t* cell_of, uint32_t* nbl, int32_t* nbc,
-                             cudaStream_t st, const float4* pos4c);
+                             cudaStream_t st, const float4* pos4c, int tiles = 0);
 cudaError_t launch_forces32(int dim, int n, void* S, const int32_t* start, const Grid& G, const void* K,
                             const float* mf, const void* vr, const float4* pos4, const int32_t* cell_of,
                             const uint32_t* nbl, const int32_t* nbc, const double* dt, int kick_on, int write_ad,

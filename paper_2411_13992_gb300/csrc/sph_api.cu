@@ -139,6 +139,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
     if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
+    if (p->pair_tiles != 0 && p->pair_tiles != 1) return SPH_ERR_ARG;
     if (p->integrator == SPH_INT_DUAL && (p->fixed_dt != 0.0 || p->adjoint_steps != 0)) return SPH_ERR_ARG;
     // the cell grid: each axis and the product of all axes bounded, so that
     // cell indices, the count and start arrays and the workspace size stay
@@ -391,7 +392,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int n = (int)c->n;
     if (!pairs) {
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->vol, c->pos4c));
+                              c->nbl, c->nbc, c->st, c->vol, c->pos4c, c->P.pair_tiles));
         SPH_CU(launch_diag_only(c->prec, c->dim, n, cur_set(c), c->partials, c->G.sms, c->st));
         SPH_CU(launch_finalize(pair_blocks(c->prec, n, c->G.sms), c->partials, c->rows, c->P, c->diag, c->dt,
                                count_step, c->st));
@@ -401,7 +402,7 @@ sph_status run_forces(sph_ctx* c, int kick_on, int pairs, int count_step)
     const int write_ad = 1;
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell, c->nbl,
-                          c->nbc, c->st, c->vol, c->pos4c));
+                          c->nbc, c->st, c->vol, c->pos4c, c->P.pair_tiles));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_FORCES, 0);
     SPH_CU(launch_forces(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->mf, c->vr, c->pos4, c->cell,
@@ -450,7 +451,7 @@ sph_status run_dual_step(sph_ctx* c)
     SPH_TRY(run_sort(c, 2, 0));
     SPH_MARK(SPH_K_DENSITY, 0);
     SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                          c->nbl, c->nbc, c->st, c->vol, c->pos4c));
+                          c->nbl, c->nbc, c->st, c->vol, c->pos4c, c->P.pair_tiles));
     SPH_MARK(SPH_K_DENSITY, 1);
     SPH_MARK(SPH_K_ADVECT, 0);
     SPH_CU(launch_dual_begin(c->P, c->diag, c->du, c->st));
@@ -764,6 +765,7 @@ sph_status sph_default_params(sph_params* p)
     p->h_pair = SPH_HPAIR_MEAN;
     p->kahan = 1;
     p->graphs = 1;
+    p->pair_tiles = 1;
     return SPH_OK;
 }
 
@@ -1002,7 +1004,7 @@ sph_status sph_get_state(sph_ctx* c, double* x, double* v, double* a, double* dr
         // density pass now (a and dr travel with the sort)
         SPH_TRY(run_sort(c, 0, 1));
         SPH_CU(launch_density(c->prec, c->dim, n, cur_set(c), c->start, c->G, consts(c), c->vr, c->pos4, c->cell,
-                              c->nbl, c->nbc, c->st, c->vol, c->pos4c));
+                              c->nbl, c->nbc, c->st, c->vol, c->pos4c, c->P.pair_tiles));
         ++c->launches;
         c->cells_pending = 0;
     }
