@@ -310,6 +310,42 @@ def _timed_steps(torch, sim, steps, profile=True):
     return e0.elapsed_time(e1), prof
 
 
+def _rooflines(case, prof, peak_tflops, hbm_gbs, peak_note, kernel_names):
+    """Rooflines of the two FP32 pair kernels from a profiled pass (live CUDA
+    events on the library stream); the first one returned is the kernel with
+    the larger share of the step."""
+    n = case["n"]
+    pairs = _pairs_per_launch(case)
+    roof_d = _alu_roofline("density", kernel_names["density"], prof, pairs + n, FLOPS_PER_PAIR_DENSITY32,
+                           BYTES_PER_PARTICLE_DENSITY, n, peak_tflops, hbm_gbs)
+    roof_f = _alu_roofline("forces", kernel_names["forces"], prof, pairs, FLOPS_PER_PAIR_FP32,
+                           BYTES_PER_PARTICLE_FORCES, n, peak_tflops, hbm_gbs)
+    for r in (roof_d, roof_f):
+        r["peak_source"] = peak_note
+    d_s = roof_d["avg_launch_ms"] * 1e-3
+    roof_d["with_candidate_tests"] = {
+        "tflops": (pairs + n) * FLOPS_PER_PAIR_DENSITY32 / d_s / 1e12
+        + n * CANDIDATES_PER_PARTICLE * FLOPS_PER_CANDIDATE / d_s / 1e12,
+        "candidates_per_particle": CANDIDATES_PER_PARTICLE, "flops_per_candidate": FLOPS_PER_CANDIDATE,
+        "note": "implementation rate: the neighbour search's candidate tests added to the algorithmic flops; "
+                "not the roofline figure"}
+    # what binds each kernel, from the ncu counters of the committed summary
+    # (null once the kernel sources have changed since they were taken)
+    roof_d["binding"] = _profiled_counters("density", "binding")
+    roof_f["binding"] = _profiled_counters("forces", "binding")
+    dominant = prof["density"][0] >= prof["forces"][0]
+    return (roof_d, roof_f) if dominant else (roof_f, roof_d)
+
+
+def _kernel_shares(prof):
+    tot = max(sum(t[0] for t in prof.values()), 1e-9)
+    return {k: {"ms_per_step": v[0] / max(v[1], 1), "share": v[0] / tot} for k, v in prof.items() if v[1]}
+
+
+def _density_kernel_name(sim):
+    return "k_density32_tile<3,KSum>" if sim.params.pair_tiles else "k_density32<3,KSum,uniform>"
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -332,18 +368,23 @@ def run_native(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- FP32 form: the headline number
+    peaks, src = _peaks()
+    hbm_gbs = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    gpu_index = _gpu_index(torch, dev)
+
+    # ---- FP32 form: the headline number.  The timed region holds the K steps
+    # only: no per-kernel events inside it (the breakdown is a separate pass).
     sim = sph.Simulation(case, precision=32)
     sim.set_state()
     sim.build_cells()
     sim.step(args.warmup)
     sim.sync()
     launches0 = sim.launches()
-    sampler = ClockSampler(_gpu_index(torch, dev))
+    sampler = ClockSampler(gpu_index)
     sampler.start()
     barrier()
     sampler.mark(True)
-    ms, prof = _timed_steps(torch, sim, args.steps)
+    ms, _ = _timed_steps(torch, sim, args.steps, profile=False)
     sampler.mark(False)
     barrier()
     clocks = sampler.stop()
@@ -352,6 +393,36 @@ def run_native(args):
     total = sum_over_ranks(float(n * args.steps), torch, dist)
     value = total / (ms_max * 1e-3)
     diag = sim.diag()
+    step0 = args.warmup + 1
+    # per-kernel breakdown right after the headline steps (not headlined)
+    kp = max(1, args.prof_steps)
+    ms_p, prof = _timed_steps(torch, sim, kp, profile=True)
+    names = {"density": _density_kernel_name(sim), "forces": "k_forces32<3,KSum,uniform>"}
+
+    # ---- steady state: the lattice disorders as the flow develops and the
+    # row runs of a warp's lanes grow unequal; step on untimed to step
+    # args.steady_from, then time args.steady_steps steps (and a profiled pass)
+    steady = None
+    if args.steady_steps > 0:
+        done = args.warmup + args.steps + kp
+        if args.steady_from > done:
+            sim.step(args.steady_from - done)
+            sim.sync()
+        sampler2 = ClockSampler(gpu_index)
+        sampler2.start()
+        barrier()
+        sampler2.mark(True)
+        ms_s, _ = _timed_steps(torch, sim, args.steady_steps, profile=False)
+        sampler2.mark(False)
+        barrier()
+        clocks_s = sampler2.stop()
+        ms_s = max_over_ranks(ms_s, torch, dist)
+        _, prof_s = _timed_steps(torch, sim, kp, profile=True)
+        first = max(args.steady_from, done) + 1
+        steady = {"value": sum_over_ranks(float(n * args.steady_steps), torch, dist) / (ms_s * 1e-3),
+                  "unit": UNIT, "ms_per_step": ms_s / args.steady_steps, "steps": args.steady_steps,
+                  "first_step": first, "last_step": first + args.steady_steps - 1, "clocks": clocks_s,
+                  "kernels": _kernel_shares(prof_s), "prof": prof_s}
     sim.close()
 
     # ---- FP64 form, same workload
@@ -362,10 +433,11 @@ def run_native(args):
     sim64.sync()
     k64 = max(1, min(args.steps, args.fp64_steps))
     barrier()
-    ms64, prof64 = _timed_steps(torch, sim64, k64)
+    ms64, _ = _timed_steps(torch, sim64, k64, profile=False)
     barrier()
     ms64 = max_over_ranks(ms64, torch, dist)
     value64 = sum_over_ranks(float(n * k64), torch, dist) / (ms64 * 1e-3)
+    _, prof64 = _timed_steps(torch, sim64, 1, profile=True)
     sim64.close()
 
     # ---- dual-criteria integrator (Sec. 2.4), FP32, same workload: one step
@@ -379,8 +451,9 @@ def run_native(args):
         simd.sync()
         kd = max(1, min(args.steps, args.dual_steps))
         barrier()
-        msd, profd = _timed_steps(torch, simd, kd)
+        msd, _ = _timed_steps(torch, simd, kd, profile=False)
         barrier()
+        _, profd = _timed_steps(torch, simd, 2, profile=True)
         dd = simd.diag()
         simd.close()
         msd = max_over_ranks(msd, torch, dist)
@@ -405,48 +478,31 @@ def run_native(args):
     # ---- the other generated workloads (rank 0 of a single-GPU run only)
     others = _other_configs(torch, sph, cases, args) if (world == 1 and not args.no_configs) else None
 
-    # ---- rooflines of the two pair kernels (live event timing); the line's
-    # "roofline" is the one that takes the larger share of the step
-    peaks, src = _peaks()
-    hbm_gbs = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
-    pairs = _pairs_per_launch(case)
+    # ---- rooflines of the two pair kernels (live event timing of the
+    # profiled pass); the line's "roofline" is the one with the larger share
     peak_tflops = measured_fma_peak(torch, sph, 32)
     dfma_tflops = measured_fma_peak(torch, sph, 64)
     units_tflops = fp32_peak_tflops(peaks.get("sm_max_mhz", SM_MAX_MHZ))
     peak_note = ("measured: FP32 FMA microbenchmark (sph_fma_peak) on this GPU; unit counts x max SM clock give "
                  "%.1f TFLOP/s; HBM peak %s" % (units_tflops, src))
-    roof_d = _alu_roofline("density", "k_density32<3,KSum,uniform>", prof, pairs + n, FLOPS_PER_PAIR_DENSITY32,
-                           BYTES_PER_PARTICLE_DENSITY, n, peak_tflops, hbm_gbs)
-    roof_f = _alu_roofline("forces", "k_forces32<3,KSum,uniform>", prof, pairs, FLOPS_PER_PAIR_FP32,
-                           BYTES_PER_PARTICLE_FORCES, n, peak_tflops, hbm_gbs)
-    for r in (roof_d, roof_f):
-        r["peak_source"] = peak_note
-    d_s = roof_d["avg_launch_ms"] * 1e-3
-    roof_d["with_candidate_tests"] = {
-        "tflops": (pairs + n) * FLOPS_PER_PAIR_DENSITY32 / d_s / 1e12
-        + n * CANDIDATES_PER_PARTICLE * FLOPS_PER_CANDIDATE / d_s / 1e12,
-        "candidates_per_particle": CANDIDATES_PER_PARTICLE, "flops_per_candidate": FLOPS_PER_CANDIDATE,
-        "note": "implementation rate: the neighbour search's candidate tests added to the algorithmic flops; "
-                "not the roofline figure"}
-    # what binds the two FP32 pair kernels, from the committed ncu summary
-    # (96^3, one launch each): instruction issue, not the FMA pipe or HBM
-    roof_d["binding"] = {"limiter": "instruction issue", "issue_active": 0.769, "lanes_active_per_warp_instr": 19.0,
-                         "fma_pipe": 0.326, "dram_throughput": 0.108,
-                         "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
-    roof_f["binding"] = {"limiter": "instruction issue", "issue_active": 0.814, "lanes_active_per_warp_instr": 31.9,
-                         "fma_pipe": 0.549, "dram_throughput": 0.134,
-                         "source": "profiles/pair_kernels_tgv3d_96_ncu.md"}
+    roof, roof_other = _rooflines(case, prof, peak_tflops, hbm_gbs, peak_note, names)
+    pairs = _pairs_per_launch(case)
     f64_ms, f64_cnt = prof64["forces"]
     f64_tflops = pairs * FLOPS_PER_PAIR_FP64 / (f64_ms / max(f64_cnt, 1) * 1e-3) / 1e12
-    roof_f["fp64_forces"] = {"achieved": f64_tflops, "peak": dfma_tflops, "frac": f64_tflops / dfma_tflops,
-                             "flops_per_pair": FLOPS_PER_PAIR_FP64,
-                             "peak_source": "measured: FP64 FMA microbenchmark (sph_fma_peak)",
-                             "binding": {"limiter": "FP64 pipe", "fp64_pipe_active": 0.877,
-                                         "source": "profiles/fp64_pair_kernels_tgv3d_96_ncu.md"}}
-    dominant = prof["density"][0] >= prof["forces"][0]
-    roof, roof_other = (roof_d, roof_f) if dominant else (roof_f, roof_d)
-    kernels = {k: {"ms_per_step": v[0] / max(v[1], 1), "share": v[0] / max(sum(t[0] for t in prof.values()), 1e-9)}
-               for k, v in prof.items()}
+    fp64_forces = {"achieved": f64_tflops, "peak": dfma_tflops, "frac": f64_tflops / dfma_tflops,
+                   "flops_per_pair": FLOPS_PER_PAIR_FP64,
+                   "peak_source": "measured: FP64 FMA microbenchmark (sph_fma_peak)",
+                   "binding": _profiled_counters("forces_f64", "binding")}
+    if steady is not None:
+        prof_s = steady.pop("prof")
+        steady["roofline"], steady["roofline_other_pair_kernel"] = _rooflines(case, prof_s, peak_tflops, hbm_gbs,
+                                                                              peak_note, names)
+
+    # ---- the larger lattice of the same workload family, 256^3 (rank 0 of a
+    # single-GPU run only)
+    big = None
+    if world == 1 and args.big_n > 0:
+        big = _big_lattice(torch, sph, cases, args, peak_tflops, hbm_gbs, peak_note)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -454,7 +510,8 @@ def run_native(args):
         rate, el, nn = oracle_rate(args.cpu_n, 1, 0, threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "one FP64 oracle step (cell-list neighbours, OpenMP) of the 3-D Taylor-Green at %d^3 = %d "
-                         "particles, %.1f s" % (args.cpu_n, nn, el)}
+                         "particles, %.1f s" % (args.cpu_n, nn, el),
+               "parity_sample": _parity_sample(torch, sph, cases)}
 
     if rank == 0:
         line = {
@@ -463,16 +520,23 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles_per_gpu": n, "precision": "FP32 pair sums (Kahan), FP64 "
                        "positions and reductions", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "timed_steps": "steps %d-%d of the run" % (step0, step0 + args.steps - 1),
+                       "density_pass": names["density"],
                        "l2": "inputs larger than L2 (%.0f MB state per GPU)" % (sph.sph_query_workspace(
                            sph.params_from_case(case, 32), n) / 1e6)},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
-                     "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof64.items()}},
+                     "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof64.items() if v[1]},
+                     "forces_roofline": fp64_forces},
             "fp32_over_fp64": value / value64,
             "simulated_time_per_s": diag["dt"] * args.steps / (ms_max * 1e-3),
+            "steady_state": steady,
+            "tgv3d_256": big,
             "dual_criteria": dual,
             "roofline": roof,
             "roofline_other_pair_kernel": roof_other,
-            "kernels": kernels,
+            "kernels": _kernel_shares(prof),
+            "kernels_pass": "a profiled pass of %d steps right after the timed steps (CUDA events per kernel "
+                            "class on the library stream), not part of the timed region" % kp,
             "e2e": e2e,
             "adjoint": adjoint,
             "other_configs": others,
@@ -488,6 +552,80 @@ def run_native(args):
     return 0
 
 
+def _big_lattice(torch, sph, cases, args, peak_tflops, hbm_gbs, peak_note):
+    """The 3-D Taylor-Green at args.big_n^3 (256^3 = 16,777,216 particles),
+    FP32: args.big_steps timed steps after 3 warm-up steps, then a profiled
+    pass for the kernel breakdown and the rooflines."""
+    c = cases.tgv3d(args.big_n)
+    sim = sph.Simulation(c, precision=32)
+    sim.set_state()
+    sim.build_cells()
+    sim.step(3)
+    sim.sync()
+    k = max(1, args.big_steps)
+    ms, _ = _timed_steps(torch, sim, k, profile=False)
+    _, prof = _timed_steps(torch, sim, 5, profile=True)
+    names = {"density": _density_kernel_name(sim), "forces": "k_forces32<3,KSum,uniform>"}
+    sim.close()
+    roof, roof_other = _rooflines(c, prof, peak_tflops, hbm_gbs, peak_note, names)
+    return {"workload": "3-D Taylor-Green vortex %d^3 = %d particles" % (args.big_n, c["n"]),
+            "value": c["n"] * k / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+            "timed_steps": "steps 4-%d" % (3 + k), "kernels": _kernel_shares(prof), "roofline": roof,
+            "roofline_other_pair_kernel": roof_other}
+
+
+def _parity_sample(torch, sph, cases):
+    """Measured per-field errors of the FP32 and FP64 GPU steps against the
+    FP64 oracle, one step from the same state (3-D Taylor-Green 24^3 =
+    13,824 particles, same h/dp as the workload): normwise relative,
+    max_i |q_i - q_i^ref| / max_i |q_i^ref| per field, with the bound each
+    field is tested to."""
+    import numpy as np
+    import oracle
+    c = cases.tgv3d(24)
+    P = oracle.make_params(3, c["lo"], c["L"], c["periodic"], c["rho0"], c["c"], c["eta"], c["h_min"],
+                           u_ref=c["u_ref"])
+    s0 = oracle.sigma0_for(c, 3)
+    fp = oracle.force_pass(P, c, c["x"], c["v"], s0)
+    dt = oracle.time_step(P, c["v"], c["kind"])
+    ref = oracle.step(P, c, {"x": c["x"], "v": c["v"], "a": fp["a"], "dr": fp["dr"]}, s0, dt)
+    L = np.asarray(c["L"])
+
+    def disp(x):
+        d = x - c["x"]
+        return d - L * np.round(d / L)
+
+    def nw(a, b):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        if a.ndim == 2:
+            num, den = np.linalg.norm(a - b, axis=1).max(), np.linalg.norm(b, axis=1).max()
+        else:
+            num, den = np.abs(a - b).max(), np.abs(b).max()
+        return float(num / den) if den > 0 else float(num)
+
+    out = {"workload": "3-D Taylor-Green 24^3 = 13,824 particles, one step from the oracle's initial force pass",
+           "metric": "normwise relative max_i|q_i - q_i^oracle| / max_i|q_i^oracle|; dr absolute (it is 0 on "
+                     "this lattice: chi = 0)"}
+    for prec in (32, 64):
+        sim = sph.Simulation(c, precision=prec, fixed_dt=dt)
+        sim.set_state(a=fp["a"], dr=fp["dr"])
+        sim.build_cells()
+        sim.step(1)
+        sim.sync()
+        got = sim.get_state()
+        d = sim.diag()
+        sim.close()
+        ke_ref = 0.5 * float((c["m"][:, None] * ref["v"] ** 2).sum())
+        out["fp%d" % prec] = {"x_displacement": nw(disp(got["x"]), disp(ref["x"])), "v": nw(got["v"], ref["v"]),
+                              "rho": nw(got["rho"], ref["rho"]), "a": nw(got["a"], ref["a"]),
+                              "dr_abs": float(np.abs(got["dr"] - ref["dr"]).max()),
+                              "ke": abs(d["ke"] - ke_ref) / ke_ref}
+    out["bounds"] = {"fp64": "1e-12 every field", "fp32": "1e-5 for x, v, rho, KE (the stated per-step bound); "
+                     "1e-3 for a and dr: p = c^2 (rho - rho0) of Eq. 2 divides the ~1e-7 relative error of FP32 "
+                     "positions by (rho - rho0)/rho ~ 1e-3..1e-4 on these flows"}
+    return out
+
+
 def _pairs_per_launch(case) -> int:
     """Ordered interacting pairs (r < 2h, j != i) of the workload: every
     particle of the jittered lattice at h = 1.3 dp has the 80 lattice
@@ -496,16 +634,18 @@ def _pairs_per_launch(case) -> int:
     return case["n"] * 80
 
 
-def _profiled_traffic(kernel: str, n: int):
-    """DRAM bytes per launch of a pair kernel ("density" or "forces") for n
-    particles, from the committed ncu summary (profiles/pair_traffic.json,
-    captured at 96^3 = 884,736 particles and scaled by the particle count),
-    or None when the kernel sources have changed since those counters were
-    taken (the summary records a SHA-1 of the sources it was measured on)."""
+COUNTERS = os.path.join(ROOT, "profiles", "pair_counters.json")
+
+
+def _profiled_counters(kernel: str, what: str):
+    """ncu counters of a pair kernel ("density", "forces" or "forces_f64")
+    from the committed summary: what = "binding" (issue activity, lanes per
+    warp instruction, pipe and DRAM utilisation) or "dram_bytes_per_particle".
+    None when the summary is absent or the kernel sources have changed since
+    the counters were taken (it records a SHA-1 of the sources)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "pair_traffic.json")
     try:
-        with open(path) as f:
+        with open(COUNTERS) as f:
             d = json.load(f)
         h = hashlib.sha1()
         for rel in d["sources"]:
@@ -513,9 +653,18 @@ def _profiled_traffic(kernel: str, n: int):
                 h.update(f.read())
         if h.hexdigest() != d["source_sha1"]:
             return None
-        return d["kernels"][kernel]["dram_bytes_per_launch_small"] * n / 884736.0
+        return d["kernels"][kernel][what]
     except (OSError, ValueError, KeyError):
         return None
+
+
+def _profiled_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of a pair kernel for n particles: the captured
+    bytes per particle (ncu on a smaller lattice of the same workload) times
+    n, since the traffic grows in proportion to the particles (the same
+    neighbours per particle); None when the counters are stale."""
+    b = _profiled_counters(kernel, "dram_bytes_per_particle")
+    return None if b is None else b * n
 
 
 def _alu_roofline(name, kernel, prof, pairs, flops_per_pair, bytes_per_particle, n, peak_tflops, hbm_gbs):
@@ -646,6 +795,12 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the throughput of the other generated workloads")
     ap.add_argument("--no-dual", action="store_true", help="skip the dual-criteria integrator timing")
     ap.add_argument("--dual-steps", type=int, default=10)
+    ap.add_argument("--prof-steps", type=int, default=20,
+                    help="steps of the profiled pass (per-kernel events) after the timed steps")
+    ap.add_argument("--steady-from", type=int, default=400, help="first step of the steady-state leg")
+    ap.add_argument("--steady-steps", type=int, default=100, help="timed steps of the steady-state leg (0: skip)")
+    ap.add_argument("--big-n", type=int, default=256, help="lattice side of the larger-lattice leg (0: skip)")
+    ap.add_argument("--big-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

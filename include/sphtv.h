@@ -237,6 +237,25 @@ SPH_API sph_status sph_get_state(sph_ctx* ctx, double* x, double* v, double* a, 
 /* Wait for the stream and copy the diagnostics of the last step. */
 SPH_API sph_status sph_get_diag(sph_ctx* ctx, sph_diag* out);
 
+/* A checkpoint of the kick-drift-kick state after a step: what
+ * sph_step_adjoint replays a segment from (its x0, v0, a0, dr0).  The four
+ * arrays are the caller's ([n][3] doubles, caller's particle order, host or
+ * device memory); the library writes them and the two scalars. */
+typedef struct sph_ckpt {
+    double* x;          /* positions */
+    double* v;          /* velocities (walls: prescribed velocity) */
+    double* a;          /* accelerations of the last force pass (Eq. 3, 7) */
+    double* dr;         /* transport displacements the next drift adds (Eq. 16) */
+    double dt_next;     /* step size the next step takes (Eq. 9-11, or fixed_dt) */
+    double steps;       /* steps taken since sph_build_cells */
+} sph_ckpt;
+
+/* Save a checkpoint (the state as sph_get_state writes it, with the next
+ * step size and the step count of sph_get_diag).  Waits for the stream.
+ * SPH_ERR_ARG for a NULL context, checkpoint or array; SPH_ERR_STATE before
+ * sph_build_cells. */
+SPH_API sph_status sph_save_ckpt(sph_ctx* ctx, sph_ckpt* ck);
+
 /* Wait for the context's stream; return the sticky device error word as a
  * status (SPH_OK if none), then clear it. */
 SPH_API sph_status sph_sync(sph_ctx* ctx);
@@ -300,8 +319,9 @@ SPH_API sph_status sph_fma_peak(int32_t precision, int32_t blocks, int32_t iters
  * (Eq. 15) has d chi / d s = C inside thresh < s < 1/C and 0 elsewhere.
  *
  *   x0, v0, a0, dr0  [n][3] checkpoint state at the start of the segment, in
- *                    the caller's order (host or device), e.g. from
- *                    sph_get_state at that step of the forward run
+ *                    the caller's order (host or device): the arrays of an
+ *                    sph_save_ckpt (or sph_get_state) at that step of the
+ *                    forward run
  *   nsteps           1 <= nsteps <= params.adjoint_steps
  *   xbar, vbar, abar, drbar  [n][3] (host or device, caller order): on entry
  *                    the cotangents of the state after the segment, on

@@ -30,7 +30,8 @@ __all__ = [
     "sph_default_params", "sph_query_workspace", "sph_create", "sph_set_state", "sph_build_cells", "sph_step",
     "sph_set_dt", "sph_set_eta", "sph_get_state", "sph_get_diag", "sph_sync", "sph_destroy", "sph_status_str",
     "sph_launch_count", "sph_profile_begin", "sph_profile_end", "sph_kernel_class_name", "KERNEL_CLASSES", "sph_fma_peak",
-    "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint",
+    "sph_density_noalloc", "NOALLOC_MAX_PARTICLES", "sph_step_adjoint", "sph_force_pass_adjoint", "SphCkpt",
+    "sph_save_ckpt",
     "params_from_case", "Simulation", "Rollout",
     "TV_OFF", "TV_LIMITED", "TV_UNLIMITED", "TV_BACKGROUND", "TVH_MIN", "TVH_PARTICLE", "HPAIR_MEAN", "HPAIR_MAX",
     "INT_KDK", "INT_DUAL", "sph_set_density_rate", "sph_get_density_rate",
@@ -81,6 +82,13 @@ class SphDiag(ctypes.Structure):
                 "dt_next": self.dt_next, "steps": int(self.steps), "substeps": int(self.substeps)}
 
 
+class SphCkpt(ctypes.Structure):
+    """Mirror of ``sph_ckpt``."""
+
+    _fields_ = [("x", ctypes.c_void_p), ("v", ctypes.c_void_p), ("a", ctypes.c_void_p), ("dr", ctypes.c_void_p),
+                ("dt_next", ctypes.c_double), ("steps", ctypes.c_double)]
+
+
 class SphError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -118,6 +126,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "sph_set_eta": (_i32, [_vp, ctypes.c_double]),
             "sph_get_state": (_i32, [_vp] + [_vp] * 5),
             "sph_get_diag": (_i32, [_vp, ctypes.POINTER(SphDiag)]),
+            "sph_save_ckpt": (_i32, [_vp, ctypes.POINTER(SphCkpt)]),
             "sph_sync": (_i32, [_vp]),
             "sph_destroy": (None, [_vp]),
             "sph_status_str": (ctypes.c_char_p, [_i32]),
@@ -255,6 +264,20 @@ def sph_get_state(ctx, x=None, v=None, a=None, dr=None, rho=None) -> None:
         assert t.flags["C_CONTIGUOUS"] and t.dtype == np.float64
         return _vp(t.ctypes.data)
     _check(load().sph_get_state(ctx, p(x), p(v), p(a), p(dr), p(rho)), "sph_get_state")
+
+
+def sph_save_ckpt(ctx, x, v, a, dr):
+    """Write a checkpoint into caller-provided [n][3] float64 buffers (numpy or
+    torch, contiguous); returns (dt_next, steps)."""
+    def p(t):
+        if hasattr(t, "data_ptr"):
+            assert t.is_contiguous()
+            return t.data_ptr()
+        assert t.flags["C_CONTIGUOUS"] and t.dtype == np.float64
+        return t.ctypes.data
+    ck = SphCkpt(p(x), p(v), p(a), p(dr), 0.0, 0.0)
+    _check(load().sph_save_ckpt(ctx, ctypes.byref(ck)), "sph_save_ckpt")
+    return ck.dt_next, int(ck.steps)
 
 
 def sph_get_diag(ctx) -> SphDiag:

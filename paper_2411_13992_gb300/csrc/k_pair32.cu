@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
 // than the tile takes the row walk over global memory instead.
 
 template <int DIM> struct TileShape;
-template <> struct TileShape<3> { static constexpr int B0 = 4, B1 = 4, B2 = 4, T = 160; };
-template <> struct TileShape<2> { static constexpr int B0 = 8, B1 = 8, B2 = 1, T = 128; };
+template <> struct TileShape<3> { static constexpr int B0 = 4, B1 = 4, B2 = 4; };
+template <> struct TileShape<2> { static constexpr int B0 = 8, B1 = 8, B2 = 1; };
 
 template <int DIM> struct TileDims {
     using S = TileShape<DIM>;
@@ -165,6 +165,9 @@ template <int DIM> struct TileDims {
     static constexpr int NHR = H1 * H2;             // halo rows along x
     static constexpr int NHOME = S::B1 * S::B2;     // home rows along x
 };
+
+// Threads per block: the per-thread tile walk and the cooperative pass.
+template <int DIM> struct TileThreads { static constexpr int WALK = DIM == 3 ? 160 : 128, COOP = 128; };
 
 // Coordinate of halo cell v (relative to the grid origin) along axis d:
 // wrapped on periodic axes, -1 outside a non-periodic axis.
@@ -216,39 +219,44 @@ __device__ __forceinline__ void block_exclusive_scan(int* a, int len, int* s_war
     __syncthreads();
 }
 
-// Bytes of dynamic shared memory of the tile kernel for a tile of cap particles.
+// Bytes of dynamic shared memory of a tile kernel for a tile of cap particles
+// (plus extra bytes of per-block tables).
 template <int DIM>
-constexpr size_t tile_smem_bytes(int cap)
+__host__ __device__ constexpr size_t tile_smem_bytes(int cap, size_t extra = 0)
 {
-    return (size_t)cap * (sizeof(float4) + sizeof(int)) + (size_t)(2 * TileDims<DIM>::NHC + 1) * sizeof(int);
+    return (size_t)cap * (sizeof(float4) + sizeof(int)) + (size_t)(2 * TileDims<DIM>::NHC + 1) * sizeof(int) + extra;
 }
 
-template <int DIM, typename Acc>
-__global__ void __launch_bounds__(TileShape<DIM>::T) k_density32_tile(
-    int n, const float4* __restrict__ pos4c, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ start,
-    Grid G, Consts<float> K, StateSet<float> S, float4* __restrict__ vr, uint32_t* __restrict__ nbl,
-    int32_t* __restrict__ nbc, int cap, int nb0, int nb1, int tile_cap)
+// Shared-memory view of a staged block: the tile and its cell tables.
+struct TileView {
+    float4* pos;     // [cap] offsets, w = halo x index of the particle's cell
+    int* gid;        // [cap] global particle index
+    int* ts;         // [NHC + 1] tile start of each halo cell
+    int* gs;         // [NHC] global start of each halo cell
+    int* home;       // [NHOME + 1] prefix counts of the home particles by home row
+    int bxn, byn, bzn;   // home cells of the block along each axis (edge blocks are partial)
+    bool fits;       // the halo's particles fit the tile (else only the tables are set)
+};
+
+// Stage block b: counts and global starts of the halo cells, their scan, the
+// particles' offsets (when they fit), and the home-row prefix counts.  Every
+// thread of the block calls it; it ends with a barrier.
+template <int DIM, int T>
+__device__ __forceinline__ void stage_tile(TileView& V, const Grid& G, const int32_t* __restrict__ start,
+                                           const float4* __restrict__ pos4c, int nb0, int nb1, int tile_cap,
+                                           int* s_warp)
 {
     using TD = TileDims<DIM>;
     using SH = TileShape<DIM>;
-    constexpr int T = SH::T, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
+    constexpr int R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
     constexpr int Rz = DIM == 3 ? R : 0;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4* s_pos = (float4*)smem;                   // [tile_cap] offsets, w = halo x index of the cell
-    int* s_gid = (int*)(s_pos + tile_cap);           // [tile_cap] global particle index
-    int* s_ts = s_gid + tile_cap;                    // [NHC + 1] tile start of each halo cell
-    int* s_gs = s_ts + NHC + 1;                      // [NHC] global start of each halo cell
-    __shared__ int s_warp[T / 32 + 1];
-    __shared__ int s_home[TD::NHOME + 1];
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
     const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
     const int cx0 = bx * SH::B0, cy0 = by * SH::B1, cz0 = bz * SH::B2;
-    const int bxn = min(SH::B0, G.nc[0] - cx0), byn = min(SH::B1, G.nc[1] - cy0);
-    const int bzn = DIM == 3 ? min(SH::B2, G.nc[2] - cz0) : 1;
-
-    // 1. counts and global starts of the halo cells
+    V.bxn = min(SH::B0, G.nc[0] - cx0);
+    V.byn = min(SH::B1, G.nc[1] - cy0);
+    V.bzn = DIM == 3 ? min(SH::B2, G.nc[2] - cz0) : 1;
     for (int c = tid; c < NHC; c += T) {
         const int hx = c % H0, hy = (c / H0) % H1, hz = c / (H0 * H1);
         const int gx = halo_coord(G, cx0 + hx - R, 0), gy = halo_coord(G, cy0 + hy - R, 1);
@@ -259,59 +267,135 @@ __global__ void __launch_bounds__(TileShape<DIM>::T) k_density32_tile(
             gs = start[g];
             cnt = start[g + 1] - gs;
         }
-        s_gs[c] = gs;
-        s_ts[c] = cnt;
+        V.gs[c] = gs;
+        V.ts[c] = cnt;
     }
     __syncthreads();
-    block_exclusive_scan<T>(s_ts, NHC, s_warp);
-    const bool fits = s_ts[NHC] <= tile_cap;
-
-    // 2. stage the tile: one warp per halo row, the particles of a row being
-    // one or two contiguous runs of the cell-sorted offsets
-    if (fits) {
+    block_exclusive_scan<T>(V.ts, NHC, s_warp);
+    V.fits = V.ts[NHC] <= tile_cap;
+    // one warp per halo row: the particles of a row are one or two
+    // contiguous runs of the cell-sorted offsets
+    if (V.fits) {
         for (int r = warp; r < TD::NHR; r += T / 32) {
             const int c0 = r * H0;
-            const int t1 = s_ts[c0 + H0];
-            for (int t = s_ts[c0] + lane; t < t1; t += 32) {
-                int lo = 0, hi = H0 - 1;           // the cell of t: last k with s_ts[c0 + k] <= t
+            const int t1 = V.ts[c0 + H0];
+            for (int t = V.ts[c0] + lane; t < t1; t += 32) {
+                int lo = 0, hi = H0 - 1;           // the cell of t: last k with ts[c0 + k] <= t
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (s_ts[c0 + mid] <= t) lo = mid;
+                    if (V.ts[c0 + mid] <= t) lo = mid;
                     else hi = mid - 1;
                 }
                 const int c = c0 + lo;
-                const int g = s_gs[c] + (t - s_ts[c]);
+                const int g = V.gs[c] + (t - V.ts[c]);
                 float4 p = pos4c[g];
                 p.w = __int_as_float(lo);
-                s_pos[t] = p;
-                s_gid[t] = g;
+                V.pos[t] = p;
+                V.gid[t] = g;
             }
         }
     }
-    // home rows: prefix counts of the home particles, row by row
     if (tid == 0) {
         int acc = 0;
-        for (int k = 0; k < byn * bzn; ++k) {
-            const int hy = R + k % byn, hz = Rz + k / byn;
+        for (int k = 0; k < V.byn * V.bzn; ++k) {
+            const int hy = R + k % V.byn, hz = Rz + k / V.byn;
             const int c = (hy + H1 * hz) * H0 + R;
-            s_home[k] = acc;
-            acc += s_ts[c + bxn] - s_ts[c];
+            V.home[k] = acc;
+            acc += V.ts[c + V.bxn] - V.ts[c];
         }
-        s_home[byn * bzn] = acc;
+        V.home[V.byn * V.bzn] = acc;
     }
     __syncthreads();
-    const int nhome = s_home[byn * bzn];
+}
+
+// Home particle t of a staged block: its home row's halo coordinates, its
+// tile index (valid when the tile fits) and its global index (home rows are
+// runs of real cells, contiguous in the global order).
+template <int DIM>
+__device__ __forceinline__ void home_particle(const TileView& V, int t, int& hy, int& hz, int& s, int& g)
+{
+    using TD = TileDims<DIM>;
+    constexpr int R = TD::R, H0 = TD::H0, H1 = TD::H1;
+    int k = 0;
+    while (V.home[k + 1] <= t) ++k;
+    hy = R + k % V.byn;
+    hz = (DIM == 3 ? R : 0) + k / V.byn;
+    const int c_row = (hy + H1 * hz) * H0 + R;
+    s = V.ts[c_row] + (t - V.home[k]);
+    g = V.gs[c_row] + (t - V.home[k]);
+}
+
+// The clipped x extent [dxlo, dxhi] of stencil row (dy, dz) for a particle
+// at cell-relative offset oi (the row walk's clipping: margins of 1e-3 of a
+// cell edge); false if the row is out of reach.
+template <int DIM>
+__device__ __forceinline__ bool row_extent(const float* oi, int dy, int dz, float reach2, float ex, float ey, float ez,
+                                           float inv_ex, int& dxlo, int& dxhi)
+{
+    constexpr int R = kStencilR;
+    float rz = 0.f;
+    if (DIM == 3) {
+        rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
+        rz = fmaxf(rz - 1e-3f * ez, 0.f);
+    }
+    const float wz2 = reach2 - rz * rz;
+    if (wz2 <= 0.f) return false;
+    float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
+    ry = fmaxf(ry - 1e-3f * ey, 0.f);
+    const float w2 = wz2 - ry * ry;
+    if (w2 <= 0.f) return false;
+    const float w = sqrtf(w2) + 1e-3f * ex;
+    dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
+    dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
+    return dxlo <= dxhi;
+}
+
+// r^2 of a candidate from the tile, in the row walk's arithmetic (so the
+// accept decisions, and the neighbour list, are those of the row walk).
+template <int DIM>
+__device__ __forceinline__ float tile_r2(const float* oi, int hx_i, const float4& pj, float ex, float shy, float shz)
+{
+    const float shx = -(float)(__float_as_int(pj.w) - hx_i) * ex;
+    const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
+                                             make_float2(oi[0], oi[1])),
+                                  make_float2(shx, shy));
+    const float2 q = __fmul2_rn(rxy, rxy);
+    float r2 = q.x + q.y;
+    if (DIM == 3) {
+        const float rz_ = (oi[2] - pj.z) + shz;
+        r2 = fmaf(rz_, rz_, r2);
+    }
+    return r2;
+}
+
+template <int DIM, typename Acc>
+__global__ void __launch_bounds__(TileThreads<DIM>::WALK) k_density32_tile(
+    int n, const float4* __restrict__ pos4c, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ start,
+    Grid G, Consts<float> K, StateSet<float> S, float4* __restrict__ vr, uint32_t* __restrict__ nbl,
+    int32_t* __restrict__ nbc, int cap, int nb0, int nb1, int tile_cap)
+{
+    using TD = TileDims<DIM>;
+    constexpr int T = TileThreads<DIM>::WALK, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
+    constexpr int Rz = DIM == 3 ? R : 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_warp[T / 32 + 1];
+    __shared__ int s_home[TD::NHOME + 1];
+    TileView V;
+    V.pos = (float4*)smem;
+    V.gid = (int*)(V.pos + tile_cap);
+    V.ts = V.gid + tile_cap;
+    V.gs = V.ts + NHC + 1;
+    V.home = s_home;
+    stage_tile<DIM, T>(V, G, start, pos4c, nb0, nb1, tile_cap, s_warp);
+    const int nhome = V.home[V.byn * V.bzn];
 
     const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
     const float inv_ex = 1.f / ex;
     const float reach = 2.f * K.h_u;
     const float reach2 = reach * reach;
-    for (int t = tid; t < nhome; t += T) {
-        int k = 0;
-        while (s_home[k + 1] <= t) ++k;
-        const int hy_i = R + k % byn, hz_i = Rz + k / byn;
-        const int c_row = (hy_i + H1 * hz_i) * H0 + R;
-        const int i = s_gs[c_row] + (t - s_home[k]);      // home rows are contiguous in the global order
+    for (int t = threadIdx.x; t < nhome; t += T) {
+        int hy_i, hz_i, s, i;
+        home_particle<DIM>(V, t, hy_i, hz_i, s, i);
         const int8_t kind = S.kind[i];
         const float s0 = (float)S.s0[i];
         float vi[3] = {0.f, 0.f, 0.f};
@@ -335,56 +419,32 @@ __global__ void __launch_bounds__(TileShape<DIM>::T) k_density32_tile(
                 ++cnt;
             }
         };
-        if (fits) {
-            const int s = s_ts[c_row] + (t - s_home[k]);
-            const float4 pi = s_pos[s];
+        if (V.fits) {
+            const float4 pi = V.pos[s];
             const float oi[3] = {pi.x, pi.y, pi.z};
             const int hx_i = __float_as_int(pi.w);
             for (int dz = -Rz; dz <= Rz; ++dz) {
-                float rz = 0.f;
-                if (DIM == 3) {
-                    rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
-                    rz = fmaxf(rz - 1e-3f * ez, 0.f);
-                }
-                const float wz2 = reach2 - rz * rz;
-                if (wz2 <= 0.f) continue;
                 const float shz = -(float)dz * ez;
                 for (int dy = -R; dy <= R; ++dy) {
-                    float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
-                    ry = fmaxf(ry - 1e-3f * ey, 0.f);
-                    const float w2 = wz2 - ry * ry;
-                    if (w2 <= 0.f) continue;
-                    const float w = sqrtf(w2) + 1e-3f * ex;
-                    const int dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
-                    const int dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
-                    if (dxlo > dxhi) continue;
+                    int dxlo, dxhi;
+                    if (!row_extent<DIM>(oi, dy, dz, reach2, ex, ey, ez, inv_ex, dxlo, dxhi)) continue;
                     const float shy = -(float)dy * ey;
                     const int rowc = (hy_i + dy + H1 * (hz_i + dz)) * H0 + hx_i;
-                    const int tend = s_ts[rowc + dxhi + 1];
+                    const int tend = V.ts[rowc + dxhi + 1];
                     const uint32_t code_row =
                         (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R)) - (uint32_t)hx_i;
                     auto one = [&](int tj, const float4& pj) {
-                        const int hxj = __float_as_int(pj.w);
-                        const float shx = -(float)(hxj - hx_i) * ex;
-                        const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
-                                                                 make_float2(oi[0], oi[1])),
-                                                      make_float2(shx, shy));
-                        const float2 q = __fmul2_rn(rxy, rxy);
-                        float r2 = q.x + q.y;
-                        if (DIM == 3) {
-                            const float rz_ = (oi[2] - pj.z) + shz;
-                            r2 = fmaf(rz_, rz_, r2);
-                        }
+                        const float r2 = tile_r2<DIM>(oi, hx_i, pj, ex, shy, shz);
                         if (r2 < K.four_h2_u)
-                            accept(r2, ((uint32_t)s_gid[tj] << kCodeBits) | (code_row + (uint32_t)hxj));
+                            accept(r2, ((uint32_t)V.gid[tj] << kCodeBits) | (code_row + (uint32_t)__float_as_int(pj.w)));
                     };
-                    int tj = s_ts[rowc + dxlo];
+                    int tj = V.ts[rowc + dxlo];
                     for (; tj + 1 < tend; tj += 2) {
-                        const float4 p0 = s_pos[tj], p1 = s_pos[tj + 1];
+                        const float4 p0 = V.pos[tj], p1 = V.pos[tj + 1];
                         one(tj, p0);
                         one(tj + 1, p1);
                     }
-                    if (tj < tend) one(tj, s_pos[tj]);
+                    if (tj < tend) one(tj, V.pos[tj]);
                 }
             }
         } else {
@@ -399,6 +459,264 @@ __global__ void __launch_bounds__(TileShape<DIM>::T) k_density32_tile(
         nbc[i] = cnt;
         const float w = K.rho0 * (sigma.value() - s0) / s0;
         vr[i] = make_float4(vi[0], vi[1], vi[2], w);
+    }
+}
+
+// ---------------------------------- density on tiles, lanes sharing a particle
+//
+// The same staged tile, walked cooperatively: a group of G lanes (8 in 3-D,
+// 4 in 2-D) takes one home particle and splits its candidates, G at a time,
+// in the row walk's order (stencil rows by (dz, dy), then the tile order of
+// each row's clipped run).  Every lane of a warp tests a candidate in every
+// iteration, whatever the lengths of the particle's row runs, so the walk
+// does not lose lanes to the unequal runs of a disordered lattice.  Each
+// lane keeps a compensated partial sum of sigma; the group combines them
+// exactly pairwise (TwoSum) at the end.  Accepted neighbours go to the list
+// in candidate order (ballot + prefix within the group), so the list and the
+// count are those of the row walk; sigma differs from it only by the
+// summation order.  The group's row table (exclusive prefix of the run
+// lengths, tile start minus prefix, stencil code and shifts) lives in shared
+// memory; a lane moves from row to row as its candidate index passes the
+// prefixes.
+
+template <int DIM> struct CoopShape {
+    static constexpr int G = DIM == 3 ? 8 : 4;                 // lanes per particle
+    static constexpr int NR = DIM == 3 ? kSide * kSide : kSide;  // stencil rows
+    static constexpr int RPL = (NR + G - 1) / G;               // rows set up per lane
+    static constexpr int NG = TileThreads<DIM>::COOP / G;      // groups per block
+};
+
+struct CoopRow {
+    int base;        // tile start of the row's run minus the row's prefix: t = f + base
+    uint32_t code;   // stencil code of the row minus hx_i: code = code + hx_j
+    float shy, shz;  // FP32 shifts of the row
+};
+
+template <int DIM>
+__host__ __device__ constexpr size_t coop_table_bytes()
+{
+    using C = CoopShape<DIM>;
+    return (size_t)C::NG * (C::NR * sizeof(CoopRow) + (C::NR + 1) * sizeof(int));
+}
+
+// Compensated partial sums combined exactly: (s, c) holds s - c.
+__device__ __forceinline__ void ksum_merge(float& s, float& c, float s2, float c2)
+{
+    const float t = __fadd_rn(s, s2);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));   // s + s2 = t + e exactly
+    c = __fsub_rn(__fadd_rn(c, c2), e);
+    s = t;
+}
+
+template <typename Acc> struct PartialSum;
+template <> struct PartialSum<KSum> {
+    static __device__ __forceinline__ void get(const KSum& a, float& s, float& c) { s = a.s; c = a.c; }
+    static constexpr bool compensated = true;
+};
+template <> struct PartialSum<PlainF> {
+    static __device__ __forceinline__ void get(const PlainF& a, float& s, float& c) { s = a.s; c = 0.f; }
+    static constexpr bool compensated = false;
+};
+
+template <int DIM, typename Acc>
+__global__ void __launch_bounds__(TileThreads<DIM>::COOP, 4) k_density32_coop(
+    int n, const float4* __restrict__ pos4c, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ start,
+    Grid G, Consts<float> K, StateSet<float> S, float4* __restrict__ vr, uint32_t* __restrict__ nbl,
+    int32_t* __restrict__ nbc, int cap, int nb0, int nb1, int tile_cap)
+{
+    using TD = TileDims<DIM>;
+    using C = CoopShape<DIM>;
+    constexpr int T = TileThreads<DIM>::COOP, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
+    constexpr int GL = C::G, NR = C::NR, RPL = C::RPL, NG = C::NG;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_warp[T / 32 + 1];
+    __shared__ int s_home[TD::NHOME + 1];
+    TileView V;
+    CoopRow* rows_all = (CoopRow*)smem;                              // [NG][NR]
+    int* pref_all = (int*)(rows_all + NG * NR);                      // [NG][NR + 1]
+    V.pos = (float4*)(smem + coop_table_bytes<DIM>());
+    V.gid = (int*)(V.pos + tile_cap);
+    V.ts = V.gid + tile_cap;
+    V.gs = V.ts + NHC + 1;
+    V.home = s_home;
+    stage_tile<DIM, T>(V, G, start, pos4c, nb0, nb1, tile_cap, s_warp);
+    const int nhome = V.home[V.byn * V.bzn];
+
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    const float inv_ex = 1.f / ex;
+    const float reach = 2.f * K.h_u;
+    const float reach2 = reach * reach;
+    const int lane = threadIdx.x & 31, q = lane % GL;
+    const int grp = threadIdx.x / GL;                   // group within the block
+    const unsigned gshift = (unsigned)((lane / GL) * GL);
+    const unsigned gmask = (GL == 32 ? 0xffffffffu : ((1u << GL) - 1u)) << gshift;
+    CoopRow* rows = rows_all + grp * NR;
+    int* pref = pref_all + grp * (NR + 1);
+
+    if (!V.fits) {
+        // the halo does not fit the tile: the row walk over global memory,
+        // one thread per particle
+        for (int t = threadIdx.x; t < nhome; t += T) {
+            int hy_i, hz_i, s, i;
+            home_particle<DIM>(V, t, hy_i, hz_i, s, i);
+            const int8_t kind = S.kind[i];
+            const float s0 = (float)S.s0[i];
+            float vi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
+            if (kind) {
+                vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
+                nbc[i] = 0;
+                continue;
+            }
+            Acc sigma;
+            int cnt = 0;
+            uint32_t* lp = nbl + i;
+            const float4 pi = pos4c[i];
+            const float oi[3] = {pi.x, pi.y, pi.z};
+            auto visit = [&](int j, uint32_t code, const float4&, float r2, float, float, float) {
+                if (r2 < K.four_h2_u) {
+                    sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), K.inv_h_u));
+                    if (r2 > 0.f) {
+                        if (cnt < cap) {
+                            *lp = ((uint32_t)j << kCodeBits) | code;
+                            lp += n;
+                        }
+                        ++cnt;
+                    }
+                }
+            };
+            for_candidates_rows<DIM, true, true>(oi, reach, cell_of[i], G, start, cell_of, pos4c, visit);
+            nbc[i] = cnt;
+            vr[i] = make_float4(vi[0], vi[1], vi[2], K.rho0 * (sigma.value() - s0) / s0);
+        }
+        return;
+    }
+
+    // rounds of NG particles, one per group; every lane of the block runs the
+    // same number of rounds (the warp-wide votes below need whole warps)
+    const int rounds = (nhome + NG - 1) / NG;
+    for (int round = 0; round < rounds; ++round) {
+        const int t = round * NG + grp;
+        int i = 0, total = 0;
+        float oi[3] = {0.f, 0.f, 0.f};
+        int hx_i = 0;
+        float s0 = 1.f, vi[3] = {0.f, 0.f, 0.f};
+        bool active = false;
+        if (t < nhome) {
+            int hy_i, hz_i, s;
+            home_particle<DIM>(V, t, hy_i, hz_i, s, i);
+            const float4 pi = V.pos[s];
+            oi[0] = pi.x;
+            oi[1] = pi.y;
+            oi[2] = pi.z;
+            hx_i = __float_as_int(pi.w);
+            const int8_t kind = S.kind[i];
+            s0 = (float)S.s0[i];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
+            if (kind) {
+                if (q == 0) {
+                    vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
+                    nbc[i] = 0;
+                }
+            } else {
+                active = true;
+                // this lane's stencil rows (RPL consecutive ones): their runs
+                // go to the group's table first (tile start, length), then
+                // get their prefixes
+                int mine = 0;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int r = q * RPL + k;
+                    if (r < NR) {
+                        const int dy = r % kSide - R, dz = DIM == 3 ? r / kSide - R : 0;
+                        int dxlo, dxhi, t0 = 0, l = 0;
+                        if (row_extent<DIM>(oi, dy, dz, reach2, ex, ey, ez, inv_ex, dxlo, dxhi)) {
+                            const int rowc = (hy_i + dy + H1 * (hz_i + dz)) * H0 + hx_i;
+                            t0 = V.ts[rowc + dxlo];
+                            l = V.ts[rowc + dxhi + 1] - t0;
+                        }
+                        rows[r].base = t0;
+                        pref[r] = l;
+                        mine += l;
+                    }
+                }
+                // exclusive prefix of the rows over the group's lanes
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < GL; o <<= 1) {
+                    const int y = __shfl_up_sync(gmask, incl, o, GL);
+                    if (q >= o) incl += y;
+                }
+                int run = incl - mine;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int r = q * RPL + k;
+                    if (r < NR) {
+                        const int dy = r % kSide - R, dz = DIM == 3 ? r / kSide - R : 0;
+                        const int l = pref[r];
+                        pref[r] = run;
+                        CoopRow rr;
+                        rr.base = rows[r].base - run;
+                        rr.code = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R)) - (uint32_t)hx_i;
+                        rr.shy = -(float)dy * ey;
+                        rr.shz = -(float)dz * ez;
+                        rows[r] = rr;
+                        run += l;
+                    }
+                }
+                total = __shfl_sync(gmask, incl, GL - 1, GL);
+                if (q == 0) pref[NR] = total;
+            }
+        }
+        __syncwarp();
+        Acc sigma;
+        int cnt = 0;
+        int r = 0;
+        // candidate f = f0 + q of the group's particle, G at a time, until
+        // every group of the warp is through its candidates
+        for (int f0 = 0; __any_sync(0xffffffffu, active && f0 < total); f0 += GL) {
+            const int f = f0 + q;
+            bool take = false;
+            float r2 = 0.f;
+            uint32_t entry = 0;
+            if (active && f < total) {
+                while (f >= pref[r + 1]) ++r;
+                const CoopRow rr = rows[r];
+                const int tj = f + rr.base;
+                const float4 pj = V.pos[tj];
+                r2 = tile_r2<DIM>(oi, hx_i, pj, ex, rr.shy, rr.shz);
+                if (r2 < K.four_h2_u) {
+                    sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), K.inv_h_u));
+                    take = r2 > 0.f;
+                    entry = ((uint32_t)V.gid[tj] << kCodeBits) | (rr.code + (uint32_t)__float_as_int(pj.w));
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, take) & gmask;
+            if (take) {
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (pos < cap) nbl[(size_t)pos * n + i] = entry;
+            }
+            cnt += __popc(m);
+        }
+        // combine the lanes' partial sums within the group
+        float ps, pc;
+        PartialSum<Acc>::get(sigma, ps, pc);
+#pragma unroll
+        for (int o = GL / 2; o >= 1; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, ps, o, GL);
+            const float c2 = __shfl_xor_sync(0xffffffffu, pc, o, GL);
+            if (PartialSum<Acc>::compensated) ksum_merge(ps, pc, s2, c2);
+            else ps += s2;
+        }
+        if (active && q == 0) {
+            const float sig = PartialSum<Acc>::compensated ? __fsub_rn(ps, pc) : ps;
+            nbc[i] = cnt;
+            vr[i] = make_float4(vi[0], vi[1], vi[2], K.rho0 * (sig - s0) / s0);
+        }
+        __syncwarp();
     }
 }
 
@@ -586,7 +904,7 @@ static int tile_capacity(int n, const Grid& G)
 }
 
 template <int DIM, typename Acc>
-static cudaError_t density_tile_t(int n, const float4* pos4c, const int32_t* cell_of, const int32_t* start,
+static cudaError_t density_tile_t(int mode, int n, const float4* pos4c, const int32_t* cell_of, const int32_t* start,
                                   const Grid& G, const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl,
                                   int32_t* nbc, cudaStream_t st)
 {
@@ -594,14 +912,20 @@ static cudaError_t density_tile_t(int n, const float4* pos4c, const int32_t* cel
     const int nb0 = (G.nc[0] + SH::B0 - 1) / SH::B0, nb1 = (G.nc[1] + SH::B1 - 1) / SH::B1;
     const int nb2 = DIM == 3 ? (G.nc[2] + SH::B2 - 1) / SH::B2 : 1;
     const int cap = tile_capacity<DIM>(n, G);
-    const size_t smem = tile_smem_bytes<DIM>(cap);
-    if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_density32_tile<DIM, Acc>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool coop = mode == 2;
+    const size_t smem = tile_smem_bytes<DIM>(cap, coop ? coop_table_bytes<DIM>() : 0);
+    auto kern = coop ? k_density32_coop<DIM, Acc> : k_density32_tile<DIM, Acc>;
+    // opt in to more than 48 KB of dynamic shared memory once per kernel (and
+    // again only for a larger size)
+    static size_t opted[2] = {48 * 1024, 48 * 1024};
+    if (smem > opted[coop]) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        opted[coop] = smem;
     }
-    k_density32_tile<DIM, Acc><<<nb0 * nb1 * nb2, SH::T, smem, st>>>(n, pos4c, cell_of, start, G, K, S, vr, nbl, nbc,
-                                                                     nbl_capacity(DIM), nb0, nb1, cap);
+    const int threads = coop ? TileThreads<DIM>::COOP : TileThreads<DIM>::WALK;
+    kern<<<nb0 * nb1 * nb2, threads, smem, st>>>(n, pos4c, cell_of, start, G, K, S, vr, nbl, nbc, nbl_capacity(DIM),
+                                                 nb0, nb1, cap);
     return cudaGetLastError();
 }
 
@@ -645,10 +969,11 @@ cudaError_t launch_density32(int dim, int n, void* Sv, const int32_t* start, con
     const Consts<float>& K = *(const Consts<float>*)Kv;
     if (K.uniform_h && !pos4c) return cudaErrorInvalidValue;   // the uniform walk reads the cell-tagged copy
     if (K.uniform_h && tiles) {
-        if (K.kahan) return dim == 2 ? density_tile_t<2, KSum>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st)
-                                     : density_tile_t<3, KSum>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
-        return dim == 2 ? density_tile_t<2, PlainF>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st)
-                        : density_tile_t<3, PlainF>(n, pos4c, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st);
+        float4* v4 = (float4*)vr;
+        if (K.kahan) return dim == 2 ? density_tile_t<2, KSum>(tiles, n, pos4c, cell_of, start, G, K, S, v4, nbl, nbc, st)
+                                     : density_tile_t<3, KSum>(tiles, n, pos4c, cell_of, start, G, K, S, v4, nbl, nbc, st);
+        return dim == 2 ? density_tile_t<2, PlainF>(tiles, n, pos4c, cell_of, start, G, K, S, v4, nbl, nbc, st)
+                        : density_tile_t<3, PlainF>(tiles, n, pos4c, cell_of, start, G, K, S, v4, nbl, nbc, st);
     }
     SPH_DISPATCH32(density_t, n, pos4, cell_of, start, G, K, S, (float4*)vr, nbl, nbc, st, pos4c);
     return cudaGetLastError();

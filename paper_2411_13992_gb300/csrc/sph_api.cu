@@ -1178,6 +1178,18 @@ const char* sph_status_str(sph_status s)
     return "unknown status";
 }
 
+sph_status sph_save_ckpt(sph_ctx* c, sph_ckpt* ck)
+{
+    if (!c || !ck || !ck->x || !ck->v || !ck->a || !ck->dr) return SPH_ERR_ARG;
+    if (!c->have_state || !c->have_cells) return SPH_ERR_STATE;
+    SPH_TRY(sph_get_state(c, ck->x, ck->v, ck->a, ck->dr, nullptr));
+    sph_diag d;
+    SPH_TRY(sph_get_diag(c, &d));
+    ck->dt_next = d.dt_next;
+    ck->steps = d.steps;
+    return SPH_OK;
+}
+
 sph_status sph_step_adjoint(sph_ctx* c, const double* x0, const double* v0, const double* a0, const double* dr0,
                             int32_t nsteps, double* xbar, double* vbar, double* abar, double* drbar, double* etabar)
 {

@@ -1,8 +1,11 @@
-"""The FP32 density pass on cell-blocked shared-memory tiles
-(sph_params.pair_tiles = 1, the default at uniform resolution) against the
-row walk over global memory (pair_tiles = 0): the tile kernel visits the
-same candidates in the same order with the same arithmetic, so every state
-field after several steps is bit for bit the same.  Cases: partial edge
+"""The FP32 density pass on cell-blocked shared-memory tiles against the
+row walk over global memory (sph_params.pair_tiles = 0).  pair_tiles = 1,
+one thread per particle over the tile, visits the same candidates in the
+same order with the same arithmetic, so every state field after several
+steps is bit for bit the same.  pair_tiles = 2, groups of lanes sharing a
+particle's candidates, writes the same neighbour lists but sums sigma in
+another order: its densities agree to FP32 rounding, and it is checked
+against the FP64 oracle like the other FP32 paths.  Cases: partial edge
 blocks, halos that wrap a periodic axis more than once (5 cells per axis),
 walls in a non-periodic box, the dual-criteria integrator (which freezes the
 density pass's neighbour list for its substeps), and a block whose halo
@@ -12,6 +15,8 @@ import pytest
 
 import paper_2411_13992_gb300 as sph
 from paper_2411_13992_gb300 import cases
+
+from gpu_helpers import compare_step, oracle_trajectory
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +61,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_tiled_density_is_bit_identical_to_the_row_walk(name):
+def test_tiled_walk_is_bit_identical_to_the_row_walk(name):
     c = CASES[name]()
     got, d_got = _run(c, 1, 5)
     ref, d_ref = _run(c, 0, 5)
@@ -72,3 +77,38 @@ def test_tiled_density_is_bit_identical_in_the_dual_criteria_integrator():
     for k in ("x", "v", "rho"):
         assert np.array_equal(got[k], ref[k]), k
     assert d_got["substeps"] == d_ref["substeps"]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_cooperative_density_matches_the_row_walk(name):
+    """From the same state (the initial force pass of sph_build_cells), the
+    cooperative pass's densities equal the row walk's to FP32 rounding of a
+    compensated sum of ~81 terms; after 5 steps the trajectories agree to the
+    FP32 per-step bound."""
+    c = CASES[name]()
+    fl = c["kind"] == 0
+    for steps in (0, 5):
+        got, _ = _run(c, 2, steps)
+        ref, _ = _run(c, 0, steps)
+        assert np.isfinite(got["rho"]).all()
+        d_rho = np.abs(got["rho"][fl] - ref["rho"][fl]).max() / np.abs(ref["rho"][fl]).max()
+        assert d_rho <= (2e-7 if steps == 0 else 1e-5), (name, steps, d_rho)
+        if steps:
+            d_v = np.linalg.norm(got["v"][fl] - ref["v"][fl], axis=1).max() / np.linalg.norm(ref["v"][fl], axis=1).max()
+            assert d_v <= 1e-5, (name, d_v)
+
+
+@pytest.mark.parametrize("kind", ["tgv3d_16", "tgv3d_15", "cavity2d_32", "tgv2d_50"])
+def test_cooperative_density_step_parity_with_the_oracle(kind):
+    """One FP32 step from the oracle's state with pair_tiles = 2: the FP32
+    bounds of the parity tests (1e-5 on x, v, rho, KE; 1e-3 on a and dr)."""
+    c = {"tgv3d_16": lambda: cases.tgv3d(16), "tgv3d_15": lambda: cases.tgv3d(15),
+         "cavity2d_32": lambda: cases.cavity2d(32, U=1.0), "tgv2d_50": lambda: cases.tgv2d(50)}[kind]()
+    dt, states, P, s0 = oracle_trajectory(c, 3, {0, 3})
+    for k in (0, 3):
+        err, _, _ = compare_step(c, states[k], dt, s0, P, precision=32, pair_tiles=2)
+        for f in ("x", "v", "rho", "ke"):
+            assert err[f] <= 1e-5, (kind, k, f, err)
+        assert err["a"] <= 1e-3, (kind, k, err)
+        if err["n_chi_ref"]:
+            assert err["dr"] <= 1e-3, (kind, k, err)
