@@ -136,11 +136,14 @@ typedef struct sph_params {
                                time from a captured CUDA graph on a library-owned stream,
                                ordered after and before the context's stream by events
                                (same results, fewer launches); 0: always launch directly */
-    int32_t pair_tiles;     /* FP32 form at uniform resolution (h_min == h_max): 1 (default)
-                               runs the density pass on cell-blocked shared-memory tiles
-                               (a block of cells and the two cells around it staged per
-                               thread block); 0 walks the cell rows in global memory.  Both
-                               give the same results bit for bit; ignored otherwise */
+    int32_t pair_tiles;     /* FP32 form at uniform resolution (h_min == h_max), the density
+                               pass: 0 walks the cell rows in global memory, one thread per
+                               particle; 1 (default) stages a block of cells and the two cells
+                               around it in shared memory per thread block and walks that tile,
+                               one thread per particle (the same results as 0 bit for bit);
+                               2 walks the tile with groups of lanes sharing each particle's
+                               candidates (the same neighbour lists, sigma summed in another
+                               order).  Ignored otherwise */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
