@@ -137,13 +137,26 @@ typedef struct sph_params {
                                ordered after and before the context's stream by events
                                (same results, fewer launches); 0: always launch directly */
     int32_t pair_tiles;     /* FP32 form at uniform resolution (h_min == h_max), the density
-                               pass: 0 walks the cell rows in global memory, one thread per
-                               particle; 1 (default) stages a block of cells and the two cells
-                               around it in shared memory per thread block and walks that tile,
-                               one thread per particle (the same results as 0 bit for bit);
-                               2 walks the tile with groups of lanes sharing each particle's
-                               candidates (the same neighbour lists, sigma summed in another
-                               order).  Ignored otherwise */
+                               pass: 0 (default, the fastest measured) walks the cell rows in
+                               global memory, one thread per particle; 1 stages a block of cells
+                               and the two cells around it in shared memory per thread block
+                               and walks that tile, one thread per particle (the same results as
+                               0 bit for bit); 2 walks the tile with groups of lanes sharing each
+                               particle's candidates (the same neighbour lists, sigma summed in
+                               another order).  Ignored otherwise */
+    int32_t body_force;     /* 1: the force pass also sums the force of the fluid on the wall
+                               particles (the body force of Eq. 18, e.g. the cylinder of
+                               Sec. 4.4), reported in sph_diag.body_force; 0 (default): not */
+    double fringe_lambda;   /* free stream in a periodic box (Sec. 4.4 names a free-stream
+                               boundary without giving it): the fringe-region forcing of
+                               Nordstrom, Nordin & Henningson (SIAM J. Sci. Comput. 20, 1999)
+                               adds lambda(x) (fringe_u - v) to the acceleration of fluid
+                               particles, lambda(x) = fringe_lambda [S((x - x0)/rise)
+                               - S((x - x1)/fall + 1)] along axis 0, S(t) = 1/(1 + exp(1/(t-1)
+                               + 1/t)) on (0, 1), 0 below, 1 above.  0 (default): off.
+                               Kick-drift-kick only (SPH_ERR_ARG with SPH_INT_DUAL) */
+    double fringe_u[3];     /* free-stream velocity U_inf */
+    double fringe_x[4];     /* x0, x1, rise > 0, fall > 0 of the fringe region */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -160,13 +173,18 @@ typedef struct sph_diag {
     double dt_next;         /* step size the next step will use */
     double steps;           /* steps taken since sph_build_cells */
     double substeps;        /* SPH_INT_DUAL: acoustic substeps of the last advection step */
+    double body_force[3];   /* params.body_force: force of the fluid on the wall particles in
+                               the last force pass (minus the fluid's momentum rate from its
+                               pair terms, which cancel between fluid pairs): the F of the
+                               drag and lift coefficients of Eq. 18, C = 2 F / (rho0 U^2 D) */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;
 
 /* Fill *p with the paper's constants: riemann_eta 3, tv_xi -0.2, tv_C 1e3,
  * tv_thresh 5e-4, cfl_ad 0.25, cfl_ac 0.6, tv_mode limited, tv_h h_min,
- * h_pair mean, kahan on, graphs on, pair_tiles on, precision 64, dim 2, rho0 1.  Returns
+ * h_pair mean, kahan on, graphs on, pair_tiles 0, body_force off, no fringe forcing,
+ * precision 64, dim 2, rho0 1.  Returns
  * SPH_ERR_ARG on NULL. */
 SPH_API sph_status sph_default_params(sph_params* p);
 

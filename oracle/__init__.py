@@ -16,7 +16,11 @@ Functions and the passages they follow (paper sections / equations):
 * ``lattice_sum`` -- the reference sum of Eq. 8 on a perfect lattice.
 * ``neighbours`` -- all j with |x_i - x_j| < 2 h_ij (brute force or cells).
 * ``density`` -- Eq. 8 with Eq. 2.
-* ``forces`` -- Eq. 3 (row 2), 5, 6, 7 and Eq. 14-16.
+* ``forces`` -- Eq. 3 (row 2), 5, 6, 7 and Eq. 14-16 (plus the free-stream
+  forcing of ``fringe_rate`` when it is switched on).
+* ``fringe_rate`` -- the fringe-region forcing rate (Nordstrom et al. 1999),
+  standing in for the free-stream boundary Sec. 4.4 cites without giving it.
+* ``wall_force`` -- the force of the fluid on the walls (Eq. 18's F).
 * ``time_step`` -- Eq. 9-11.
 * ``step`` -- one kick-drift-kick step (Sec. 1, Sec. 3).
 * ``viscous``, ``pressure``, ``continuity`` -- Eq. 7, Eq. 3 (row 2) with
@@ -96,14 +100,19 @@ class Params(ctypes.Structure):
         ("u_ref", ctypes.c_double),
         ("dt_tv", ctypes.c_double),
         ("tv_p0", ctypes.c_double),
+        ("fs_lambda", ctypes.c_double),
+        ("fs_u", ctypes.c_double * 3),
+        ("fs_x", ctypes.c_double * 4),
     ]
 
 
 def make_params(dim, lo, L, periodic, rho0, c, eta, h_min, g=(0.0, 0.0, 0.0), u_ref=0.0,
                 tv_mode=TV_LIMITED, tv_h_per_particle=False, h_pair_max=False,
                 riemann_eta=3.0, tv_xi=-0.2, tv_C=1.0e3, tv_thresh=5.0e-4,
-                cfl_ad=0.25, cfl_ac=0.6) -> Params:
-    """Oracle parameters; defaults are the paper's constants (Eq. 6, 9-11, 15, 16)."""
+                cfl_ad=0.25, cfl_ac=0.6, fringe=None) -> Params:
+    """Oracle parameters; defaults are the paper's constants (Eq. 6, 9-11, 15, 16).
+    fringe = (lambda_max, (Ux, Uy, Uz), (x_start, x_end, rise, fall)) switches
+    on the free-stream forcing of ``fringe_rate``."""
     P = Params()
     P.dim = int(dim)
     for d in range(3):
@@ -117,6 +126,13 @@ def make_params(dim, lo, L, periodic, rho0, c, eta, h_min, g=(0.0, 0.0, 0.0), u_
     P.tv_xi, P.tv_C, P.tv_thresh = float(tv_xi), float(tv_C), float(tv_thresh)
     P.h_pair_max = int(bool(h_pair_max))
     P.cfl_ad, P.cfl_ac, P.u_ref = float(cfl_ad), float(cfl_ac), float(u_ref)
+    if fringe is not None:
+        lam, u, xs = fringe
+        P.fs_lambda = float(lam)
+        for d in range(3):
+            P.fs_u[d] = float(u[d])
+        for k in range(4):
+            P.fs_x[k] = float(xs[k])
     return P
 
 
@@ -166,6 +182,8 @@ def lib():
                 "orc_pressure": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
                 "orc_continuity": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
                 "orc_riemann_ustar": (ctypes.c_double, [_pp] + [ctypes.c_double] * 5),
+                "orc_fringe": (ctypes.c_double, [_pp, ctypes.c_double]),
+                "orc_wall_force": (None, [_pp, _i64, _dp, _dp, _dp, _dp, _bp, _dp, _dp, _ip, _ip, _dp]),
                 "orc_advection_step": (ctypes.c_double, [_pp, _i64, _dp, _bp, _dp]),
                 "orc_acoustic_step": (ctypes.c_double, [_pp, _i64, _dp, _bp]),
                 "orc_dual_step": (_i64, [_pp, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _bp, _dp, _dp, ctypes.c_int,
@@ -276,6 +294,28 @@ def forces(P, x, v, h, m, kind, vw, rho, nbrs):
     lib().orc_forces(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp), _d(vw), _d(rho),
                      start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), _d(a), _d(R), _d(chi), _d(dr))
     return {"a": a, "R": R, "chi": chi, "dr": dr}
+
+
+def fringe_rate(P, x):
+    """lambda(x) of the free-stream forcing lambda(x) (U_inf - v) (fringe
+    region along axis 0; 0 when P.fs_lambda is 0)."""
+    return lib().orc_fringe(ctypes.byref(P), float(x))
+
+
+def wall_force(P, x, v, h, m, kind, vw, rho, nbrs):
+    """Force of the fluid on the wall particles (the body of Eq. 18): minus
+    the sum over fluid i of m_i times its wall neighbours' pressure and
+    viscous terms.  Returns a 3-vector."""
+    n = len(x)
+    x, v, vw = _vec(x, n), _vec(v, n), _vec(vw, n)
+    h, m, rho = _sca(h, n), _sca(m, n), _sca(rho, n)
+    kind = _sca(kind, n, np.int8)
+    start, idx = nbrs
+    idx = np.ascontiguousarray(idx, dtype=np.int64) if len(idx) else np.zeros(1, np.int64)
+    F = np.zeros(3)
+    lib().orc_wall_force(ctypes.byref(P), n, _d(x), _d(v), _d(h), _d(m), kind.ctypes.data_as(_bp), _d(vw),
+                         _d(rho), start.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), _d(F))
+    return F
 
 
 def time_step(P, v, kind):

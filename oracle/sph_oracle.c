@@ -32,6 +32,10 @@
  *   Riemann continuity equation (U*) ................... Sec. 2.4, Eq. 3 (first row), Eq. 5 (first row),
  *                                                          Eq. 9-11, Sec. 3 (correction per advection step)
  *   background pressure p0 = alpha rho0 |v|_ad^2 ....... Eq. 12-13, alpha = 7
+ *   force on the body (drag and lift coefficients) ..... Eq. 18, Sec. 4.4
+ *   free stream in a periodic box: fringe-region forcing (Nordstrom et al.
+ *   1999), standing in for the free-stream boundary the paper cites without
+ *   specifying it ....................................... Sec. 4.4
  *
  * Readings where the paper is silent or ambiguous (each is also listed in the
  * design notes of the repository):
@@ -106,6 +110,12 @@ typedef struct {
     double u_ref;              /* reference velocity (Eq. 10) */
     double dt_tv;              /* step size in the background-pressure mode (tv_mode 3) */
     double tv_p0;              /* background pressure of Eq. 12; 0: rho0 c^2 (kick-drift-kick) */
+    /* free stream (flow past the cylinder, Sec. 4.4; the paper's free-stream
+     * boundary is not specified there): a fringe region along axis 0 in a
+     * periodic box forces the fluid toward the free stream (see orc_fringe) */
+    double fs_lambda;          /* peak forcing rate lambda_max (0: off) */
+    double fs_u[3];            /* free-stream velocity */
+    double fs_x[4];            /* x_start, x_end, rise length, fall length of the fringe */
 } orc_params;
 
 static int g_threads = 1;
@@ -404,6 +414,28 @@ double orc_tv_limiter(const orc_params* P, double s)
     return 0.0;
 }
 
+/* Free-stream forcing rate of the fringe region technique (Nordstrom, Nordin
+ * & Henningson, SIAM J. Sci. Comput. 20 (1999) 1365): the momentum equation
+ * gets lambda(x) (U_inf - v) with
+ *   lambda(x) = lambda_max [S((x - x_start)/d_rise) - S((x - x_end)/d_fall + 1)],
+ *   S(t) = 0 (t <= 0), 1 / (1 + exp(1/(t - 1) + 1/t)) (0 < t < 1), 1 (t >= 1),
+ * a smooth step from 0 to 1 over [0, 1] (S(t) + S(1 - t) = 1).  In a periodic
+ * box the region, placed downstream of the body, returns the wake to the free
+ * stream before it re-enters upstream.  The paper's free-stream boundary (Sec.
+ * 4.4) is not specified in it; this published forcing stands in for it. */
+static double fringe_step(double t)
+{
+    if (t <= 0.0) return 0.0;
+    if (t >= 1.0) return 1.0;
+    return 1.0 / (1.0 + exp(1.0 / (t - 1.0) + 1.0 / t));
+}
+
+double orc_fringe(const orc_params* P, double x)
+{
+    if (!(P->fs_lambda > 0.0)) return 0.0;
+    return P->fs_lambda * (fringe_step((x - P->fs_x[0]) / P->fs_x[2]) - fringe_step((x - P->fs_x[1]) / P->fs_x[3] + 1.0));
+}
+
 /* Pressure (Eq. 3, 5, 6) and viscous (Eq. 7) accelerations plus g, and the
  * zero-order residual R_i = sum_j V_j grad_i W_ij with the limited
  * displacement dr_i = xi chi_i h^2 R_i (Eq. 14-16), for every fluid i.
@@ -450,6 +482,11 @@ void orc_forces(const orc_params* P, int64_t n, const double* x, const double* v
                 Ri[d] += V_j * gradW[d];
             }
         }
+        if (P->fs_lambda > 0.0) {
+            /* free-stream forcing of the fringe region (orc_fringe) */
+            double lam = orc_fringe(P, x[3 * i]);
+            for (int d = 0; d < P->dim; ++d) ai[d] += lam * (P->fs_u[d] - vi[d]);
+        }
         double htv = P->tv_h_per_particle ? h[i] : P->h_min;
         double s = htv * htv * dot3(Ri, Ri);
         double ch = orc_tv_limiter(P, s);
@@ -465,6 +502,51 @@ void orc_forces(const orc_params* P, int64_t n, const double* x, const double* v
         }
         if (chi) chi[i] = ch;
     }
+}
+
+/* Force of the fluid on the wall particles (the body of Eq. 18, e.g. the
+ * cylinder of Sec. 4.4): minus the sum over fluid i of m_i times the pressure
+ * (Eq. 3, 5, 6) and viscous (Eq. 7) terms of i's wall neighbours, each pair
+ * term as in orc_forces (the wall stands in with rho_j = rho_i, p_j = p_i and
+ * its prescribed velocity).  F[3] out.  The drag and lift coefficients of
+ * Eq. 18 are C_D = 2 F_x / (rho0 U^2 D), C_L = 2 F_y / (rho0 U^2 D). */
+void orc_wall_force(const orc_params* P, int64_t n, const double* x, const double* v, const double* h,
+                    const double* m, const int8_t* kind, const double* vw, const double* rho,
+                    const int64_t* start, const int64_t* idx, double* F)
+{
+    const double c2 = P->c * P->c;
+    double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (kind[i]) continue;
+        const double rho_i = rho[i];
+        const double p_i = c2 * (rho_i - P->rho0);
+        const double* vi = v + 3 * i;
+        double fi[3] = {0, 0, 0};
+        for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+            int64_t j = idx[k];
+            if (j == i || !kind[j]) continue;
+            double rij[3];
+            orc_min_image(P, x + 3 * i, x + 3 * j, rij);
+            double r = norm3(rij);
+            if (r == 0.0) continue;
+            double dw = orc_kernel_dW(r, orc_pair_h(P, h[i], h[j]), P->dim);
+            double gradW[3], e[3];
+            for (int d = 0; d < 3; ++d) { gradW[d] = dw * rij[d] / r; e[d] = -rij[d] / r; }
+            const double rho_j = rho_i, p_j = p_i;
+            const double* vj = vw + 3 * j;
+            double ul = dot3(vi, e), ur = dot3(vj, e);
+            double pstar = orc_riemann_pstar(P, p_i, p_j, 0.5 * (rho_i + rho_j), ul, ur);
+            double cp = -2.0 * m[j] * pstar / (rho_i * rho_j);
+            double cv = 2.0 * m[j] * P->eta / (rho_i * rho_j) * dw / r;
+            for (int d = 0; d < 3; ++d) fi[d] += cp * gradW[d] + cv * (vi[d] - vj[d]);
+        }
+        Fx -= m[i] * fi[0];
+        Fy -= m[i] * fi[1];
+        Fz -= m[i] * fi[2];
+    }
+    F[0] = Fx;
+    F[1] = Fy;
+    F[2] = Fz;
 }
 
 /* ------------------------------------------------------------ integration */

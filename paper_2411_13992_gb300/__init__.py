@@ -62,7 +62,8 @@ class SphParams(ctypes.Structure):
         ("fixed_dt", ctypes.c_double),
         ("tv_h", ctypes.c_int32), ("h_pair", ctypes.c_int32), ("kahan", ctypes.c_int32),
         ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("graphs", ctypes.c_int32),
-        ("pair_tiles", ctypes.c_int32),
+        ("pair_tiles", ctypes.c_int32), ("body_force", ctypes.c_int32),
+        ("fringe_lambda", ctypes.c_double), ("fringe_u", ctypes.c_double * 3), ("fringe_x", ctypes.c_double * 4),
     ]
 
 
@@ -73,13 +74,14 @@ class SphDiag(ctypes.Structure):
         ("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
         ("vmax", ctypes.c_double), ("vt_max", ctypes.c_double), ("dr_max", ctypes.c_double),
         ("n_chi", ctypes.c_double), ("dt", ctypes.c_double), ("dt_next", ctypes.c_double),
-        ("steps", ctypes.c_double), ("substeps", ctypes.c_double),
+        ("steps", ctypes.c_double), ("substeps", ctypes.c_double), ("body_force", ctypes.c_double * 3),
     ]
 
     def as_dict(self):
         return {"mass": self.mass, "momentum": np.array(self.momentum[:]), "ke": self.kinetic, "vmax": self.vmax,
                 "vt_max": self.vt_max, "dr_max": self.dr_max, "n_chi": int(self.n_chi), "dt": self.dt,
-                "dt_next": self.dt_next, "steps": int(self.steps), "substeps": int(self.substeps)}
+                "dt_next": self.dt_next, "steps": int(self.steps), "substeps": int(self.substeps),
+                "body_force": np.array(self.body_force[:])}
 
 
 class SphCkpt(ctypes.Structure):

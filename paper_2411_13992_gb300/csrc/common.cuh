@@ -30,12 +30,13 @@ enum {
     DU_COUNT = 16
 };
 
-// Number of FP64 per-block partial values the fused force kernel writes.
-constexpr int kNPart = 10;
+// Number of FP64 per-block partial values the fused force kernel writes
+// (layout in block_partials).
+constexpr int kNPart = 12;
 // Indices into the device diagnostics block (doubles).
 enum {
     DG_MASS = 0, DG_MOM = 1, DG_KE = 4, DG_VMAX = 5, DG_VTMAX = 6, DG_DRMAX = 7, DG_NCHI = 8,
-    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_SUBSTEPS = 12, DG_COUNT = 16
+    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_SUBSTEPS = 12, DG_FBODY = 13, DG_COUNT = 16
 };
 
 // Cell grid of the cell-linked list: edge >= 2 h_max / R along every axis,
@@ -66,6 +67,14 @@ struct Consts {
     int tv_mode, tv_h_particle, h_pair_max, kahan;
     // uniform resolution (h_min == h_max): every pair has h_ij = h
     int uniform_h;
+    // sum the fluid's pair-force momentum rate (the body force of Eq. 18)
+    int body_force;
+    // fringe-region free-stream forcing lambda(x) (U_inf - v) along axis 0:
+    // fr_lambda (0: off), U_inf, and x0, x1, rise, fall
+    int fr_on;
+    Real fr_lambda;
+    Real fr_u[3];
+    Real fr_x[4];
     // h_u = h_max (the h of every pair at uniform resolution)
     Real h_u, inv_h_u, four_h2_u, dwr_coef_u;   // dwr_coef_u: W'(r)/r = dwr_coef_u t^3
 };

@@ -307,16 +307,22 @@ __global__ void __launch_bounds__(256, 2) k_forces_f64(int n, StateSet<double> S
         }
         double a[3] = {0, 0, 0}, R[3] = {0, 0, 0};
         double R2 = 0.0;
+        const double m_i = S.m[i];
+        // free-stream forcing lambda(x) (U_inf - v) of the fringe region
+        const double lam = K.fr_on ? fringe_rate<double>(K, xi[0]) : 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            a[d] = K.g[d] + acc_a[d].value();
+            const double pair_a = acc_a[d].value();
+            // the fluid's momentum rate from its pair terms: minus the force on the walls
+            if (K.body_force) part[9 + d] = m_i * pair_a;
+            a[d] = K.g[d] + pair_a;
+            if (K.fr_on) a[d] += lam * (K.fr_u[d] - vi[d]);
             R[d] = C * acc_R[d].value();
             R2 += R[d] * R[d];
         }
         const double htv = K.tv_h_particle ? hi : K.h_min;
         const double htv2 = htv * htv;
         const double chi = tv_limiter(K, htv2 * R2);
-        const double m_i = S.m[i];
         // Eq. 12 (background pressure p0 = rho0 c^2): dr = dt^2/2 a_bg = -(dt^2 p0 / rho_i) R_i
         const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
         const double bg = bgmode ? -(dt * dt * (K.rho0 * K.c2) / rho_i) : 0.0;
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(256, 2) k_forces_f64(int n, StateSet<double> S
         }
         chi_out[i] = 0.0;
     }
-    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart, true, K.body_force != 0);
 }
 
 // ================================================ diagnostics only
@@ -450,6 +456,7 @@ __global__ void __launch_bounds__(256) k_finalize(int nblocks, const double* __r
         diag[DG_DT] = count_step ? dt_used : 0.0;
         diag[DG_DTNEXT] = dt_next;
         diag[DG_STEPS] = count_step ? diag[DG_STEPS] + 1.0 : 0.0;
+        for (int d = 0; d < 3; ++d) diag[DG_FBODY + d] = -out[9 + d];    // force on the walls
         *dt_ptr = dt_next;
     }
 }

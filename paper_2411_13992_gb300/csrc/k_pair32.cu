@@ -817,16 +817,23 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
         }
         float a[3] = {0, 0, 0}, R[3] = {0, 0, 0};
         float R2 = 0.f;
+        const double m_i = S.m[i];
+        // free-stream forcing lambda(x) (U_inf - v) of the fringe region,
+        // at the particle's FP64 position along axis 0
+        const float lam = K.fr_on ? fringe_rate<float>(K, (float)S.x[i]) : 0.f;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            a[d] = K.g[d] + acc_a[d].value();
+            const float pair_a = acc_a[d].value();
+            // the fluid's momentum rate from its pair terms: minus the force on the walls
+            if (K.body_force) part[9 + d] = m_i * (double)pair_a;
+            a[d] = K.g[d] + pair_a;
+            if (K.fr_on) a[d] = fmaf(lam, K.fr_u[d] - vi[d], a[d]);
             R[d] = acc_R[d].value();
             R2 += R[d] * R[d];
         }
         const float htv = K.tv_h_particle ? hi : K.h_min;
         const float htv2 = htv * htv;
         const float chi = tv_limiter(K, htv2 * R2);
-        const double m_i = S.m[i];
         // Eq. 12 (background pressure p0 = rho0 c^2): dr = -(dt^2 p0 / rho_i) R_i
         // (its FP64 division only in that mode: FP64 is 1/74 of the FP32 rate)
         const bool bgmode = K.tv_mode == SPH_TV_BACKGROUND;
@@ -873,7 +880,7 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
         }
         chi_out[i] = 0.f;
     }
-    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart);
+    block_partials<true>(part, partials + (size_t)blockIdx.x * kNPart, true, K.body_force != 0);
 }
 
 // --------------------------------------------------------------- launchers

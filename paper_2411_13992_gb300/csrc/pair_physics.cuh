@@ -112,9 +112,30 @@ __device__ __forceinline__ void pair_force64(const Consts<double>& K, const Pair
     }
 }
 
+// Free-stream forcing rate of the fringe region technique (Nordstrom, Nordin
+// & Henningson 1999): lambda(x) = lambda_max [S((x - x0)/rise) - S((x -
+// x1)/fall + 1)] with the smooth step S(t) = 1/(1 + exp(1/(t - 1) + 1/t)) on
+// (0, 1), 0 below, 1 above; the acceleration gets lambda(x) (U_inf - v).
+template <typename Real>
+__device__ __forceinline__ Real fringe_step(Real t)
+{
+    if (t <= Real(0)) return Real(0);
+    if (t >= Real(1)) return Real(1);
+    return Real(1) / (Real(1) + exp(Real(1) / (t - Real(1)) + Real(1) / t));
+}
+
+template <typename Real>
+__device__ __forceinline__ Real fringe_rate(const Consts<Real>& K, Real x)
+{
+    return K.fr_lambda *
+           (fringe_step<Real>((x - K.fr_x[0]) / K.fr_x[2]) - fringe_step<Real>((x - K.fr_x[1]) / K.fr_x[3] + Real(1)));
+}
+
 // Block reduction of the diagnostics partials into out_block (layout: 0
 // mass, 1-3 momentum, 4 KE, 5 n_chi, 6 max|v|, 7 max|v + dr/dt|, 8 max|dr|,
-// 9 unused, written 0).  FIRST: per-particle values of a pair pass, with
+// 9-11 the fluid's momentum rate from its pair terms, sum m_i (a_i - g -
+// forcing), whose negative is the force on the walls; zero unless the pass
+// computes it).  FIRST: per-particle values of a pair pass, with
 // slot 5 a 0/1 flag and slots 6-8 the SQUARES of the magnitudes: the square
 // root of the largest square is the largest magnitude (both correctly
 // rounded), so one root per block replaces one per particle.  Otherwise:
@@ -125,7 +146,7 @@ __device__ __forceinline__ void pair_force64(const Consts<double>& K, const Pair
 // (1/74 of the FP32 rate on this part).  sums = false (the same for every
 // thread of the grid) when the caller's sums are all zero: they are skipped.
 template <bool FIRST>
-__device__ __forceinline__ void block_partials(double* vals, double* out_block, bool sums = true)
+__device__ __forceinline__ void block_partials(double* vals, double* out_block, bool sums = true, bool body = false)
 {
     __shared__ double sh[32][kNPart];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -146,6 +167,18 @@ __device__ __forceinline__ void block_partials(double* vals, double* out_block, 
             if (lane == 0) sh[w][k] = x;
         }
     }
+    // slots 9-11 (uniform over the grid: body is the same for every thread)
+    if (body || !FIRST) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            double x = vals[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            if (lane == 0) sh[w][k] = x;
+        }
+    } else if (lane == 0) {
+        for (int k = 9; k < 12; ++k) sh[w][k] = 0.0;
+    }
     if (FIRST) {
         const unsigned flags = __ballot_sync(0xffffffffu, __double_as_longlong(vals[5]) != 0);
         if (lane == 0) sh[w][5] = (double)__popc(flags);
@@ -159,14 +192,12 @@ __device__ __forceinline__ void block_partials(double* vals, double* out_block, 
         }
     }
     __syncthreads();
-    if (threadIdx.x < 9) {
+    if (threadIdx.x < kNPart) {
         const int k = threadIdx.x;
         double x = sh[0][k];
         for (int t = 1; t < nw; ++t) x = (k >= 6 && k <= 8) ? fmax(x, sh[t][k]) : x + sh[t][k];
-        if (FIRST && k >= 6) x = sqrt(x);
+        if (FIRST && k >= 6 && k <= 8) x = sqrt(x);
         out_block[k] = x;
-    } else if (threadIdx.x == 9) {
-        out_block[9] = 0.0;
     }
 }
 

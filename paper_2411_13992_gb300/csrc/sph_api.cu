@@ -140,6 +140,16 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
     if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
     if (p->pair_tiles < 0 || p->pair_tiles > 2) return SPH_ERR_ARG;
+    if (p->body_force != 0 && p->body_force != 1) return SPH_ERR_ARG;
+    if (!(p->fringe_lambda >= 0.0) || !std::isfinite(p->fringe_lambda)) return SPH_ERR_ARG;
+    if (p->fringe_lambda > 0.0) {
+        if (p->integrator != SPH_INT_KDK) return SPH_ERR_ARG;     // the forcing acts in the kick-drift-kick force pass
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(p->fringe_x[k])) return SPH_ERR_ARG;
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(p->fringe_u[d])) return SPH_ERR_ARG;
+        if (!(p->fringe_x[2] > 0.0) || !(p->fringe_x[3] > 0.0)) return SPH_ERR_ARG;
+    }
     if (p->integrator == SPH_INT_DUAL && (p->fixed_dt != 0.0 || p->adjoint_steps != 0)) return SPH_ERR_ARG;
     // the cell grid: each axis and the product of all axes bounded, so that
     // cell indices, the count and start arrays and the workspace size stay
@@ -227,6 +237,11 @@ Consts<Real> make_consts(const sph_params* p)
     K.h_pair_max = p->h_pair == SPH_HPAIR_MAX;
     K.kahan = p->kahan;
     K.uniform_h = p->h_min == p->h_max;
+    K.body_force = p->body_force;
+    K.fr_on = p->fringe_lambda > 0.0;
+    K.fr_lambda = (Real)p->fringe_lambda;
+    for (int d = 0; d < 3; ++d) K.fr_u[d] = (Real)p->fringe_u[d];
+    for (int k = 0; k < 4; ++k) K.fr_x[k] = (Real)p->fringe_x[k];
     K.h_u = (Real)p->h_max;
     K.inv_h_u = (Real)(1.0 / p->h_max);
     K.four_h2_u = (Real)(4.0 * p->h_max * p->h_max);
@@ -765,7 +780,7 @@ sph_status sph_default_params(sph_params* p)
     p->h_pair = SPH_HPAIR_MEAN;
     p->kahan = 1;
     p->graphs = 1;
-    p->pair_tiles = 1;
+    p->pair_tiles = 0;
     return SPH_OK;
 }
 
@@ -1061,6 +1076,7 @@ sph_status sph_get_diag(sph_ctx* c, sph_diag* out)
     out->dt_next = buf[DG_DTNEXT];
     out->steps = buf[DG_STEPS];
     out->substeps = buf[DG_SUBSTEPS];
+    for (int d = 0; d < 3; ++d) out->body_force[d] = buf[DG_FBODY + d];
     return SPH_OK;
 }
 
