@@ -177,6 +177,11 @@ typedef struct sph_diag {
                                the last force pass (minus the fluid's momentum rate from its
                                pair terms, which cancel between fluid pairs): the F of the
                                drag and lift coefficients of Eq. 18, C = 2 F / (rho0 U^2 D) */
+    double body_impulse[3]; /* kick-drift-kick with params.body_force: sum over the steps since
+                               sph_build_cells of each step's body force times its dt (its
+                               differences over an interval, divided by the interval's time,
+                               give the force averaged over every step of it) */
+    double time;            /* kick-drift-kick: simulated time since sph_build_cells (sum of dt) */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;

@@ -75,13 +75,15 @@ class SphDiag(ctypes.Structure):
         ("vmax", ctypes.c_double), ("vt_max", ctypes.c_double), ("dr_max", ctypes.c_double),
         ("n_chi", ctypes.c_double), ("dt", ctypes.c_double), ("dt_next", ctypes.c_double),
         ("steps", ctypes.c_double), ("substeps", ctypes.c_double), ("body_force", ctypes.c_double * 3),
+        ("body_impulse", ctypes.c_double * 3), ("time", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {"mass": self.mass, "momentum": np.array(self.momentum[:]), "ke": self.kinetic, "vmax": self.vmax,
                 "vt_max": self.vt_max, "dr_max": self.dr_max, "n_chi": int(self.n_chi), "dt": self.dt,
                 "dt_next": self.dt_next, "steps": int(self.steps), "substeps": int(self.substeps),
-                "body_force": np.array(self.body_force[:])}
+                "body_force": np.array(self.body_force[:]), "body_impulse": np.array(self.body_impulse[:]),
+                "time": self.time}
 
 
 class SphCkpt(ctypes.Structure):

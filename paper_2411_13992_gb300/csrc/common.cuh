@@ -36,7 +36,8 @@ constexpr int kNPart = 12;
 // Indices into the device diagnostics block (doubles).
 enum {
     DG_MASS = 0, DG_MOM = 1, DG_KE = 4, DG_VMAX = 5, DG_VTMAX = 6, DG_DRMAX = 7, DG_NCHI = 8,
-    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_SUBSTEPS = 12, DG_FBODY = 13, DG_COUNT = 16
+    DG_DT = 9, DG_DTNEXT = 10, DG_STEPS = 11, DG_SUBSTEPS = 12, DG_FBODY = 13, DG_IMPULSE = 16, DG_TIME = 19,
+    DG_COUNT = 20
 };
 
 // Cell grid of the cell-linked list: edge >= 2 h_max / R along every axis,

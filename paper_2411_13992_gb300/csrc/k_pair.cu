@@ -457,6 +457,10 @@ __global__ void __launch_bounds__(256) k_finalize(int nblocks, const double* __r
         diag[DG_DTNEXT] = dt_next;
         diag[DG_STEPS] = count_step ? diag[DG_STEPS] + 1.0 : 0.0;
         for (int d = 0; d < 3; ++d) diag[DG_FBODY + d] = -out[9 + d];    // force on the walls
+        // simulated time and the body's impulse since sph_build_cells (the time
+        // integral of the force over the steps, each step's force times its dt)
+        for (int d = 0; d < 3; ++d) diag[DG_IMPULSE + d] = count_step ? diag[DG_IMPULSE + d] - out[9 + d] * dt_used : 0.0;
+        diag[DG_TIME] = count_step ? diag[DG_TIME] + dt_used : 0.0;
         *dt_ptr = dt_next;
     }
 }

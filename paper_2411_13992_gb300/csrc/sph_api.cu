@@ -1077,6 +1077,8 @@ sph_status sph_get_diag(sph_ctx* c, sph_diag* out)
     out->steps = buf[DG_STEPS];
     out->substeps = buf[DG_SUBSTEPS];
     for (int d = 0; d < 3; ++d) out->body_force[d] = buf[DG_FBODY + d];
+    for (int d = 0; d < 3; ++d) out->body_impulse[d] = buf[DG_IMPULSE + d];
+    out->time = buf[DG_TIME];
     return SPH_OK;
 }
 

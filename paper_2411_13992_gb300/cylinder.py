@@ -10,8 +10,9 @@ free-stream boundary is named but not given in it; in its place a fringe
 region (Nordstrom, Nordin & Henningson 1999) over x in [24, 29.5] forces the
 wake back to the free stream before it re-enters the periodic box upstream
 (sph_params.fringe_*).  Every ``every`` steps it records the force of the
-fluid on the cylinder (sph_params.body_force) and the coefficients of
-Eq. 18, C_D = 2 F_x / (rho0 U^2 D) and C_L = 2 F_y / (rho0 U^2 D); over the
+fluid on the cylinder averaged over those steps (sph_params.body_force; the
+change of sph_diag.body_impulse over the change of sph_diag.time) and the
+coefficients of Eq. 18, C_D = 2 F_x / (rho0 U^2 D) and C_L = 2 F_y / (rho0 U^2 D); over the
 last ``window`` time units it reports the mean drag, and, from the
 coefficients smoothed by a running mean over ``smooth_width`` time units
 (the acoustic noise of the weakly compressible method lies far above the
@@ -78,16 +79,19 @@ def run(res: int = 36, t_end: float = 200.0, every: int = 20, window: float = 60
         sim.set_state()
         sim.build_cells()
         t, steps = 0.0, 0
+        imp = np.zeros(3)
         t0 = time.perf_counter()
         while t < t_end:
             sim.step(every)
             d = sim.diag()
-            t += d["dt"] * every          # the step size changes slowly; the last one stands for the batch
             steps += every
-            a, b = coefficients(d["body_force"], c["rho0"], c["U"], 1.0)
-            ts.append(t)
+            # the force averaged over every step of the interval: the change
+            # of the body's impulse over the change of the simulated time
+            a, b = coefficients((d["body_impulse"] - imp) / (d["time"] - t), c["rho0"], c["U"], 1.0)
+            ts.append(0.5 * (t + d["time"]))
             cd.append(a)
             cl.append(b)
+            t, imp = d["time"], d["body_impulse"].copy()
         sim.sync()
         wall = time.perf_counter() - t0
     finally:

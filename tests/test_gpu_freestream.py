@@ -108,3 +108,26 @@ def test_body_force_is_zero_unless_asked():
         assert np.all(sim.diag()["body_force"] == 0.0)
     finally:
         sim.close()
+
+
+def test_time_and_body_impulse_accumulate_over_the_steps():
+    """sph_diag.time is the sum of the steps' dt and body_impulse the sum of
+    each step's body force times its dt, both from zero at sph_build_cells."""
+    c, fr = _cylinder()
+    dt = 2.0e-4
+    sim = sph.Simulation(c, precision=64, body_force=1, fixed_dt=dt, graphs=0, **_lib_fringe(fr))
+    try:
+        sim.set_state()
+        sim.build_cells()
+        d0 = sim.diag()
+        assert d0["time"] == 0.0 and np.all(d0["body_impulse"] == 0.0)
+        imp = np.zeros(3)
+        for k in range(6):
+            sim.step(1)
+            d = sim.diag()
+            imp += d["body_force"] * dt
+            assert d["time"] == pytest.approx((k + 1) * dt, rel=1e-14)
+            np.testing.assert_allclose(d["body_impulse"], imp, rtol=1e-13, atol=1e-300)
+        assert np.abs(imp[:2]).max() > 0.0
+    finally:
+        sim.close()
