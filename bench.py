@@ -343,7 +343,8 @@ def _kernel_shares(prof):
 
 
 def _density_kernel_name(sim):
-    return "k_density32_tile<3,KSum>" if sim.params.pair_tiles else "k_density32<3,KSum,uniform>"
+    return {0: "k_density32<3,KSum,uniform>", 1: "k_density32_tile<3,KSum>",
+            2: "k_density32_coop<3,KSum>"}[int(sim.params.pair_tiles)]
 
 
 def run_native(args):
@@ -374,7 +375,7 @@ def run_native(args):
 
     # ---- FP32 form: the headline number.  The timed region holds the K steps
     # only: no per-kernel events inside it (the breakdown is a separate pass).
-    sim = sph.Simulation(case, precision=32)
+    sim = sph.Simulation(case, precision=32, pair_tiles=args.pair_tiles)
     sim.set_state()
     sim.build_cells()
     sim.step(args.warmup)
@@ -801,6 +802,8 @@ def main():
     ap.add_argument("--steady-steps", type=int, default=100, help="timed steps of the steady-state leg (0: skip)")
     ap.add_argument("--big-n", type=int, default=256, help="lattice side of the larger-lattice leg (0: skip)")
     ap.add_argument("--big-steps", type=int, default=20)
+    ap.add_argument("--pair-tiles", type=int, default=0, choices=(0, 1, 2),
+                    help="density pass of the headline: 0 row walk (default), 1 tile walk, 2 cooperative tile walk")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -55,33 +55,52 @@ def sample(x: np.ndarray, vel: np.ndarray, h: np.ndarray, vol: np.ndarray, pts: 
     return out
 
 
-def run(n: int, t_end: float, points: int = 37, precision: int = 32) -> dict:
-    """Step the Re = 1000 cavity at dp = 1/n to t_end; centre-line profiles."""
-    c = cases.cavity2d(n, U=1.0, Re=RE)
-    sim = Simulation(c, precision=precision, integrator=INT_DUAL)
-    try:
-        sim.set_state()
-        sim.build_cells()
-        t, steps = 0.0, 0
-        t0 = time.perf_counter()
-        while t < t_end:
-            sim.step(1)
-            t += sim.diag()["dt"]
-            steps += 1
-        sim.sync()
-        wall = time.perf_counter() - t0
-        st = sim.get_state()
-    finally:
-        sim.close()
+def _profiles(c, st, points):
     fl = c["kind"] == 0
     x, vel, h = st["x"][fl], st["v"][fl], c["h"][fl]
     vol = c["m"][fl] / st["rho"][fl]
     s = stations(points)
     u_line = sample(x, vel, h, vol, np.stack([np.full(points, 0.5), s], axis=1))[:, 0]
     v_line = sample(x, vel, h, vol, np.stack([s, np.full(points, 0.5)], axis=1))[:, 1]
+    return u_line, v_line
+
+
+def run(n: int, t_end: float, points: int = 37, precision: int = 32, average_from: float | None = None,
+        sample_dt: float = 0.5, **params) -> dict:
+    """Step the Re = 1000 cavity at dp = 1/n to t_end; centre-line profiles
+    at t_end, or averaged over samples every sample_dt from average_from to
+    t_end (the weakly compressible flow at Re = 1000 fluctuates: the
+    instantaneous extremes move by a few percent from one time to the next).
+    Extra keyword arguments are sph_params fields."""
+    c = cases.cavity2d(n, U=1.0, Re=RE)
+    sim = Simulation(c, precision=precision, integrator=INT_DUAL, **params)
+    u_acc, v_acc, nsamp = 0.0, 0.0, 0
+    try:
+        sim.set_state()
+        sim.build_cells()
+        t, steps = 0.0, 0
+        t_next = average_from
+        t0 = time.perf_counter()
+        while t < t_end:
+            sim.step(1)
+            t += sim.diag()["dt"]
+            steps += 1
+            if t_next is not None and t >= t_next and t < t_end:
+                u_line, v_line = _profiles(c, sim.get_state(), points)
+                u_acc, v_acc, nsamp = u_acc + u_line, v_acc + v_line, nsamp + 1
+                t_next += sample_dt
+        sim.sync()
+        wall = time.perf_counter() - t0
+        u_line, v_line = _profiles(c, sim.get_state(), points)
+        if t_next is not None:
+            u_line, v_line = (u_acc + u_line) / (nsamp + 1), (v_acc + v_line) / (nsamp + 1)
+            nsamp += 1
+    finally:
+        sim.close()
     return {"n": n, "dp": 1.0 / n, "t": t, "advection_steps": steps, "wall_s": wall,
+            "samples": max(nsamp, 1), "average_from": average_from,
             "u_min": float(u_line.min()), "v_max": float(v_line.max()), "v_min": float(v_line.min()),
-            "u_on_x_half": u_line.tolist(), "v_on_y_half": v_line.tolist(), "stations": s.tolist()}
+            "u_on_x_half": u_line.tolist(), "v_on_y_half": v_line.tolist(), "stations": stations(points).tolist()}
 
 
 def main():
@@ -89,10 +108,12 @@ def main():
     ap.add_argument("--n", type=int, nargs="+", default=[50, 100, 200])
     ap.add_argument("--t", type=float, default=60.0)
     ap.add_argument("--points", type=int, default=37)
+    ap.add_argument("--average-from", type=float, default=None,
+                    help="average the profiles over samples from this time to --t")
     ap.add_argument("--profiles", action="store_true", help="print the sampled profiles too")
     args = ap.parse_args()
     for n in args.n:
-        r = run(n, args.t, args.points)
+        r = run(n, args.t, args.points, average_from=args.average_from)
         if not args.profiles:
             for k in ("u_on_x_half", "v_on_y_half", "stations"):
                 r.pop(k)
