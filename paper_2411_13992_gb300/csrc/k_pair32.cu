@@ -68,53 +68,6 @@ __device__ __forceinline__ void pair_force32(const Consts<float>& K, const float
     }
 }
 
-// Per-particle factors of i for pair_force32f: P* and the coefficients of
-// the pair terms from the density deviations w = rho - rho0 (the form of the
-// FP64 pass): (p_i + p_j)/2 = hp_i + (c^2/2) w_j, (c/2) rho_bar = crho_i +
-// (c/4) w_j, and the factor C of W'/r = C t^3 taken out of the sums.
-struct PairI32 {
-    float w, inv_rho, hp, crho, m2_ir, eta_ir;
-};
-
-__device__ __forceinline__ PairI32 pair_i32(const Consts<float>& K, float w, float inv_rho)
-{
-    PairI32 I;
-    I.w = w;
-    I.inv_rho = inv_rho;
-    I.hp = (0.5f * K.c2) * w;
-    I.crho = (0.5f * K.c) * (K.rho0 + 0.5f * w);
-    I.m2_ir = -2.f * inv_rho;
-    I.eta_ir = K.two_eta * inv_rho;
-    return I;
-}
-
-// pair_force32 with t3 = W'/(r C): the same terms, accumulated without C.
-template <int DIM, typename Acc>
-__device__ __forceinline__ void pair_force32f(const Consts<float>& K, const float* rv, float inv_r, float t3,
-                                              const float* vi, const PairI32& I, const float4& oj, float m_j,
-                                              Acc* acc_a, Acc* acc_R)
-{
-    const bool wall = isinf(oj.w);
-    const float w_j = wall ? I.w : oj.w;
-    const float inv_rho_j = wall ? I.inv_rho : rcp_approx(K.rho0 + w_j);
-    const float dv[3] = {vi[0] - oj.x, vi[1] - oj.y, DIM == 3 ? vi[2] - oj.z : 0.f};
-    float dvr = dv[0] * rv[0] + dv[1] * rv[1];
-    if (DIM == 3) dvr += dv[2] * rv[2];
-    const float du = -dvr * inv_r;                           // U_l - U_r, e_ij from i to j
-    const float beta = __saturatef(K.beta_slope * K.inv_c * du);
-    const float hpsum = fmaf(0.5f * K.c2, w_j, I.hp);        // (p_i + p_j) / 2
-    const float crhobar = fmaf(0.25f * K.c, w_j, I.crho);    // (c/2) rho_bar
-    const float pstar = fmaf(beta * du, crhobar, hpsum);
-    const float g = m_j * inv_rho_j * t3;                    // V_j W'/(r C)
-    const float cpw = I.m2_ir * (g * pstar);                 // -2 m_j P* / (rho_i rho_j) W'/(r C)
-    const float cv = I.eta_ir * g;                           // 2 eta m_j / (rho_i rho_j) W'/(r C)
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        acc_a[d].add(cpw * rv[d] + cv * dv[d]);
-        acc_R[d].add(g * rv[d]);
-    }
-}
-
 // W'(r)/r for r < 2h: a_D h^-(D+2) (-5) t^3 with t = 1 - r/(2h).
 template <int DIM>
 __device__ __forceinline__ float dwr_of(float r, float inv_h, float coef)
@@ -145,7 +98,7 @@ __device__ __forceinline__ float w_term_uniform(const Consts<float>& K, float wn
 // (which may exceed cap: the force kernel then scans the cells itself).
 
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kTPB32, 9) k_density32(int n, const float4* __restrict__ pos4,
                                                       const int32_t* __restrict__ cell_of,
                                                       const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                       StateSet<float> S, float4* __restrict__ vr,
@@ -176,13 +129,13 @@ __global__ void __launch_bounds__(kTPB32) k_density32(int n, const float4* __res
     auto visit = [&](int j, uint32_t code, const float4& pj, float r2, float, float, float) {
         if (UNIFORM) {
             sigma.add(w_term_uniform(K, wnorm, r2));
-            if (r2 < K.four_h2_u && r2 > 0.f) {
-                if (cnt < cap) {
-                    *lp = ((uint32_t)j << kCodeBits) | code;
-                    lp += n;
-                }
-                ++cnt;
-            }
+            // the list write as predicated stores and a selected pointer step:
+            // no branch for the warp to diverge on
+            const bool take = r2 < K.four_h2_u && r2 > 0.f;
+            const bool store = take && cnt < cap;
+            if (store) *lp = ((uint32_t)j << kCodeBits) | code;
+            lp += store ? n : 0;
+            cnt += take ? 1 : 0;
         } else if (r2 < support2<UNIFORM>(K, hi, pj.w)) {
             const float inv_h = 1.f / pair_h(K, hi, pj.w);
             sigma.add(wendland_W<DIM, float>(sqrt_approx(r2), inv_h));
@@ -830,19 +783,20 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
         Acc acc_a[DIM], acc_R[DIM];
         // W'/r = coef t^3, coef = -5 a_D h^-(D+2) (uniform h: one constant)
         const float norm = kernel_norm<DIM, float>();
-        const PairI32 I = pair_i32(K, me.w, inv_rho_i);
         auto pair = [&](int j, const float4& pj, const float4& oj, const float* rv, float r2) {
             const float inv_r = rsqrtf(r2);
             const float r = r2 * inv_r;
+            float inv_h, m_j;
             if (UNIFORM) {
-                const float t = fmaf(-0.5f * K.inv_h_u, r, 1.f);
-                pair_force32f<DIM, Acc>(K, rv, inv_r, t * t * t, vi, I, oj, pj.w, acc_a, acc_R);
+                inv_h = K.inv_h_u;
+                m_j = pj.w;
             } else {
-                const float inv_h = __frcp_rn(pair_h(K, hi, pj.w));
-                const float coef = -5.f * norm * pow_dim<DIM, float>(inv_h) * inv_h * inv_h;
-                const float dwr = dwr_of<DIM>(r, inv_h, coef);
-                pair_force32<DIM, Acc>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, oj, mf[j], acc_a, acc_R);
+                inv_h = __frcp_rn(pair_h(K, hi, pj.w));
+                m_j = mf[j];
             }
+            const float coef = UNIFORM ? K.dwr_coef_u : -5.f * norm * pow_dim<DIM, float>(inv_h) * inv_h * inv_h;
+            const float dwr = dwr_of<DIM>(r, inv_h, coef);
+            pair_force32<DIM, Acc>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, oj, m_j, acc_a, acc_R);
         };
         const int cnt = nbc[i];
         if (cnt <= cap) {
@@ -895,12 +849,12 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             // at uniform resolution the sums were taken without the factor C of W'/r
-            const float pair_a = UNIFORM ? K.dwr_coef_u * acc_a[d].value() : acc_a[d].value();
+            const float pair_a = acc_a[d].value();
             // the fluid's momentum rate from its pair terms: minus the force on the walls
             if (K.body_force) part[9 + d] = m_i * (double)pair_a;
             a[d] = K.g[d] + pair_a;
             if (K.fr_on) a[d] = fmaf(lam, K.fr_u[d] - vi[d], a[d]);
-            R[d] = UNIFORM ? K.dwr_coef_u * acc_R[d].value() : acc_R[d].value();
+            R[d] = acc_R[d].value();
             R2 += R[d] * R[d];
         }
         const float htv = K.tv_h_particle ? hi : K.h_min;
