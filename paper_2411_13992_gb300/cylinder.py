@@ -13,11 +13,9 @@ wake back to the free stream before it re-enters the periodic box upstream
 fluid on the cylinder averaged over those steps (sph_params.body_force; the
 change of sph_diag.body_impulse over the change of sph_diag.time) and the
 coefficients of Eq. 18, C_D = 2 F_x / (rho0 U^2 D) and C_L = 2 F_y / (rho0 U^2 D); over the
-last ``window`` time units it reports the mean drag, and, from the
-coefficients smoothed by a running mean over ``smooth_width`` time units
-(the acoustic noise of the weakly compressible method lies far above the
-shedding frequency), the lift amplitude and the Strouhal number St = f D / U
-from the mean period between upward zero crossings of C_L.  Table 2 of the paper reports C_D = 1.48 +- 0.015,
+last ``window`` time units it reports the mean drag and, from the spectrum
+of C_L (``shedding``), the Strouhal number St = f D / U and the lift and drag
+oscillation amplitudes.  Table 2 of the paper reports C_D = 1.48 +- 0.015,
 C_L = +-0.405 and St = 0.178 at D/dp = 80 (context, not a target here).
 
     python -m paper_2411_13992_gb300.cylinder --res 36 --t 200
@@ -42,35 +40,37 @@ def coefficients(F, rho0=1.0, U=1.0, D=1.0):
     return 2.0 * F[0] / (rho0 * U * U * D), 2.0 * F[1] / (rho0 * U * U * D)
 
 
-def smooth(t: np.ndarray, y: np.ndarray, width: float) -> np.ndarray:
-    """Running mean of y over a window of the given width in time: the body
-    force of a weakly compressible particle method carries acoustic noise at
-    frequencies far above the shedding frequency (c = 10 U), which the
-    window removes."""
-    out = np.empty_like(y)
-    lo = 0
-    csum = np.concatenate([[0.0], np.cumsum(y)])
-    for k in range(len(t)):
-        while t[k] - t[lo] > width:
-            lo += 1
-        out[k] = (csum[k + 1] - csum[lo]) / (k + 1 - lo)
-    return out
+def shedding(t: np.ndarray, cl: np.ndarray, cd: np.ndarray, band=(0.05, 0.5), D=1.0, U=1.0) -> dict:
+    """Strouhal number and lift amplitude from a C_L history: the body force
+    of a weakly compressible particle method carries acoustic noise (c = 10 U)
+    at frequencies far above the shedding frequency, so the history is
+    resampled on a uniform grid, the shedding frequency f0 is the largest
+    peak of the Hann-windowed spectrum of C_L in ``band`` (in U/D, with a
+    Gaussian interpolation between bins), and the lift amplitude is sqrt(2) times the RMS of C_L
+    band-passed to [f0/2, 3 f0/2]; the drag oscillates at 2 f0 and is
+    band-passed to [3 f0/2, 5 f0/2].  St = f0 D / U."""
+    tu = np.linspace(t[0], t[-1], len(t))
+    dt = tu[1] - tu[0]
+    f = np.fft.rfftfreq(len(tu), dt)
+    yl = np.interp(tu, t, cl - cl.mean())
+    L = np.fft.rfft(yl)
+    Dr = np.fft.rfft(np.interp(tu, t, cd - cd.mean()))
+    # the peak from the Hann-windowed spectrum, interpolated on its logarithm
+    # (a Gaussian fit through the three bins around the maximum)
+    Lw = np.abs(np.fft.rfft(yl * np.hanning(len(yl))))
+    sel = np.flatnonzero((f >= band[0]) & (f <= band[1]))
+    k = sel[np.argmax(Lw[sel])]
+    a, b, c = np.log(Lw[k - 1]), np.log(Lw[k]), np.log(Lw[k + 1])
+    f0 = f[k] + 0.5 * (a - c) / (a - 2 * b + c) * (f[1] - f[0])
+
+    def amp(X, lo, hi):
+        return float(np.sqrt(2.0) * np.fft.irfft(np.where((f >= lo) & (f <= hi), X, 0), len(tu)).std())
+
+    return {"St": float(f0 * D / U), "C_L_amplitude": amp(L, 0.5 * f0, 1.5 * f0),
+            "C_D_amplitude": amp(Dr, 1.5 * f0, 2.5 * f0), "frequency_resolution": float(f[1] - f[0])}
 
 
-def strouhal(t: np.ndarray, cl: np.ndarray, D=1.0, U=1.0):
-    """St = f D / U from the mean period between upward zero crossings of
-    C_L - mean(C_L) (linear interpolation between samples; pass a smoothed
-    signal); None with fewer than two crossings."""
-    y = cl - cl.mean()
-    k = np.flatnonzero((y[:-1] < 0.0) & (y[1:] >= 0.0))
-    if len(k) < 2:
-        return None
-    tc = t[k] - y[k] * (t[k + 1] - t[k]) / (y[k + 1] - y[k])
-    return float(D / (U * np.mean(np.diff(tc))))
-
-
-def run(res: int = 36, t_end: float = 200.0, every: int = 20, window: float = 60.0, precision: int = 32,
-        smooth_width: float = 1.0) -> dict:
+def run(res: int = 36, t_end: float = 200.0, every: int = 20, window: float = 100.0, precision: int = 32) -> dict:
     c = cases.cylinder2d(res=res)
     lam, u, xs = FRINGE
     sim = Simulation(c, precision=precision, body_force=1, fringe_lambda=lam, fringe_u=u, fringe_x=xs)
@@ -98,15 +98,13 @@ def run(res: int = 36, t_end: float = 200.0, every: int = 20, window: float = 60
         sim.close()
     ts, cd, cl = np.array(ts), np.array(cd), np.array(cl)
     late = ts > t_end - window
-    cds, cls = smooth(ts, cd, smooth_width), smooth(ts, cl, smooth_width)
-    return {"res": res, "D_over_dp_min": 2 * res, "particles": int(c["n"]), "t": float(ts[-1]), "steps": steps,
-            "wall_s": wall, "window": [float(t_end - window), float(t_end)], "smoothing_width": smooth_width,
-            "C_D_mean": float(cd[late].mean()),
-            "C_D_amplitude": float(0.5 * (cds[late].max() - cds[late].min())),
-            "C_L_amplitude": float(0.5 * (cls[late].max() - cls[late].min())),
-            "St": strouhal(ts[late], cls[late]),
-            "paper_table2_present": {"C_D": "1.48 +- 0.015", "C_L": "+-0.405", "St": 0.178, "D_over_dp": 80},
-            "history": {"t": ts.tolist(), "C_D": cd.tolist(), "C_L": cl.tolist()}}
+    out = {"res": res, "D_over_dp_min": 2 * res, "particles": int(c["n"]), "t": float(ts[-1]), "steps": steps,
+           "wall_s": wall, "window": [float(t_end - window), float(t_end)], "C_D_mean": float(cd[late].mean())}
+    out.update(shedding(ts[late], cl[late], cd[late]))
+    out.update({
+        "paper_table2_present": {"C_D": "1.48 +- 0.015", "C_L": "+-0.405", "St": 0.178, "D_over_dp": 80},
+        "history": {"t": ts.tolist(), "C_D": cd.tolist(), "C_L": cl.tolist()}})
+    return out
 
 
 def main():
@@ -114,7 +112,7 @@ def main():
     ap.add_argument("--res", type=int, default=36)
     ap.add_argument("--t", type=float, default=200.0)
     ap.add_argument("--every", type=int, default=20)
-    ap.add_argument("--window", type=float, default=60.0)
+    ap.add_argument("--window", type=float, default=100.0)
     ap.add_argument("--history", action="store_true", help="print the C_D, C_L history too")
     args = ap.parse_args()
     r = run(args.res, args.t, args.every, args.window)
