@@ -97,8 +97,12 @@ __device__ __forceinline__ float w_term_uniform(const Consts<float>& K, float wn
 // entry k of particle i at nbl[k * n + i] = (j << 7) | code, and the count
 // (which may exceed cap: the force kernel then scans the cells itself).
 
+// Register budget: eight blocks of 128 threads per SM (at most 64 registers;
+// 56 used, no spills).  The compiler's own choice, 48 registers with spills,
+// ran the 128^3 pass 7 % longer early in the run and 25 % longer after step
+// 400; nine and seven blocks were within 1-3 % of eight.
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32, 9) k_density32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kTPB32, 8) k_density32(int n, const float4* __restrict__ pos4,
                                                       const int32_t* __restrict__ cell_of,
                                                       const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                       StateSet<float> S, float4* __restrict__ vr,
