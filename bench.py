@@ -344,7 +344,7 @@ def _kernel_shares(prof):
 
 def _density_kernel_name(sim):
     return {0: "k_density32<3,KSum,uniform>", 1: "k_density32_tile<3,KSum>",
-            2: "k_density32_coop<3,KSum>"}[int(sim.params.pair_tiles)]
+            2: "k_density32_coop<3,KSum>", 3: "k_density32_flat<3,KSum>"}[int(sim.params.pair_tiles)]
 
 
 def run_native(args):
@@ -802,8 +802,9 @@ def main():
     ap.add_argument("--steady-steps", type=int, default=100, help="timed steps of the steady-state leg (0: skip)")
     ap.add_argument("--big-n", type=int, default=256, help="lattice side of the larger-lattice leg (0: skip)")
     ap.add_argument("--big-steps", type=int, default=20)
-    ap.add_argument("--pair-tiles", type=int, default=0, choices=(0, 1, 2),
-                    help="density pass of the headline: 0 row walk (default), 1 tile walk, 2 cooperative tile walk")
+    ap.add_argument("--pair-tiles", type=int, default=0, choices=(0, 1, 2, 3),
+                    help="density pass of the headline: 0 row walk (default), 1 tile walk, 2 cooperative tile "
+                         "walk, 3 flattened tile walk")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

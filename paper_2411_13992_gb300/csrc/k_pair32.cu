@@ -492,6 +492,152 @@ __global__ void __launch_bounds__(TileThreads<DIM>::WALK) k_density32_tile(
     }
 }
 
+// ------------------------------------ density on tiles, flattened row walk
+//
+// The tile walk with the rows of a particle's stencil walked as one sequence
+// per lane: each lane first lists its particle's clipped row runs (tile
+// start and length per stencil row, in shared memory, row-major so that the
+// lanes of a warp read distinct banks), then steps through them two
+// candidates at a time, moving to its next non-empty row when a run ends,
+// while the other lanes of the warp are still inside theirs.  The warp then
+// runs as many iterations as its longest particle has candidates, not the
+// sum over rows of each row's longest run.  Same candidates, order and
+// arithmetic as the row walk: the same sums and lists bit for bit.
+
+constexpr int kFlatThreads3 = 160, kFlatThreads2 = 128;
+template <int DIM> struct FlatShape {
+    static constexpr int T = DIM == 3 ? kFlatThreads3 : kFlatThreads2;
+    static constexpr int NR = DIM == 3 ? kSide * kSide : kSide;    // stencil rows
+};
+
+template <int DIM>
+__host__ __device__ constexpr size_t flat_table_bytes()
+{
+    return (size_t)FlatShape<DIM>::NR * FlatShape<DIM>::T * sizeof(uint32_t);
+}
+
+template <int DIM, typename Acc>
+__global__ void __launch_bounds__(FlatShape<DIM>::T) k_density32_flat(
+    int n, const float4* __restrict__ pos4c, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ start,
+    Grid G, Consts<float> K, StateSet<float> S, float4* __restrict__ vr, uint32_t* __restrict__ nbl,
+    int32_t* __restrict__ nbc, int cap, int nb0, int nb1, int tile_cap)
+{
+    using TD = TileDims<DIM>;
+    constexpr int T = FlatShape<DIM>::T, NR = FlatShape<DIM>::NR, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
+    constexpr int Rz = DIM == 3 ? R : 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_warp[T / 32 + 1];
+    __shared__ int s_home[TD::NHOME + 1];
+    __shared__ float4 s_rowc[NR];            // per stencil row: shy, shz, code of (dy, dz) with dx = -R, -
+    uint32_t* runs = (uint32_t*)smem;        // [NR][T]: tile start | run length << 16
+    TileView V;
+    V.pos = (float4*)(smem + flat_table_bytes<DIM>());
+    V.gid = (int*)(V.pos + tile_cap);
+    V.ts = V.gid + tile_cap;
+    V.gs = V.ts + NHC + 1;
+    V.home = s_home;
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    for (int r = threadIdx.x; r < NR; r += T) {
+        const int dy = r % kSide - R, dz = DIM == 3 ? r / kSide - R : 0;
+        s_rowc[r] = make_float4(-(float)dy * ey, -(float)dz * ez,
+                                __int_as_float(R + kSide * (dy + R) + kSide * kSide * (dz + R)), 0.f);
+    }
+    stage_tile<DIM, T>(V, G, start, pos4c, nb0, nb1, tile_cap, s_warp);
+    const int nhome = V.home[V.byn * V.bzn];
+
+    const float inv_ex = 1.f / ex;
+    const float reach = 2.f * K.h_u;
+    const float reach2 = reach * reach;
+    const float wnorm = kernel_norm<DIM, float>() * pow_dim<DIM, float>(K.inv_h_u);
+    for (int t = threadIdx.x; t < nhome; t += T) {
+        int hy_i, hz_i, s, i;
+        home_particle<DIM>(V, t, hy_i, hz_i, s, i);
+        const int8_t kind = S.kind[i];
+        const float s0 = (float)S.s0[i];
+        float vi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) vi[d] = S.v[(size_t)d * n + i];
+        if (kind) {
+            vr[i] = make_float4(vi[0], vi[1], vi[2], __int_as_float(0x7f800000));
+            nbc[i] = 0;
+            continue;
+        }
+        Acc sigma;
+        int cnt = 0;
+        uint32_t* lp = nbl + i;
+        auto candidate = [&](float r2, uint32_t entry) {
+            sigma.add(w_term_uniform(K, wnorm, r2));
+            const bool take = r2 < K.four_h2_u && r2 > 0.f;
+            const bool store = take && cnt < cap;
+            if (store) *lp = entry;
+            lp += store ? n : 0;
+            cnt += take ? 1 : 0;
+        };
+        if (V.fits) {
+            const float4 pi = V.pos[s];
+            const float oi[3] = {pi.x, pi.y, pi.z};
+            const int hx_i = __float_as_int(pi.w);
+            // this lane's row runs: tile start and length of each stencil row
+            for (int r = 0; r < NR; ++r) {
+                const int dy = r % kSide - R, dz = DIM == 3 ? r / kSide - R : 0;
+                int dxlo, dxhi;
+                uint32_t run = 0;
+                if (row_extent<DIM>(oi, dy, dz, reach2, ex, ey, ez, inv_ex, dxlo, dxhi)) {
+                    const int rowc = (hy_i + dy + H1 * (hz_i + dz)) * H0 + hx_i;
+                    const int t0 = V.ts[rowc + dxlo];
+                    run = (uint32_t)t0 | ((uint32_t)(V.ts[rowc + dxhi + 1] - t0) << 16);
+                }
+                runs[r * T + threadIdx.x] = run;
+            }
+            // the flattened walk: (row, position, end) of this lane
+            int r = -1, tj = 0, tend = 0;
+            float shy = 0.f, shz = 0.f;
+            uint32_t code_row = 0;
+            auto next_row = [&]() {
+                while (tj >= tend && ++r < NR) {
+                    const uint32_t run = runs[r * T + threadIdx.x];
+                    tj = (int)(run & 0xffffu);
+                    tend = tj + (int)(run >> 16);
+                }
+                if (r < NR) {
+                    const float4 rc = s_rowc[r];
+                    shy = rc.x;
+                    shz = rc.y;
+                    code_row = (uint32_t)__float_as_int(rc.z) - (uint32_t)hx_i;
+                }
+            };
+            next_row();
+            auto one = [&](int tq, const float4& pj) {
+                const float r2 = tile_r2<DIM>(oi, hx_i, pj, ex, shy, shz);
+                candidate(r2, ((uint32_t)V.gid[tq] << kCodeBits) | (code_row + (uint32_t)__float_as_int(pj.w)));
+            };
+            while (r < NR) {
+                if (tj + 1 < tend) {
+                    const float4 p0 = V.pos[tj], p1 = V.pos[tj + 1];
+                    one(tj, p0);
+                    one(tj + 1, p1);
+                    tj += 2;
+                } else {
+                    one(tj, V.pos[tj]);
+                    tj += 1;
+                }
+                if (tj >= tend) next_row();
+            }
+        } else {
+            // the halo does not fit the tile: the row walk over global memory
+            const float4 pi = pos4c[i];
+            const float oi[3] = {pi.x, pi.y, pi.z};
+            auto visit = [&](int j, uint32_t code, const float4&, float r2, float, float, float) {
+                candidate(r2, ((uint32_t)j << kCodeBits) | code);
+            };
+            for_candidates_rows<DIM, true, true>(oi, reach, cell_of[i], G, start, cell_of, pos4c, visit);
+        }
+        nbc[i] = cnt;
+        const float w = K.rho0 * (sigma.value() - s0) / s0;
+        vr[i] = make_float4(vi[0], vi[1], vi[2], w);
+    }
+}
+
 // ---------------------------------- density on tiles, lanes sharing a particle
 //
 // The same staged tile, walked cooperatively: a group of G lanes (8 in 3-D,
@@ -949,18 +1095,19 @@ static cudaError_t density_tile_t(int mode, int n, const float4* pos4c, const in
     const int nb0 = (G.nc[0] + SH::B0 - 1) / SH::B0, nb1 = (G.nc[1] + SH::B1 - 1) / SH::B1;
     const int nb2 = DIM == 3 ? (G.nc[2] + SH::B2 - 1) / SH::B2 : 1;
     const int cap = tile_capacity<DIM>(n, G);
-    const bool coop = mode == 2;
-    const size_t smem = tile_smem_bytes<DIM>(cap, coop ? coop_table_bytes<DIM>() : 0);
-    auto kern = coop ? k_density32_coop<DIM, Acc> : k_density32_tile<DIM, Acc>;
+    const int v = mode - 1;      // 0 tile walk, 1 cooperative, 2 flattened
+    const size_t extra = v == 1 ? coop_table_bytes<DIM>() : (v == 2 ? flat_table_bytes<DIM>() : 0);
+    const size_t smem = tile_smem_bytes<DIM>(cap, extra);
+    auto kern = v == 1 ? k_density32_coop<DIM, Acc> : (v == 2 ? k_density32_flat<DIM, Acc> : k_density32_tile<DIM, Acc>);
     // opt in to more than 48 KB of dynamic shared memory once per kernel (and
     // again only for a larger size)
-    static size_t opted[2] = {48 * 1024, 48 * 1024};
-    if (smem > opted[coop]) {
+    static size_t opted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+    if (smem > opted[v]) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        opted[coop] = smem;
+        opted[v] = smem;
     }
-    const int threads = coop ? TileThreads<DIM>::COOP : TileThreads<DIM>::WALK;
+    const int threads = v == 1 ? TileThreads<DIM>::COOP : (v == 2 ? FlatShape<DIM>::T : TileThreads<DIM>::WALK);
     kern<<<nb0 * nb1 * nb2, threads, smem, st>>>(n, pos4c, cell_of, start, G, K, S, vr, nbl, nbc, nbl_capacity(DIM),
                                                  nb0, nb1, cap);
     return cudaGetLastError();

@@ -139,7 +139,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->adjoint_steps < 0 || p->adjoint_steps > 100000) return SPH_ERR_ARG;
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
     if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
-    if (p->pair_tiles < 0 || p->pair_tiles > 2) return SPH_ERR_ARG;
+    if (p->pair_tiles < 0 || p->pair_tiles > 3) return SPH_ERR_ARG;
     if (p->body_force != 0 && p->body_force != 1) return SPH_ERR_ARG;
     if (!(p->fringe_lambda >= 0.0) || !std::isfinite(p->fringe_lambda)) return SPH_ERR_ARG;
     if (p->fringe_lambda > 0.0) {

@@ -82,7 +82,7 @@ def test_workspace_query_and_argument_checks(lib):
         dict(h_max=0.5 * c["h_min"]), dict(tv_mode=4), dict(fixed_dt=-1.0), dict(adjoint_steps=-1),
         dict(h_max=0.3),          # fewer than 5 cells along a periodic axis
         dict(integrator=2), dict(integrator=1, fixed_dt=1e-3), dict(integrator=1, adjoint_steps=4), dict(graphs=2),
-        dict(pair_tiles=3), dict(pair_tiles=-1),
+        dict(pair_tiles=4), dict(pair_tiles=-1),
     ]
     for kw in bad:
         q = sph.params_from_case(c, 64)

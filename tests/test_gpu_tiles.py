@@ -2,7 +2,8 @@
 row walk over global memory (sph_params.pair_tiles = 0).  pair_tiles = 1,
 one thread per particle over the tile, visits the same candidates in the
 same order with the same arithmetic, so every state field after several
-steps is bit for bit the same.  pair_tiles = 2, groups of lanes sharing a
+steps is bit for bit the same; so does pair_tiles = 3, the same walk with
+each lane's rows taken as one sequence.  pair_tiles = 2, groups of lanes sharing a
 particle's candidates, writes the same neighbour lists but sums sigma in
 another order: its densities agree to FP32 rounding, and it is checked
 against the FP64 oracle like the other FP32 paths.  Cases: partial edge
@@ -60,19 +61,21 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("mode", [1, 3])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_tiled_walk_is_bit_identical_to_the_row_walk(name):
+def test_tiled_walk_is_bit_identical_to_the_row_walk(name, mode):
     c = CASES[name]()
-    got, d_got = _run(c, 1, 5)
+    got, d_got = _run(c, mode, 5)
     ref, d_ref = _run(c, 0, 5)
     for k in FIELDS:
         assert np.array_equal(got[k], ref[k]), (name, k)
     assert d_got["ke"] == d_ref["ke"]
 
 
-def test_tiled_density_is_bit_identical_in_the_dual_criteria_integrator():
+@pytest.mark.parametrize("mode", [1, 3])
+def test_tiled_density_is_bit_identical_in_the_dual_criteria_integrator(mode):
     c = cases.tgv3d(20)
-    got, d_got = _run(c, 1, 3, integrator=sph.INT_DUAL)
+    got, d_got = _run(c, mode, 3, integrator=sph.INT_DUAL)
     ref, d_ref = _run(c, 0, 3, integrator=sph.INT_DUAL)
     for k in ("x", "v", "rho"):
         assert np.array_equal(got[k], ref[k]), k
