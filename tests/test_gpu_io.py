@@ -59,3 +59,39 @@ def test_every_source_and_destination_gives_the_same_state(precision):
                 assert np.array_equal(st[k], ref[k]), (kind, dest, k)
     # rows come back in the caller's order: particle k's position moved by less than a cell
     assert np.abs(ref["x"] - c["x"]).max() < c["h_max"]
+
+
+def test_save_ckpt_writes_the_state_the_adjoint_replays_from():
+    """sph_save_ckpt writes x, v, a, dr as sph_get_state does, with the next
+    step size and the step count of sph_get_diag; an adjoint segment replayed
+    from it equals one replayed from sph_get_state's arrays."""
+    import torch
+    from paper_2411_13992_gb300 import cases
+    c = cases.tgv2d(24)
+    sim = sph.Simulation(c, precision=64, fixed_dt=1.0e-3, adjoint_steps=3)
+    try:
+        sim.set_state()
+        sim.build_cells()
+        sim.step(4)
+        n = c["n"]
+        ck = {k: np.zeros((n, 3)) for k in ("x", "v", "a", "dr")}
+        dt_next, steps = sph.sph_save_ckpt(sim.ctx, ck["x"], ck["v"], ck["a"], ck["dr"])
+        st = sim.get_state()
+        for k in ("x", "v", "a", "dr"):
+            assert np.array_equal(ck[k], st[k]), k
+        d = sim.diag()
+        assert dt_next == d["dt_next"] and steps == d["steps"] == 4
+        # device destinations too
+        dev = {k: torch.zeros((n, 3), dtype=torch.float64, device=sim.device) for k in ck}
+        sph.sph_save_ckpt(sim.ctx, dev["x"], dev["v"], dev["a"], dev["dr"])
+        for k in ck:
+            assert np.array_equal(dev[k].cpu().numpy(), ck[k]), k
+        outs = []
+        for src in (ck, st):
+            xb, vb = np.ones((n, 3)), np.zeros((n, 3))
+            ab, drb = np.zeros((n, 3)), np.zeros((n, 3))
+            eb = sph.sph_step_adjoint(sim.ctx, src["x"], src["v"], src["a"], src["dr"], 3, xb, vb, ab, drb)
+            outs.append((xb, vb, eb))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    finally:
+        sim.close()
