@@ -954,20 +954,7 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
             // Software pipeline: the list entry two ahead and the neighbour
             // data one ahead are in flight while this pair is computed.
             const uint32_t* lp = nbl + i;
-            uint32_t e_cur = cnt > 0 ? lp[0] : 0u;
-            uint32_t e_nxt = cnt > 1 ? lp[(size_t)n] : 0u;
-            float4 pj_n = pos4[e_cur >> kCodeBits];
-            float4 oj_n = vr[e_cur >> kCodeBits];
-            for (int k = 0; k < cnt; ++k) {
-                const uint32_t ec = e_cur;
-                const float4 pj = pj_n;
-                const float4 oj = oj_n;
-                if (k + 1 < cnt) {
-                    pj_n = pos4[e_nxt >> kCodeBits];
-                    oj_n = vr[e_nxt >> kCodeBits];
-                }
-                e_cur = e_nxt;
-                e_nxt = (k + 2 < cnt) ? lp[(size_t)(k + 2) * n] : 0u;
+            auto one = [&](uint32_t ec, const float4& pj, const float4& oj) {
                 const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
                 float rv[3];
                 rv[0] = (oi[0] - pj.x) + sh.x;
@@ -979,7 +966,27 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
                     r2 += rv[2] * rv[2];
                 }
                 pair((int)(ec >> kCodeBits), pj, oj, rv, r2);
+            };
+            // two pairs per iteration in ping-pong registers: the neighbour
+            // data one pair ahead and the list entries two ahead in flight
+            uint32_t eA = cnt > 0 ? lp[0] : 0u;
+            uint32_t eB = cnt > 1 ? lp[(size_t)n] : 0u;
+            float4 pA = pos4[eA >> kCodeBits], oA = vr[eA >> kCodeBits];
+            int k = 0;
+            for (; k + 1 < cnt; k += 2) {
+                const float4 pB = pos4[eB >> kCodeBits], oB = vr[eB >> kCodeBits];
+                const uint32_t eC = k + 2 < cnt ? lp[(size_t)(k + 2) * n] : 0u;
+                one(eA, pA, oA);
+                if (k + 2 < cnt) {
+                    pA = pos4[eC >> kCodeBits];
+                    oA = vr[eC >> kCodeBits];
+                }
+                const uint32_t eD = k + 3 < cnt ? lp[(size_t)(k + 3) * n] : 0u;
+                one(eB, pB, oB);
+                eA = eC;
+                eB = eD;
             }
+            if (k < cnt) one(eA, pA, oA);
         } else {
             // more neighbours than the list holds: scan the cells
             auto visit = [&](int j, uint32_t, const float4& pj, float r2, float rx, float ry, float rz) {
