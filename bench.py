@@ -375,7 +375,7 @@ def run_native(args):
 
     # ---- FP32 form: the headline number.  The timed region holds the K steps
     # only: no per-kernel events inside it (the breakdown is a separate pass).
-    sim = sph.Simulation(case, precision=32, pair_tiles=args.pair_tiles)
+    sim = sph.Simulation(case, precision=32, pair_tiles=args.pair_tiles, x_subcells=args.x_subcells)
     sim.set_state()
     sim.build_cells()
     sim.step(args.warmup)
@@ -522,7 +522,7 @@ def run_native(args):
             "config": {"workload": WORKLOAD, "particles_per_gpu": n, "precision": "FP32 pair sums (Kahan), FP64 "
                        "positions and reductions", "parallelism": "replicas" if world > 1 else "single GPU",
                        "timed_steps": "steps %d-%d of the run" % (step0, step0 + args.steps - 1),
-                       "density_pass": names["density"],
+                       "density_pass": names["density"], "x_subcells": int(sim.params.x_subcells),
                        "l2": "inputs larger than L2 (%.0f MB state per GPU)" % (sph.sph_query_workspace(
                            sph.params_from_case(case, 32), n) / 1e6)},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
@@ -805,6 +805,8 @@ def main():
     ap.add_argument("--pair-tiles", type=int, default=0, choices=(0, 1, 2, 3),
                     help="density pass of the headline: 0 row walk (default), 1 tile walk, 2 cooperative tile "
                          "walk, 3 flattened tile walk")
+    ap.add_argument("--x-subcells", type=int, default=4, choices=(1, 2, 4),
+                    help="sub-cells per cell along x of the sort, where the row walk cuts its runs (default 4)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

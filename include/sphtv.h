@@ -143,7 +143,13 @@ typedef struct sph_params {
                                and walks that tile, one thread per particle (the same results as
                                0 bit for bit); 2 walks the tile with groups of lanes sharing each
                                particle's candidates (the same neighbour lists, sigma summed in
-                               another order).  Ignored otherwise */
+                               another order); 3 walks the tile with each thread's cell rows taken
+                               as one sequence (the same results as 0 bit for bit).  The tiles
+                               hold whole cells: with x_subcells > 1, 1 and 3 visit the row walk's
+                               pairs in its order plus the candidates of the sub-cells that its
+                               cut drops, whose zero terms enter the compensated sums, so their
+                               results equal 0's bit for bit only with x_subcells = 1.  Ignored
+                               otherwise */
     int32_t body_force;     /* 1: the force pass also sums the force of the fluid on the wall
                                particles (the body force of Eq. 18, e.g. the cylinder of
                                Sec. 4.4), reported in sph_diag.body_force; 0 (default): not */
@@ -157,6 +163,15 @@ typedef struct sph_params {
                                Kick-drift-kick only (SPH_ERR_ARG with SPH_INT_DUAL) */
     double fringe_u[3];     /* free-stream velocity U_inf */
     double fringe_x[4];     /* x0, x1, rise > 0, fall > 0 of the fringe region */
+    int32_t x_subcells;     /* 1, 2 or 4 (default 4; 0 means 1): the counting sort refines each
+                               cell along axis 0 into this many sub-cells (particles ordered by
+                               sub-cell, then by id, within their cell), and the row walks of the
+                               density passes cut each row's x extent at sub-cell instead of cell
+                               granularity: fewer candidate tests for the same neighbours in the
+                               same order (only the order of particles within a cell changes, and
+                               with it the rounding of the sums).  Reduced to 2, then 1, where the
+                               cells times the sub-cells would exceed 2^30.  SPH_ERR_ARG for other
+                               values */
 } sph_params;
 
 /* FP64 diagnostics of the fluid particles after a step (or after
@@ -189,6 +204,7 @@ typedef struct sph_ctx sph_ctx;
 /* Fill *p with the paper's constants: riemann_eta 3, tv_xi -0.2, tv_C 1e3,
  * tv_thresh 5e-4, cfl_ad 0.25, cfl_ac 0.6, tv_mode limited, tv_h h_min,
  * h_pair mean, kahan on, graphs on, pair_tiles 0, body_force off, no fringe forcing,
+ * x_subcells 4,
  * precision 64, dim 2, rho0 1.  Returns
  * SPH_ERR_ARG on NULL. */
 SPH_API sph_status sph_default_params(sph_params* p);

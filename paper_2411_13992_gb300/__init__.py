@@ -64,6 +64,7 @@ class SphParams(ctypes.Structure):
         ("adjoint_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("graphs", ctypes.c_int32),
         ("pair_tiles", ctypes.c_int32), ("body_force", ctypes.c_int32),
         ("fringe_lambda", ctypes.c_double), ("fringe_u", ctypes.c_double * 3), ("fringe_x", ctypes.c_double * 4),
+        ("x_subcells", ctypes.c_int32),
     ]
 
 

@@ -57,6 +57,14 @@ struct Grid {
     float edgef[3];
     int ncell;
     int sms;            // streaming multiprocessors of the device (grid sizing of the pair passes)
+    // The counting sort may refine each cell along axis 0 into 2^sub_shift
+    // sub-cells (sorted by sub-cell, then by id, inside the cell): sub_start
+    // [(ncell << sub_shift) + 1] holds the first particle of each sub-cell
+    // in the sort order, so that a row walk can cut its runs at sub-cell
+    // rather than cell granularity.  inv_edge_sub0 = inv_edge[0] 2^sub_shift.
+    int sub_shift;
+    double inv_edge_sub0;
+    const int32_t* sub_start;
 };
 
 // Constants of the method for one precision.
@@ -236,6 +244,24 @@ __device__ __forceinline__ int cell_index(const Grid& G, const double* xs)
     int c1 = cell_coord(G, xs[1], 1);
     int c2 = DIM == 3 ? cell_coord(G, xs[2], 2) : 0;
     return c0 + G.nc[0] * (c1 + G.nc[1] * c2);
+}
+
+// The sort key of a position: the cell index when sub_shift = 0; else the
+// sub-cell index ((cell << sub_shift) | sub-cell along axis 0), whose high
+// bits are cell_index's: the sub-cell coordinate is the truncation of
+// (x - lo) inv_edge 2^s, and the scaling by 2^s is exact, so shifting the
+// coordinate right by s gives the truncation of (x - lo) inv_edge (the
+// clamps to the last cell and sub-cell commute with the shift as well).
+template <int DIM>
+__device__ __forceinline__ int sort_key(const Grid& G, const double* xs)
+{
+    if (G.sub_shift == 0) return cell_index<DIM>(G, xs);
+    const int nsx = G.nc[0] << G.sub_shift;
+    const double t = (__double_as_longlong(G.lo[0]) << 1) == 0 ? xs[0] : __dsub_rn(xs[0], G.lo[0]);
+    const int s0 = min(max(trunc_nonneg(t * G.inv_edge_sub0), 0), nsx - 1);
+    const int c1 = cell_coord(G, xs[1], 1);
+    const int c2 = DIM == 3 ? cell_coord(G, xs[2], 2) : 0;
+    return s0 + nsx * (c1 + G.nc[1] * c2);
 }
 
 __device__ __forceinline__ void cell_decode(const Grid& G, int key, int* c)

@@ -121,7 +121,7 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
         else if (!G.periodic[d] && (dkey(xs[d]) < dkey(G.lo[d]) || dkey(xs[d]) > dkey(G.hi[d]))) e |= ERRB_DOMAIN;
     }
     if (e) atomicOr(err, e);
-    int k = cell_index<DIM>(G, xs);
+    int k = sort_key<DIM>(G, xs);
     key[i] = k;
     // Lanes of a warp are neighbours in the cell order and mostly share a
     // cell: one atomic per distinct cell in the warp.
@@ -235,15 +235,22 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t*
     perm[pos] = i;
 }
 
-// One thread per cell: place the cell's particles in increasing caller id
-// (ids are unique, so the rank of each is its slot).  Cells hold about two
-// particles (edge >= h_max), so the quadratic rank count is short.
-__global__ void k_order_cells(int ncell, const int32_t* __restrict__ start, const int32_t* __restrict__ perm_in,
-                              const int32_t* __restrict__ id, int32_t* __restrict__ perm_out)
+// One thread per sort bin (cell, or sub-cell when the sort refines the
+// cells): place the bin's particles in increasing caller id (ids are
+// unique, so the rank of each is its slot).  Cells hold about two particles
+// (edge >= h_max), so the quadratic rank count is short.  With sub-cells
+// (shift > 0) the thread of each cell's first sub-cell also writes the
+// cell's start (the thread nbin, past the last bin, the end n).
+__global__ void k_order_cells(int nbin, const int32_t* __restrict__ start, const int32_t* __restrict__ perm_in,
+                              const int32_t* __restrict__ id, int32_t* __restrict__ perm_out, int shift,
+                              int32_t* __restrict__ cell_start)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int s = start[c], e = start[c + 1];
+    if (c > nbin) return;
+    const int s = start[c];
+    if (shift && (c & ((1 << shift) - 1)) == 0) cell_start[c >> shift] = s;
+    if (c == nbin) return;
+    const int e = start[c + 1];
     for (int k = s; k < e; ++k) {
         const int p = perm_in[k];
         const int myid = id[p];
@@ -290,7 +297,7 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
     dst.id[k] = src.id[i];
     dst.kind[k] = src.kind[i];
     if (F32POS) {
-        int kk = key[i];
+        int kk = key[i] >> G.sub_shift;   // the cell of the sort key
         int c[3];
         cell_decode(G, kk, c);
         float o[3] = {0.f, 0.f, 0.f};
@@ -326,13 +333,13 @@ cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_order(int n, int ncell, const int32_t* key, const int32_t* start, int32_t* cursor,
-                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, cudaStream_t st,
-                                 int64_t* launches)
+cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int32_t* start, int32_t* cursor,
+                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, int shift, int32_t* cell_start,
+                                 cudaStream_t st, int64_t* launches)
 {
     const int T = 256;
     k_scatter<<<nblk(n, T), T, 0, st>>>(n, key, start, cursor, perm_tmp);
-    k_order_cells<<<nblk(ncell, T), T, 0, st>>>(ncell, start, perm_tmp, id, perm);
+    k_order_cells<<<nblk(nbin + 1, T), T, 0, st>>>(nbin, start, perm_tmp, id, perm, shift, cell_start);
     *launches += 2;
     return cudaGetLastError();
 }

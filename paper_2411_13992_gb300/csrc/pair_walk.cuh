@@ -72,7 +72,13 @@ __device__ __forceinline__ void for_candidates(const float* oi, int cell_i, cons
 // row is cut to the cells within the remaining half-chord; every margin is
 // 1e-3 of a cell edge, far above FP32 rounding, so every candidate that the
 // full stencil would accept is still visited, in the same order.  About 2/3
-// of the 5^3 cells remain in 3-D.  CELL_IN_W: the cell index of each
+// of the 5^3 cells remain in 3-D.  When the sort refines the cells along x
+// into 2^s sub-cells (G.sub_shift = s), the x extent is cut at sub-cell
+// granularity (the runs' bounds from G.sub_start; the same floor at 2^s
+// times the resolution, whose coarsening is the cell cut): a row run then
+// starts and ends within a sub-cell of the half-chord's ends.  The runs are
+// still contiguous in the sort order, and the accepted candidates and their
+// order are those of the cell cut.  CELL_IN_W: the cell index of each
 // candidate is read from the bits of pos4.w (the copy with the cell index
 // that the permute writes at uniform resolution) instead of a separate load
 // from cell_of.
@@ -89,6 +95,12 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
     const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
     const float inv_ex = 1.f / ex;
     const float reach2 = reach * reach;
+    // the x cut in sub-cells (s = 0: cells): nsx along a row, the stencil's
+    // sub-cells -R 2^s .. (R + 1) 2^s - 1 around the first of cell c[0]
+    const int sh = G.sub_shift;
+    const int32_t* __restrict__ rstart = sh ? G.sub_start : start;
+    const int nsx = ncx << sh;
+    const float inv_exs = inv_ex * (float)(1 << sh);   // exact: a power of two
     for (int dz = -zr; dz <= zr; ++dz) {
         int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
         if (cz < 0) continue;
@@ -108,34 +120,35 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
             const float w2 = wz2 - ry * ry;
             if (w2 <= 0.f) continue;
             const float w = sqrtf(w2) + 1e-3f * ex;
-            const int dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
-            const int dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
-            if (dxlo > dxhi) continue;
-            // runs along x: first cell (x index), number of cells, x step of the
-            // first cell; a periodic window (at most 5 <= ncx cells) wraps once at most
+            const int slo = max(__float2int_rd((oi[0] - w) * inv_exs), -(R << sh));
+            const int shi = min(__float2int_rd((oi[0] + w) * inv_exs), ((R + 1) << sh) - 1);
+            if (slo > shi) continue;
+            // runs along x: first sub-cell (x index along the row), number of
+            // sub-cells, x step of the cell of the first sub-cell (>> is a floor
+            // division); a periodic window (at most 5 <= ncx cells) wraps once at most
             int rc0[2], rn[2], rdx[2], nrun;
-            const int a = c[0] + dxlo, b = c[0] + dxhi;
+            const int a = (c[0] << sh) + slo, b = (c[0] << sh) + shi;
             if (!G.periodic[0]) {
-                const int a0 = max(a, 0), b0 = min(b, ncx - 1);
-                rc0[0] = a0; rn[0] = b0 - a0 + 1; rdx[0] = a0 - c[0]; nrun = rn[0] > 0 ? 1 : 0;
-            } else if (a >= 0 && b < ncx) {
-                rc0[0] = a; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+                const int a0 = max(a, 0), b0 = min(b, nsx - 1);
+                rc0[0] = a0; rn[0] = b0 - a0 + 1; rdx[0] = (a0 >> sh) - c[0]; nrun = rn[0] > 0 ? 1 : 0;
+            } else if (a >= 0 && b < nsx) {
+                rc0[0] = a; rn[0] = b - a + 1; rdx[0] = slo >> sh; nrun = 1;
             } else if (a < 0) {
-                rc0[0] = ncx + a; rn[0] = min(-a, b - a + 1); rdx[0] = dxlo;
+                rc0[0] = nsx + a; rn[0] = min(-a, b - a + 1); rdx[0] = slo >> sh;
                 rc0[1] = 0; rn[1] = b + 1; rdx[1] = -c[0]; nrun = b >= 0 ? 2 : 1;
-            } else if (a >= ncx) {
-                rc0[0] = a - ncx; rn[0] = b - a + 1; rdx[0] = dxlo; nrun = 1;
+            } else if (a >= nsx) {
+                rc0[0] = a - nsx; rn[0] = b - a + 1; rdx[0] = slo >> sh; nrun = 1;
             } else {
-                rc0[0] = a; rn[0] = ncx - a; rdx[0] = dxlo;
-                rc0[1] = 0; rn[1] = b - ncx + 1; rdx[1] = ncx - c[0]; nrun = 2;
+                rc0[0] = a; rn[0] = nsx - a; rdx[0] = slo >> sh;
+                rc0[1] = 0; rn[1] = b - nsx + 1; rdx[1] = ncx - c[0]; nrun = 2;
             }
             const float shy = -(float)dy * ey;
             const int row = ncx * (cy + G.nc[1] * cz);
             const uint32_t code_row = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
             for (int r = 0; r < nrun; ++r) {
-                const int cell = row + rc0[r];
-                const int kr = cell - rdx[r];      // dx of candidate j = cell_of[j] - kr
-                const int jend = start[cell + rn[r]];
+                const int bin = (row << sh) + rc0[r];
+                const int kr = row + (rc0[r] >> sh) - rdx[r];   // dx of candidate j = cell_of[j] - kr
+                const int jend = rstart[bin + rn[r]];
                 auto one = [&](int j, const float4& pj, int dx) {
                     const float shx = -(float)dx * ex;
                     // x and y in packed FP32x2 arithmetic (o_i - o_j as fma(o_j, -1, o_i): one rounding)
@@ -154,7 +167,7 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
                 auto cell_at = [&](int j, const float4& pj) {
                     return CELL_IN_W ? __float_as_int(pj.w) : cell_of[j];
                 };
-                int j = start[cell];
+                int j = rstart[bin];
                 for (; TWO && j + 1 < jend; j += 2) {
                     const float4 p0 = pos4[j], p1 = pos4[j + 1];
                     const int d0 = cell_at(j, p0) - kr, d1 = cell_at(j + 1, p1) - kr;

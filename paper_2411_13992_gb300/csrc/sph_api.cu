@@ -52,6 +52,7 @@ struct sph_ctx {
     SetPtrs set[2];
     int cur;
     int32_t *key, *perm_tmp, *perm, *count, *cursor, *start, *scan_tmp;
+    int32_t* sub_start;  // the sort's sub-cell starts (x_subcells > 1), else null
     void* vr;
     float4* pos4;
     float4* pos4c;      // FP32 form, uniform h: pos4 with the cell index bits in w
@@ -140,6 +141,7 @@ sph_status check_params(const sph_params* p, int64_t n)
     if (p->integrator != SPH_INT_KDK && p->integrator != SPH_INT_DUAL) return SPH_ERR_ARG;
     if (p->graphs != 0 && p->graphs != 1) return SPH_ERR_ARG;
     if (p->pair_tiles < 0 || p->pair_tiles > 3) return SPH_ERR_ARG;
+    if (p->x_subcells != 0 && p->x_subcells != 1 && p->x_subcells != 2 && p->x_subcells != 4) return SPH_ERR_ARG;
     if (p->body_force != 0 && p->body_force != 1) return SPH_ERR_ARG;
     if (!(p->fringe_lambda >= 0.0) || !std::isfinite(p->fringe_lambda)) return SPH_ERR_ARG;
     if (p->fringe_lambda > 0.0) {
@@ -180,6 +182,15 @@ int device_sms()
     return v;
 }
 
+// log2 of the sub-cells per cell of the sort: the requested count (1, 2 or
+// 4), reduced while the cells times the sub-cells exceed the bin bound.
+int sub_shift_for(int64_t ncell, int x_subcells)
+{
+    int s = x_subcells == 4 ? 2 : (x_subcells == 2 ? 1 : 0);
+    while (s > 0 && (ncell << s) > kMaxCells) --s;
+    return s;
+}
+
 Grid make_grid(const sph_params* p)
 {
     Grid G;
@@ -212,6 +223,22 @@ Grid make_grid(const sph_params* p)
     }
     G.ncell = (int)ncell;
     G.sms = device_sms();
+    G.sub_shift = sub_shift_for(ncell, p->x_subcells);
+    G.inv_edge_sub0 = G.inv_edge[0] * (double)(1 << G.sub_shift);
+    G.sub_start = nullptr;   // set when the workspace is laid out
+    return G;
+}
+
+// Sort bins: the cells, or their sub-cells along x.
+static inline size_t sort_bins(const Grid& G) { return (size_t)G.ncell << G.sub_shift; }
+
+// The grid without the sub-cell refinement (for walks over stored cell
+// starts, such as the adjoint's tape).
+static inline Grid cells_only(Grid G)
+{
+    G.sub_shift = 0;
+    G.inv_edge_sub0 = G.inv_edge[0];
+    G.sub_start = nullptr;
     return G;
 }
 
@@ -281,10 +308,13 @@ size_t carve(sph_ctx* c, char* base)
     c->key = W.take<int32_t>(n);
     c->perm_tmp = W.take<int32_t>(n);
     c->perm = W.take<int32_t>(n);
-    c->count = W.take<int32_t>(nc1);
-    c->cursor = W.take<int32_t>(nc1);
+    const size_t nb1 = sort_bins(c->G) + 1;
+    c->count = W.take<int32_t>(nb1);
+    c->cursor = W.take<int32_t>(nb1);
     c->start = W.take<int32_t>(nc1);
-    c->scan_tmp = W.take<int32_t>(scan_temp_elems((int)nc1));
+    c->sub_start = c->G.sub_shift ? W.take<int32_t>(nb1) : nullptr;
+    c->G.sub_start = c->sub_start;
+    c->scan_tmp = W.take<int32_t>(scan_temp_elems((int)nb1));
     c->vr = W.take<char>(n * 4 * rs);
     c->pos4 = W.take<float4>(n);     // both forms: FP32 cell-relative positions for the candidate walks
     c->pos4c = c->prec == 32 && c->P.h_min == c->P.h_max ? W.take<float4>(n) : nullptr;
@@ -375,20 +405,22 @@ inline cudaError_t prof_mark(sph_ctx* c, int cls, int end)
 sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
 {
     const int n = (int)c->n;
-    const size_t nc1 = (size_t)c->G.ncell + 1;
+    const size_t nb1 = sort_bins(c->G) + 1;
+    // the bins' starts: the sub-cells' (the cells' then follow from them) or the cells'
+    int32_t* bin_start = c->G.sub_shift ? c->sub_start : c->start;
     SPH_MARK(SPH_K_KICKDRIFT, 0);
-    SPH_CU(cudaMemsetAsync(c->count, 0, nc1 * sizeof(int32_t), c->st));
-    SPH_CU(cudaMemsetAsync(c->cursor, 0, nc1 * sizeof(int32_t), c->st));
+    SPH_CU(cudaMemsetAsync(c->count, 0, nb1 * sizeof(int32_t), c->st));
+    SPH_CU(cudaMemsetAsync(c->cursor, 0, nb1 * sizeof(int32_t), c->st));
     SPH_CU(launch_kick_drift_key(c->prec, c->dim, n, cur_set(c), c->dt, drift, c->G, c->key, c->count, c->err, c->st));
     ++c->launches;
     SPH_MARK(SPH_K_KICKDRIFT, 1);
     SPH_MARK(SPH_K_SCAN, 0);
-    SPH_CU(launch_exclusive_scan(c->count, c->start, (int)nc1, c->scan_tmp, c->st, &c->launches));
+    SPH_CU(launch_exclusive_scan(c->count, bin_start, (int)nb1, c->scan_tmp, c->st, &c->launches));
     SPH_MARK(SPH_K_SCAN, 1);
     const int32_t* id = c->prec == 64 ? c->set[c->cur].d.id : c->set[c->cur].f.id;
     SPH_MARK(SPH_K_ORDER, 0);
-    SPH_CU(launch_scatter_order(n, c->G.ncell, c->key, c->start, c->cursor, c->perm_tmp, id, c->perm, c->st,
-                                &c->launches));
+    SPH_CU(launch_scatter_order(n, (int)sort_bins(c->G), c->key, bin_start, c->cursor, c->perm_tmp, id, c->perm,
+                                c->G.sub_shift, c->start, c->st, &c->launches));
     SPH_MARK(SPH_K_ORDER, 1);
     SPH_MARK(SPH_K_PERMUTE, 0);
     SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
@@ -722,7 +754,8 @@ sph_status adjoint_segment(sph_ctx* c, int nsteps)
     AdjView& A = c->adj;
     SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
     for (int t = nsteps - 1; t >= 0; --t) {
-        SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), c->G, consts(c), A, 1, c->st));
+        SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), cells_only(c->G), consts(c), A, 1,
+                                      c->st));
         c->launches += 4;
     }
     return SPH_OK;
@@ -781,6 +814,7 @@ sph_status sph_default_params(sph_params* p)
     p->kahan = 1;
     p->graphs = 1;
     p->pair_tiles = 0;
+    p->x_subcells = 4;
     return SPH_OK;
 }
 
@@ -1260,7 +1294,8 @@ sph_status sph_force_pass_adjoint(sph_ctx* c, const double* x, const double* v, 
     SPH_TRY(cot_in(c, vbar, A.vc));
     SPH_TRY(cot_in(c, abar, A.ac));
     SPH_TRY(cot_in(c, drbar, A.drc));
-    SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[0]), c->G, consts(c), A, 0, c->st));
+    SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[0]), cells_only(c->G), consts(c), A, 0,
+                              c->st));
     c->launches += 4;
     SPH_TRY(cot_out(c, A.xc, xbar));
     SPH_TRY(cot_out(c, A.vc, vbar));
@@ -1341,7 +1376,8 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     if (s != SPH_OK) return s;
     if (p->precision != 64 || !x || !h || !m || !rho) return SPH_ERR_ARG;
     if (n > SPH_NOALLOC_MAX_PARTICLES) return SPH_ERR_WORKSPACE;
-    const Grid G = make_grid(p);
+    // the cell sort of this view does not refine the cells into sub-cells
+    const Grid G = cells_only(make_grid(p));
     if (G.ncell > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_WORKSPACE;
     void* base = nullptr;
     s = noalloc_scratch((cudaStream_t)stream, &base);

@@ -82,7 +82,7 @@ def test_workspace_query_and_argument_checks(lib):
         dict(h_max=0.5 * c["h_min"]), dict(tv_mode=4), dict(fixed_dt=-1.0), dict(adjoint_steps=-1),
         dict(h_max=0.3),          # fewer than 5 cells along a periodic axis
         dict(integrator=2), dict(integrator=1, fixed_dt=1e-3), dict(integrator=1, adjoint_steps=4), dict(graphs=2),
-        dict(pair_tiles=4), dict(pair_tiles=-1),
+        dict(pair_tiles=4), dict(pair_tiles=-1), dict(x_subcells=3), dict(x_subcells=8), dict(x_subcells=-1),
     ]
     for kw in bad:
         q = sph.params_from_case(c, 64)
@@ -93,6 +93,36 @@ def test_workspace_query_and_argument_checks(lib):
         assert e.value.status == 1, kw
     with pytest.raises(sph.SphError):
         sph.sph_query_workspace(p, 0)
+
+
+def test_sub_cells_of_the_sort(lib):
+    """x_subcells 0/1 (no refinement), 2 and 4 are accepted (default 4); the
+    sort's count, cursor and sub-cell start arrays grow with the bins; where
+    the cells times the sub-cells would exceed 2^30 the sort refines less."""
+    c = cases.tgv3d(16)
+    assert sph.sph_default_params().x_subcells == 4
+    sizes = {}
+    for xs in (0, 1, 2, 4):
+        q = sph.params_from_case(c, 32, x_subcells=xs)
+        sizes[xs] = sph.sph_query_workspace(q, c["n"])
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[4]
+    # 2^20 x 2^10 cells: at the bound, so no sub-cells whatever is asked;
+    # 2^20 x 2^9: two sub-cells when four are asked
+    q = sph.params_from_case(c, 32, x_subcells=1)
+    q.dim, q.h_max, q.h_min = 2, 0.5, 0.5
+    q.L[0], q.L[1] = float(1 << 19), float(1 << 9)      # floor(L / h_max) cells per axis
+    q.periodic[0] = q.periodic[1] = 0
+    at = {}
+    for xs in (1, 2, 4):
+        q.x_subcells = xs
+        at[xs] = sph.sph_query_workspace(q, 1000)
+    assert at[1] == at[2] == at[4]
+    q.L[1] = float(1 << 8)
+    half = {}
+    for xs in (1, 2, 4):
+        q.x_subcells = xs
+        half[xs] = sph.sph_query_workspace(q, 1000)
+    assert half[1] < half[2] == half[4]
 
 
 def test_create_rejects_bad_workspace_without_touching_it(lib):

@@ -3,7 +3,10 @@ row walk over global memory (sph_params.pair_tiles = 0).  pair_tiles = 1,
 one thread per particle over the tile, visits the same candidates in the
 same order with the same arithmetic, so every state field after several
 steps is bit for bit the same; so does pair_tiles = 3, the same walk with
-each lane's rows taken as one sequence.  pair_tiles = 2, groups of lanes sharing a
+each lane's rows taken as one sequence.  (Both hold whole cells: bit for
+bit with a sort that does not refine the cells, x_subcells = 1; with the
+default sub-cells the row walk cuts its runs finer, so the tiles add more
+zero terms to the compensated sums and agree to FP32 rounding.)  pair_tiles = 2, groups of lanes sharing a
 particle's candidates, writes the same neighbour lists but sums sigma in
 another order: its densities agree to FP32 rounding, and it is checked
 against the FP64 oracle like the other FP32 paths.  Cases: partial edge
@@ -65,18 +68,31 @@ CASES = {
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_tiled_walk_is_bit_identical_to_the_row_walk(name, mode):
     c = CASES[name]()
-    got, d_got = _run(c, mode, 5)
-    ref, d_ref = _run(c, 0, 5)
+    got, d_got = _run(c, mode, 5, x_subcells=1)
+    ref, d_ref = _run(c, 0, 5, x_subcells=1)
     for k in FIELDS:
         assert np.array_equal(got[k], ref[k]), (name, k)
     assert d_got["ke"] == d_ref["ke"]
 
 
 @pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("name", ["tgv3d_24_partial_blocks", "tgv3d_7_five_cells_per_axis", "cavity2d_48_walls"])
+def test_tiled_walk_matches_the_sub_cell_row_walk(name, mode):
+    """With the default sub-cell sort the tiles walk whole cells and the row
+    walk sub-cells: the same pairs, densities within FP32 rounding."""
+    c = CASES[name]()
+    fl = c["kind"] == 0
+    got, _ = _run(c, mode, 0)
+    ref, _ = _run(c, 0, 0)
+    d_rho = np.abs(got["rho"][fl] - ref["rho"][fl]).max() / np.abs(ref["rho"][fl]).max()
+    assert d_rho <= 2e-7, (name, d_rho)
+
+
+@pytest.mark.parametrize("mode", [1, 3])
 def test_tiled_density_is_bit_identical_in_the_dual_criteria_integrator(mode):
     c = cases.tgv3d(20)
-    got, d_got = _run(c, mode, 3, integrator=sph.INT_DUAL)
-    ref, d_ref = _run(c, 0, 3, integrator=sph.INT_DUAL)
+    got, d_got = _run(c, mode, 3, integrator=sph.INT_DUAL, x_subcells=1)
+    ref, d_ref = _run(c, 0, 3, integrator=sph.INT_DUAL, x_subcells=1)
     for k in ("x", "v", "rho"):
         assert np.array_equal(got[k], ref[k]), k
     assert d_got["substeps"] == d_ref["substeps"]
