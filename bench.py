@@ -47,13 +47,14 @@ FLOPS_PER_PAIR_FP32 = 111
 # Algorithmic cost of the density pass (k_density32, FP32 form) per
 # interacting pair, self included: pair vector and r^2 11, sqrt 1,
 # W = a_D h^-D t^4 (2q + 1) with q = r/h, t = 1 - q/2: 9, Kahan 4     -> 25.
-# The candidate tests of the cell scan (about 184 per particle in 3-D, for
+# The candidate tests of the cell scan (about 146 per particle in 3-D, for
 # 81 pairs) are implementation overhead and are not counted.
 FLOPS_PER_PAIR_DENSITY32 = 25
 # For context only (not algorithmic): the clipped 5^3-cell walk of the density
-# pass tests about 184 candidates per particle on this lattice (81 accepted,
-# self included), 8 flops each (pair vector and r^2 against the support).
-CANDIDATES_PER_PARTICLE = 184
+# pass, its rows cut at quarter-cell sub-cells, tests about 146 candidates per
+# particle on this lattice (81 accepted, self included; 184 with the rows cut
+# at whole cells), 8 flops each (pair vector and r^2 against the support).
+CANDIDATES_PER_PARTICLE = {1: 184, 2: 161, 4: 146}     # by sph_params.x_subcells
 FLOPS_PER_CANDIDATE = 8
 # Algorithmic bytes of k_density32 per particle: read the float4 position,
 # v (12 B), kind (1 B), sigma0 (8 B), cell index (4 B); write the float4
@@ -325,8 +326,9 @@ def _rooflines(case, prof, peak_tflops, hbm_gbs, peak_note, kernel_names):
     d_s = roof_d["avg_launch_ms"] * 1e-3
     roof_d["with_candidate_tests"] = {
         "tflops": (pairs + n) * FLOPS_PER_PAIR_DENSITY32 / d_s / 1e12
-        + n * CANDIDATES_PER_PARTICLE * FLOPS_PER_CANDIDATE / d_s / 1e12,
-        "candidates_per_particle": CANDIDATES_PER_PARTICLE, "flops_per_candidate": FLOPS_PER_CANDIDATE,
+        + n * CANDIDATES_PER_PARTICLE[_RUN["x_subcells"]] * FLOPS_PER_CANDIDATE / d_s / 1e12,
+        "candidates_per_particle": CANDIDATES_PER_PARTICLE[_RUN["x_subcells"]],
+        "flops_per_candidate": FLOPS_PER_CANDIDATE,
         "note": "implementation rate: the neighbour search's candidate tests added to the algorithmic flops; "
                 "not the roofline figure"}
     # what binds each kernel, from the ncu counters of the committed summary
@@ -375,6 +377,7 @@ def run_native(args):
 
     # ---- FP32 form: the headline number.  The timed region holds the K steps
     # only: no per-kernel events inside it (the breakdown is a separate pass).
+    _RUN["x_subcells"] = args.x_subcells
     sim = sph.Simulation(case, precision=32, pair_tiles=args.pair_tiles, x_subcells=args.x_subcells)
     sim.set_state()
     sim.build_cells()
@@ -638,12 +641,17 @@ def _pairs_per_launch(case) -> int:
 COUNTERS = os.path.join(ROOT, "profiles", "pair_counters.json")
 
 
+# settings of this run that the committed ncu counters depend on
+_RUN = {"x_subcells": 4}
+
+
 def _profiled_counters(kernel: str, what: str):
     """ncu counters of a pair kernel ("density", "forces" or "forces_f64")
     from the committed summary: what = "binding" (issue activity, lanes per
     warp instruction, pipe and DRAM utilisation) or "dram_bytes_per_particle".
-    None when the summary is absent or the kernel sources have changed since
-    the counters were taken (it records a SHA-1 of the sources)."""
+    None when the summary is absent, the kernel sources have changed since
+    the counters were taken (it records a SHA-1 of the sources) or this run
+    sorts with other sub-cells than the captured one."""
     import hashlib
     try:
         with open(COUNTERS) as f:
@@ -652,7 +660,7 @@ def _profiled_counters(kernel: str, what: str):
         for rel in d["sources"]:
             with open(os.path.join(ROOT, rel), "rb") as f:
                 h.update(f.read())
-        if h.hexdigest() != d["source_sha1"]:
+        if h.hexdigest() != d["source_sha1"] or d.get("x_subcells") != _RUN["x_subcells"]:
             return None
         return d["kernels"][kernel][what]
     except (OSError, ValueError, KeyError):

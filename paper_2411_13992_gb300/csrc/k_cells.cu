@@ -214,43 +214,77 @@ cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_
     return cudaGetLastError();
 }
 
+// The sort's scan without its last pass: prefix[k] = the exclusive sum of
+// count[0, k) within k's tile of kScanTile bins, tile_off[b] (tmp) the sum of
+// the tiles before tile b.  The start of bin k is prefix[k] +
+// tile_off[k / kScanTile]; the scatter and the per-bin ordering add the tile
+// offset as they read a start (one pass over the bins fewer).  Returns
+// tile_off, or null for a single tile.
+cudaError_t launch_scan_tiles(const int32_t* count, int32_t* prefix, int n, int32_t* tmp, cudaStream_t st,
+                              int64_t* launches, const int32_t** tile_off)
+{
+    int nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_tile<<<nb, kScanThreads, 0, st>>>(count, prefix, tmp, n);
+    ++*launches;
+    *tile_off = nullptr;
+    if (nb > 1) {
+        cudaError_t e = launch_exclusive_scan(tmp, tmp, nb, tmp + nb + 1, st, launches);
+        if (e != cudaSuccess) return e;
+        *tile_off = tmp;
+    }
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ int bin_start_of(const int32_t* __restrict__ prefix, const int32_t* __restrict__ tile_off,
+                                            int k)
+{
+    return prefix[k] + (tile_off ? tile_off[k / kScanTile] : 0);
+}
+
 // ------------------------------------------------ scatter and cell order
 
-__global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
-                          int32_t* __restrict__ cursor, int32_t* __restrict__ perm)
+// Slots by warp-aggregated atomics on the bins' counts, counting down: a bin
+// of c particles hands out c - 1 .. 0, so every count is back at zero after
+// the scatter (the next sort needs no clearing).  The order inside a bin is
+// fixed afterwards by k_order_cells.
+__global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t* __restrict__ prefix,
+                          const int32_t* __restrict__ tile_off, int32_t* __restrict__ count,
+                          int32_t* __restrict__ perm)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = key[i];
-    // warp-aggregated slot reservation (the order inside a cell is fixed
-    // afterwards by k_order_cells)
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, k);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
+    const int np = __popc(peers);
     int base = 0;
-    if (lane == leader) base = atomicAdd(&cursor[k], __popc(peers));
+    if (lane == leader) base = atomicSub(&count[k], np) - np;
     base = __shfl_sync(act, base, leader);
-    const int pos = start[k] + base + __popc(peers & ((1u << lane) - 1u));
+    const int pos = bin_start_of(prefix, tile_off, k) + base + __popc(peers & ((1u << lane) - 1u));
     perm[pos] = i;
 }
 
 // One thread per sort bin (cell, or sub-cell when the sort refines the
-// cells): place the bin's particles in increasing caller id (ids are
-// unique, so the rank of each is its slot).  Cells hold about two particles
-// (edge >= h_max), so the quadratic rank count is short.  With sub-cells
-// (shift > 0) the thread of each cell's first sub-cell also writes the
-// cell's start (the thread nbin, past the last bin, the end n).
-__global__ void k_order_cells(int nbin, const int32_t* __restrict__ start, const int32_t* __restrict__ perm_in,
-                              const int32_t* __restrict__ id, int32_t* __restrict__ perm_out, int shift,
+// cells): write the bin's start, and place the bin's particles in
+// increasing caller id (ids are unique, so the rank of each is its slot).
+// Cells hold about two particles (edge >= h_max), so the quadratic rank
+// count is short.  With sub-cells (shift > 0) the thread of each cell's
+// first sub-cell also writes the cell's start (the thread nbin, past the
+// last bin, the end n).
+__global__ void k_order_cells(int nbin, const int32_t* __restrict__ prefix, const int32_t* __restrict__ tile_off,
+                              const int32_t* __restrict__ perm_in, const int32_t* __restrict__ id,
+                              int32_t* __restrict__ perm_out, int32_t* __restrict__ start, int shift,
                               int32_t* __restrict__ cell_start)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > nbin) return;
-    const int s = start[c];
+    const int s = bin_start_of(prefix, tile_off, c);
+    start[c] = s;
     if (shift && (c & ((1 << shift) - 1)) == 0) cell_start[c >> shift] = s;
     if (c == nbin) return;
-    const int e = start[c + 1];
+    const int e = bin_start_of(prefix, tile_off, c + 1);
     for (int k = s; k < e; ++k) {
         const int p = perm_in[k];
         const int myid = id[p];
@@ -333,13 +367,14 @@ cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int32_t* start, int32_t* cursor,
-                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, int shift, int32_t* cell_start,
-                                 cudaStream_t st, int64_t* launches)
+cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int32_t* prefix, const int32_t* tile_off,
+                                 int32_t* count, int32_t* perm_tmp, const int32_t* id, int32_t* perm, int32_t* start,
+                                 int shift, int32_t* cell_start, cudaStream_t st, int64_t* launches)
 {
     const int T = 256;
-    k_scatter<<<nblk(n, T), T, 0, st>>>(n, key, start, cursor, perm_tmp);
-    k_order_cells<<<nblk(nbin + 1, T), T, 0, st>>>(nbin, start, perm_tmp, id, perm, shift, cell_start);
+    k_scatter<<<nblk(n, T), T, 0, st>>>(n, key, prefix, tile_off, count, perm_tmp);
+    k_order_cells<<<nblk(nbin + 1, T), T, 0, st>>>(nbin, prefix, tile_off, perm_tmp, id, perm, start, shift,
+                                                   cell_start);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -41,11 +41,17 @@ cudaError_t launch_kick_drift_key(int prec, int dim, int n, void* S, const doubl
 size_t scan_temp_elems(int n);
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* tmp, cudaStream_t st,
                                   int64_t* launches);
-// nbin sort bins (cells, or sub-cells when shift > 0, start[nbin + 1] their
-// starts); with shift > 0 also writes the cells' starts into cell_start.
-cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int32_t* start, int32_t* cursor,
-                                 int32_t* perm_tmp, const int32_t* id, int32_t* perm, int shift, int32_t* cell_start,
-                                 cudaStream_t st, int64_t* launches);
+// The sort's scan without its last pass (see k_cells.cu): prefix within
+// tiles, *tile_off the tiles' offsets (null for one tile).
+cudaError_t launch_scan_tiles(const int32_t* count, int32_t* prefix, int n, int32_t* tmp, cudaStream_t st,
+                              int64_t* launches, const int32_t** tile_off);
+// nbin sort bins (cells, or sub-cells when shift > 0) whose starts are
+// prefix + tile_off: scatter by the counts (left at zero), order each bin by
+// id, write the bins' starts into start[nbin + 1] and, with shift > 0, the
+// cells' starts into cell_start.
+cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int32_t* prefix, const int32_t* tile_off,
+                                 int32_t* count, int32_t* perm_tmp, const int32_t* id, int32_t* perm, int32_t* start,
+                                 int shift, int32_t* cell_start, cudaStream_t st, int64_t* launches);
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                            const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
                            cudaStream_t st, float4* pos4c = nullptr);

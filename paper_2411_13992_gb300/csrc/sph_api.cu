@@ -51,8 +51,11 @@ struct sph_ctx {
     Consts<float> K32;
     SetPtrs set[2];
     int cur;
-    int32_t *key, *perm_tmp, *perm, *count, *cursor, *start, *scan_tmp;
+    // the sort: keys, permutations, bin counts (zero between sorts), the
+    // scan's within-tile prefixes, the cells' starts and its scratch
+    int32_t *key, *perm_tmp, *perm, *count, *prefix, *start, *scan_tmp;
     int32_t* sub_start;  // the sort's sub-cell starts (x_subcells > 1), else null
+    int count_zero;      // count[] is known to be all zero (a complete sort ran since it was cleared)
     void* vr;
     float4* pos4;
     float4* pos4c;      // FP32 form, uniform h: pos4 with the cell index bits in w
@@ -310,7 +313,7 @@ size_t carve(sph_ctx* c, char* base)
     c->perm = W.take<int32_t>(n);
     const size_t nb1 = sort_bins(c->G) + 1;
     c->count = W.take<int32_t>(nb1);
-    c->cursor = W.take<int32_t>(nb1);
+    c->prefix = W.take<int32_t>(nb1);
     c->start = W.take<int32_t>(nc1);
     c->sub_start = c->G.sub_shift ? W.take<int32_t>(nb1) : nullptr;
     c->G.sub_start = c->sub_start;
@@ -409,18 +412,22 @@ sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
     // the bins' starts: the sub-cells' (the cells' then follow from them) or the cells'
     int32_t* bin_start = c->G.sub_shift ? c->sub_start : c->start;
     SPH_MARK(SPH_K_KICKDRIFT, 0);
-    SPH_CU(cudaMemsetAsync(c->count, 0, nb1 * sizeof(int32_t), c->st));
-    SPH_CU(cudaMemsetAsync(c->cursor, 0, nb1 * sizeof(int32_t), c->st));
+    // the scatter counts every bin back down to zero: clear only when a sort
+    // did not complete since the counts were last known to be zero
+    if (!c->count_zero) SPH_CU(cudaMemsetAsync(c->count, 0, nb1 * sizeof(int32_t), c->st));
+    c->count_zero = 0;
     SPH_CU(launch_kick_drift_key(c->prec, c->dim, n, cur_set(c), c->dt, drift, c->G, c->key, c->count, c->err, c->st));
     ++c->launches;
     SPH_MARK(SPH_K_KICKDRIFT, 1);
     SPH_MARK(SPH_K_SCAN, 0);
-    SPH_CU(launch_exclusive_scan(c->count, bin_start, (int)nb1, c->scan_tmp, c->st, &c->launches));
+    const int32_t* tile_off = nullptr;
+    SPH_CU(launch_scan_tiles(c->count, c->prefix, (int)nb1, c->scan_tmp, c->st, &c->launches, &tile_off));
     SPH_MARK(SPH_K_SCAN, 1);
     const int32_t* id = c->prec == 64 ? c->set[c->cur].d.id : c->set[c->cur].f.id;
     SPH_MARK(SPH_K_ORDER, 0);
-    SPH_CU(launch_scatter_order(n, (int)sort_bins(c->G), c->key, bin_start, c->cursor, c->perm_tmp, id, c->perm,
-                                c->G.sub_shift, c->start, c->st, &c->launches));
+    SPH_CU(launch_scatter_order(n, (int)sort_bins(c->G), c->key, c->prefix, tile_off, c->count, c->perm_tmp, id,
+                                c->perm, bin_start, c->G.sub_shift, c->start, c->st, &c->launches));
+    c->count_zero = 1;
     SPH_MARK(SPH_K_ORDER, 1);
     SPH_MARK(SPH_K_PERMUTE, 0);
     SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
@@ -1403,7 +1410,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     StateSet<double>& S0 = c.set[0].d;
     // The scratch keeps the previous call's contents: clear what is summed into.
     SPH_CU(cudaMemsetAsync(c.count, 0, nc1 * sizeof(int32_t), c.st));
-    SPH_CU(cudaMemsetAsync(c.cursor, 0, nc1 * sizeof(int32_t), c.st));
+    SPH_CU(cudaMemsetAsync(c.prefix, 0, nc1 * sizeof(int32_t), c.st));
     SPH_CU(cudaMemsetAsync(c.err, 0, 4 * sizeof(uint32_t), c.st));
     SPH_CU(cudaMemsetAsync(S0.v, 0, (size_t)c.dim * n * sizeof(double), c.st));
     SPH_CU(launch_vec_in(64, c.dim, ni, x, S0.x, c.st));
