@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kTPB32, 8) k_density32(int n, const float4* __
             // no branch for the warp to diverge on
             const bool take = r2 < K.four_h2_u && r2 > 0.f;
             const bool store = take && cnt < cap;
-            if (store) *lp = ((uint32_t)j << kCodeBits) | code;
+            if (store) __stcs(lp, ((uint32_t)j << kCodeBits) | code);   // read once, by the force pass
             lp += store ? n : 0;
             cnt += take ? 1 : 0;
         } else if (r2 < support2<UNIFORM>(K, hi, pj.w)) {
@@ -969,19 +969,20 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
             };
             // two pairs per iteration in ping-pong registers: the neighbour
             // data one pair ahead and the list entries two ahead in flight
-            uint32_t eA = cnt > 0 ? lp[0] : 0u;
-            uint32_t eB = cnt > 1 ? lp[(size_t)n] : 0u;
+            // (the entries read once, as streaming loads)
+            uint32_t eA = cnt > 0 ? __ldcs(lp) : 0u;
+            uint32_t eB = cnt > 1 ? __ldcs(lp + (size_t)n) : 0u;
             float4 pA = pos4[eA >> kCodeBits], oA = vr[eA >> kCodeBits];
             int k = 0;
             for (; k + 1 < cnt; k += 2) {
                 const float4 pB = pos4[eB >> kCodeBits], oB = vr[eB >> kCodeBits];
-                const uint32_t eC = k + 2 < cnt ? lp[(size_t)(k + 2) * n] : 0u;
+                const uint32_t eC = k + 2 < cnt ? __ldcs(lp + (size_t)(k + 2) * n) : 0u;
                 one(eA, pA, oA);
                 if (k + 2 < cnt) {
                     pA = pos4[eC >> kCodeBits];
                     oA = vr[eC >> kCodeBits];
                 }
-                const uint32_t eD = k + 3 < cnt ? lp[(size_t)(k + 3) * n] : 0u;
+                const uint32_t eD = k + 3 < cnt ? __ldcs(lp + (size_t)(k + 3) * n) : 0u;
                 one(eB, pB, oB);
                 eA = eC;
                 eB = eD;
