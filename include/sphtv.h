@@ -101,7 +101,8 @@ typedef struct sph_params {
     int32_t dim;            /* 2 or 3 */
     int32_t precision;      /* 64: FP64 throughout; 32: FP32 pair sums with
                                Kahan compensation, FP32 cell-relative positions,
-                               FP64 positions for the drift and FP64 reductions */
+                               FP64 positions (each step's displacement in FP32,
+                               accumulated in FP64) and FP64 reductions */
     int32_t periodic[3];    /* 1: periodic along that axis */
     int32_t tv_mode;        /* SPH_TV_*: none / limited (Eq. 16) / unlimited (Eq. 14) /
                                background pressure p0 = rho0 c^2 (Eq. 12): the drift

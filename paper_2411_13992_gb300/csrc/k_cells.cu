@@ -98,12 +98,19 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
     } else if (drift == 1 && S.kind[i] == 0) {
         const double dt = *dt_ptr;
         const double hdt = 0.5 * dt;
+        // FP32 form: the displacement dt v + dr in FP32 (one rounding, from
+        // FP32 inputs), accumulated into the FP64 position
+        const float dt_f = d2f_rn(dt);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             size_t o = (size_t)d * n + i;
             Real vh = kick<Real>(S.v[o], hdt, S.a[o]);
             S.v[o] = vh;
-            double xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(S.dr[o]));
+            double xn;
+            if (sizeof(Real) == 4)
+                xn = __dadd_rn(xs[d], to_double(__fmaf_rn(dt_f, (float)vh, (float)S.dr[o])));
+            else
+                xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(S.dr[o]));
             if (G.periodic[d]) {
                 // the wrap only in warps where a particle left the box (the
                 // FP64 operation would otherwise be issued for every warp)
