@@ -155,6 +155,40 @@ __device__ __forceinline__ void block_partials(double* vals, double* out_block, 
         // the caller's sums are all zero (uniform over the grid): skip them
         if (lane == 0)
             for (int k = 0; k < 5; ++k) sh[w][k] = 0.0;
+    } else if (FIRST) {
+        // the five sums as a transposing reduction: at each of the first three
+        // levels a lane keeps half of its values and adds its partner's copy
+        // of them (4 + 2 + 1 additions instead of 5 per level), then the last
+        // two levels reduce one value per group of four lanes; value g ends in
+        // lane 4 g (eight slots, the last three zero)
+        double v8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v8[k] = k < 5 ? vals[k] : 0.0;
+        const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
+        double a4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double send = hi16 ? v8[j] : v8[4 + j];
+            const double keep = hi16 ? v8[4 + j] : v8[j];
+            a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        double a2[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double send = hi8 ? a4[j] : a4[2 + j];
+            const double keep = hi8 ? a4[2 + j] : a4[j];
+            a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        double a1;
+        {
+            const double send = hi4 ? a2[0] : a2[1];
+            const double keep = hi4 ? a2[1] : a2[0];
+            a1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+        const int g = (lane >> 2);   // value index held by this group of four lanes
+        if ((lane & 3) == 0 && g < 5) sh[w][g] = a1;
     } else {
 #pragma unroll
         for (int k = 0; k < kSums; ++k) {
