@@ -152,6 +152,15 @@ struct KSum {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
+    // add(x) when p holds, else nothing (selected, no branch)
+    __device__ __forceinline__ void add_if(float x, bool p)
+    {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        const float cn = __fsub_rn(__fsub_rn(t, s), y);
+        s = p ? t : s;
+        c = p ? cn : c;
+    }
     __device__ __forceinline__ float value() const { return s; }
 };
 
@@ -159,6 +168,7 @@ struct PlainF {
     float s;
     __device__ __forceinline__ PlainF() : s(0.f) {}
     __device__ __forceinline__ void add(float x) { s += x; }
+    __device__ __forceinline__ void add_if(float x, bool p) { s = p ? s + x : s; }
     __device__ __forceinline__ float value() const { return s; }
 };
 

@@ -90,6 +90,157 @@ __device__ __forceinline__ float w_term_uniform(const Consts<float>& K, float wn
     return wnorm * (t2 * t2) * fmaf(2.f * K.inv_h_u, r, 1.f);
 }
 
+// One candidate's neighbour-list step, predicated (no branch): a force
+// neighbour (0 < r^2 < 4h^2) takes slot cnt of the particle's transposed list
+// (at base_i + cnt x the list's row stride) while the list has room, and is
+// counted either way.  The entry is written once and read once (by the force
+// pass): a streaming store.
+__device__ __forceinline__ void list_take(const uint32_t* base_i, int& cnt, float r2, float four_h2, int cap,
+                                          uint32_t entry, uint32_t stride_bytes)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .u64 a;\n\t"
+        "setp.lt.f32 p, %1, %2;\n\t"
+        "setp.gt.and.f32 p, %1, 0f00000000, p;\n\t"
+        "setp.lt.and.s32 q, %0, %3, p;\n\t"
+        "mad.wide.u32 a, %0, %6, %5;\n\t"
+        "@q st.global.cs.u32 [a], %4;\n\t"
+        "@p add.s32 %0, %0, 1;\n\t}"
+        : "+r"(cnt)
+        : "f"(r2), "f"(four_h2), "r"(cap), "r"(entry), "l"(base_i), "r"(stride_bytes));
+}
+
+// The uniform-resolution density walk: the candidates, their order and their
+// arithmetic are those of for_candidates_rows<DIM, true, true> with the
+// density visit (rows by (dz, dy); each row cut to the sub-cells inside the
+// half-chord, as one run of the sort order or, across a periodic x boundary,
+// two; two candidates per iteration).  A run of odd length takes its last
+// candidate with a second one whose distance is set far outside the support
+// (no term of the sum, no list entry) instead of a separate one-candidate
+// loop, and the list entry (j << 7) | code is formed as
+// (j << 7) + dx + code of the row's dx = 0 cell.  A row that no lane of the
+// warp needs is skipped by a vote; a lane that does not need a row the warp
+// walks takes an empty run.  INNER: every particle of the warp lies R cells
+// or more from both x ends of the grid, so that no row wraps or is clipped
+// along x and the run bounds need no case analysis.
+template <int DIM, typename Acc, bool INNER>
+__device__ __forceinline__ void density_rows(const float* oi, const int* c, const Grid& G, const Consts<float>& K,
+                                             float wnorm, const int32_t* __restrict__ rstart,
+                                             const float4* __restrict__ pos4c, Acc& sigma, int& cnt,
+                                             const uint32_t* base_i, int n, int cap)
+{
+    constexpr int R = kStencilR, zr = DIM == 3 ? R : 0;
+    const unsigned mask = __activemask();
+    const int ncx = G.nc[0];
+    const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+    const float inv_ex = 1.f / ex;
+    const float reach = 2.f * K.h_u;
+    const float reach2 = reach * reach;
+    const int sh = G.sub_shift;
+    const int nsx = ncx << sh;
+    const float inv_exs = inv_ex * (float)(1 << sh);
+    const float four_h2 = K.four_h2_u;
+    const uint32_t stride = (uint32_t)n * (uint32_t)sizeof(uint32_t);
+    const float2 oxy = make_float2(oi[0], oi[1]);
+    auto dist2 = [&](const float4& pj, int dx, float shy, float shz, bool real) {
+        const float shx = -(float)dx * ex;
+        const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f), oxy),
+                                      make_float2(shx, shy));
+        const float2 q = __fmul2_rn(rxy, rxy);
+        float r2 = q.x + q.y;
+        if (DIM == 3) {
+            const float rz = (oi[2] - pj.z) + shz;
+            r2 = fmaf(rz, rz, r2);
+        }
+        return real ? r2 : 1.0e30f;
+    };
+    // candidates jb .. je - 1 of one run; kr = cell index of the run's dx = 0
+    // cell (the candidate's dx is its cell index minus kr)
+    auto run = [&](int jb, int je, int kr, float shy, float shz, uint32_t code0) {
+        for (int j = jb; j < je; j += 2) {
+            const bool two = j + 1 < je;
+            const float4 p0 = pos4c[j];
+            const float4 p1 = pos4c[two ? j + 1 : j];
+            const int d0 = __float_as_int(p0.w) - kr, d1 = __float_as_int(p1.w) - kr;
+            const float r20 = dist2(p0, d0, shy, shz, true);
+            const float r21 = dist2(p1, d1, shy, shz, two);
+            const uint32_t jv = (uint32_t)j << kCodeBits;
+            sigma.add(w_term_uniform(K, wnorm, r20));
+            list_take(base_i, cnt, r20, four_h2, cap, jv + code0 + (uint32_t)d0, stride);
+            sigma.add_if(w_term_uniform(K, wnorm, r21), two);
+            list_take(base_i, cnt, r21, four_h2, cap, jv + (1u << kCodeBits) + code0 + (uint32_t)d1, stride);
+        }
+    };
+    for (int dz = -zr; dz <= zr; ++dz) {
+        const int cz = DIM == 3 ? cell_step(G, c[2], dz, 2) : 0;
+        float rz = 0.f;
+        if (DIM == 3) {
+            rz = dz > 0 ? dz * ez - oi[2] : (dz < 0 ? oi[2] + (-dz - 1) * ez : 0.f);
+            rz = fmaxf(rz - 1e-3f * ez, 0.f);
+        }
+        const float wz2 = reach2 - rz * rz;
+        const bool zok = cz >= 0 && wz2 > 0.f;
+        if (!__any_sync(mask, zok)) continue;
+        const float shz = -(float)dz * ez;
+        for (int dy = -R; dy <= R; ++dy) {
+            const int cy = cell_step(G, c[1], dy, 1);
+            float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
+            ry = fmaxf(ry - 1e-3f * ey, 0.f);
+            const float w2 = wz2 - ry * ry;
+            const float w = sqrtf(fmaxf(w2, 0.f)) + 1e-3f * ex;
+            const int slo = max(__float2int_rd((oi[0] - w) * inv_exs), -(R << sh));
+            const int shi = min(__float2int_rd((oi[0] + w) * inv_exs), ((R + 1) << sh) - 1);
+            const bool ok = zok && cy >= 0 && w2 > 0.f && slo <= shi;
+            if (!__any_sync(mask, ok)) continue;
+            const int row = ncx * (cy + G.nc[1] * cz);
+            const int rb = row << sh;                            // first sort bin of the row
+            const float shy = -(float)dy * ey;
+            const uint32_t code0 = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
+            // sub-cells a .. b along the row (may leave [0, nsx) on a periodic axis)
+            const int a = (c[0] << sh) + slo, b = (c[0] << sh) + shi;
+            if (INNER) {
+                int jb = 0, je = 0;
+                if (ok) {
+                    jb = rstart[rb + a];
+                    je = rstart[rb + b + 1];
+                }
+                run(jb, je, row + c[0], shy, shz, code0);
+                continue;
+            }
+            // runs lo .. hi (sub-cells of the row) with their dx = 0 cell
+            int lo0 = a, hi0 = b, kr0 = row + c[0], lo1 = 0, hi1 = -1, kr1 = row + c[0];
+            if (!G.periodic[0]) {
+                lo0 = max(a, 0);
+                hi0 = min(b, nsx - 1);
+            } else if (a < 0) {
+                lo0 = nsx + a;
+                hi0 = min(nsx - 1, nsx + b);
+                kr0 = row + c[0] + ncx;
+                hi1 = b;
+            } else if (a >= nsx) {
+                lo0 = a - nsx;
+                hi0 = b - nsx;
+                kr0 = row + c[0] - ncx;
+            } else if (b >= nsx) {
+                hi0 = nsx - 1;
+                hi1 = b - nsx;
+                kr1 = row + c[0] - ncx;
+            }
+            int jb0 = 0, je0 = 0, jb1 = 0, je1 = 0;
+            if (ok && lo0 <= hi0) {
+                jb0 = rstart[rb + lo0];
+                je0 = rstart[rb + hi0 + 1];
+            }
+            if (ok && lo1 <= hi1) {
+                jb1 = rstart[rb + lo1];
+                je1 = rstart[rb + hi1 + 1];
+            }
+            run(jb0, je0, kr0, shy, shz, code0);
+            run(jb1, je1, kr1, shy, shz, code0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- density
 //
 // sigma_i over all neighbours (self included); also writes the particle's
@@ -97,12 +248,14 @@ __device__ __forceinline__ float w_term_uniform(const Consts<float>& K, float wn
 // entry k of particle i at nbl[k * n + i] = (j << 7) | code, and the count
 // (which may exceed cap: the force kernel then scans the cells itself).
 
-// Register budget: eight blocks of 128 threads per SM (at most 64 registers;
-// 56 used, no spills).  The compiler's own choice, 48 registers with spills,
-// ran the 128^3 pass 7 % longer early in the run and 25 % longer after step
-// 400; nine and seven blocks were within 1-3 % of eight.
+// Blocks of 512 threads (16 warps of neighbouring particles, whose walks
+// share the candidates' cache lines in L1), two per SM, with the register
+// budget of 1,024 threads per SM (at most 64 registers; 56 used, no spills).
+// The compiler's own choice, 48 registers with spills, ran the 128^3 pass
+// 7 % longer early in the run and 25 % longer after step 400.
+constexpr int kDensityTPB32 = 512;
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32, 8) k_density32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kDensityTPB32, 2) k_density32(int n, const float4* __restrict__ pos4,
                                                       const int32_t* __restrict__ cell_of,
                                                       const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                       StateSet<float> S, float4* __restrict__ vr,
@@ -157,8 +310,20 @@ __global__ void __launch_bounds__(kTPB32, 8) k_density32(int n, const float4* __
     // at uniform resolution the walk reads the copy of the offsets that
     // carries each candidate's cell index in w (one load per candidate
     // instead of two)
-    if (UNIFORM) for_candidates_rows<DIM, true, true>(oi, reach, cell_i, G, start, cell_of, pos4c, visit);
-    else for_candidates_rows<DIM>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
+    if (UNIFORM) {
+        // warps whose particles all sit R cells or more from the x ends of
+        // the grid take the walk without the periodic split and the clip
+        int c[3];
+        cell_decode(G, cell_i, c);
+        const bool inner = c[0] >= kStencilR && c[0] < G.nc[0] - kStencilR;
+        const int32_t* rstart = G.sub_shift ? G.sub_start : start;
+        if (__all_sync(__activemask(), inner))
+            density_rows<DIM, Acc, true>(oi, c, G, K, wnorm, rstart, pos4c, sigma, cnt, nbl + i, n, cap);
+        else
+            density_rows<DIM, Acc, false>(oi, c, G, K, wnorm, rstart, pos4c, sigma, cnt, nbl + i, n, cap);
+    } else {
+        for_candidates_rows<DIM>(oi, reach, cell_i, G, start, cell_of, pos4, visit);
+    }
     nbc[i] = cnt;
     // rho - rho0 = rho0 (sigma - sigma0) / sigma0; sigma - sigma0 is exact in FP32
     const float w = K.rho0 * (sigma.value() - s0) / s0;
@@ -1078,7 +1243,7 @@ static void density_t(int n, const float4* pos4, const int32_t* cell_of, const i
                       const Consts<float>& K, StateSet<float> S, float4* vr, uint32_t* nbl, int32_t* nbc,
                       cudaStream_t st, const float4* pos4c)
 {
-    const int T = pair_threads(32, n, G.sms);
+    const int T = n >= G.sms * kDensityTPB32 ? kDensityTPB32 : pair_threads(32, n, G.sms);
     k_density32<DIM, Acc, U><<<nblk(n, T), T, 0, st>>>(n, pos4, cell_of, start, G, K, S, vr, nbl, nbc,
                                                        nbl_capacity(DIM), pos4c);
 }
