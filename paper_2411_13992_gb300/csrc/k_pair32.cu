@@ -35,6 +35,67 @@ __device__ __forceinline__ float support2(const Consts<float>& K, float hi, floa
     return 4.f * h * h;
 }
 
+// The force pass's sums a_i and R_i (DIM components each).  Generic form:
+// one accumulator per component.
+template <int DIM, typename Acc>
+struct PairSums {
+    Acc a[DIM], R[DIM];
+    __device__ __forceinline__ void add(const float* xa, const float* xR)
+    {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            a[d].add(xa[d]);
+            R[d].add(xR[d]);
+        }
+    }
+    __device__ __forceinline__ float a_value(int d) const { return a[d].value(); }
+    __device__ __forceinline__ float R_value(int d) const { return R[d].value(); }
+};
+
+// Compensated form: the same Kahan steps as KSum, component by component,
+// taken two components at a time in packed FP32x2 arithmetic (each lane of a
+// packed operation is the IEEE operation of KSum, so the sums are bit for
+// bit those of six KSum accumulators).  Components: (a0, a1), (a2, R0),
+// (R1, R2) in 3-D; (a0, a1), (R0, R1) in 2-D.
+struct KSum2 {
+    float2 s, c;
+    __device__ __forceinline__ KSum2() : s(make_float2(0.f, 0.f)), c(make_float2(0.f, 0.f)) {}
+    __device__ __forceinline__ void add(float2 x)
+    {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 y = __ffma2_rn(c, m1, x);      // x - c
+        const float2 t = __fadd2_rn(s, y);
+        const float2 u = __ffma2_rn(s, m1, t);      // t - s
+        c = __ffma2_rn(y, m1, u);                   // (t - s) - y
+        s = t;
+    }
+};
+
+template <int DIM>
+struct PairSums<DIM, KSum> {
+    KSum2 p[DIM];
+    __device__ __forceinline__ void add(const float* xa, const float* xR)
+    {
+        if (DIM == 3) {
+            p[0].add(make_float2(xa[0], xa[1]));
+            p[1].add(make_float2(xa[2], xR[0]));
+            p[2].add(make_float2(xR[1], xR[2]));
+        } else {
+            p[0].add(make_float2(xa[0], xa[1]));
+            p[1].add(make_float2(xR[0], xR[1]));
+        }
+    }
+    __device__ __forceinline__ float a_value(int d) const
+    {
+        return d == 0 ? p[0].s.x : (d == 1 ? p[0].s.y : p[1].s.x);
+    }
+    __device__ __forceinline__ float R_value(int d) const
+    {
+        if (DIM == 2) return d == 0 ? p[1].s.x : p[1].s.y;
+        return d == 0 ? p[1].s.y : (d == 1 ? p[2].s.x : p[2].s.y);
+    }
+};
+
 // One neighbour's contribution to a_i and R_i in the FP32 form, given
 // rv = x_i - x_j, 1/r and dwr = W'(r)/r: the same formulas as pair_force64
 // (Eq. 3, 5-7, 14) arranged for FP32 throughput -- W' only enters through
@@ -43,7 +104,7 @@ __device__ __forceinline__ float support2(const Consts<float>& K, float hi, floa
 template <int DIM, typename Acc>
 __device__ __forceinline__ void pair_force32(const Consts<float>& K, const float* rv, float inv_r, float dwr,
                                              const float* vi, float rho_i, float inv_rho_i, float p_i,
-                                             const float4& oj, float m_j, Acc* acc_a, Acc* acc_R)
+                                             const float4& oj, float m_j, PairSums<DIM, Acc>& sums)
 {
     const bool wall = isinf(oj.w);
     const float rho_j = wall ? rho_i : K.rho0 + oj.w;
@@ -61,11 +122,13 @@ __device__ __forceinline__ void pair_force32(const Consts<float>& K, const float
     const float cpw = -2.f * mr * pstar * dwr;           // pressure: cp * W'/r
     const float cv = K.two_eta * mr * dwr;               // viscous
     const float vw = m_j * inv_rho_j * dwr;              // residual: V_j W'/r
+    float xa[DIM], xR[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        acc_a[d].add(cpw * rv[d] + cv * dv[d]);
-        acc_R[d].add(vw * rv[d]);
+        xa[d] = cpw * rv[d] + cv * dv[d];
+        xR[d] = vw * rv[d];
     }
+    sums.add(xa, xR);
 }
 
 // W'(r)/r for r < 2h: a_D h^-(D+2) (-5) t^3 with t = 1 - r/(2h).
@@ -187,7 +250,7 @@ __device__ __forceinline__ void density_rows(const float* oi, const int* c, cons
             float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
             ry = fmaxf(ry - 1e-3f * ey, 0.f);
             const float w2 = wz2 - ry * ry;
-            const float w = sqrtf(fmaxf(w2, 0.f)) + 1e-3f * ex;
+            const float w = sqrt_approx(fmaxf(w2, 0.f)) + 1e-3f * ex;
             const int slo = max(__float2int_rd((oi[0] - w) * inv_exs), -(R << sh));
             const int shi = min(__float2int_rd((oi[0] + w) * inv_exs), ((R + 1) << sh) - 1);
             const bool ok = zok && cy >= 0 && w2 > 0.f && slo <= shi;
@@ -537,7 +600,7 @@ __device__ __forceinline__ bool row_extent(const float* oi, int dy, int dz, floa
     ry = fmaxf(ry - 1e-3f * ey, 0.f);
     const float w2 = wz2 - ry * ry;
     if (w2 <= 0.f) return false;
-    const float w = sqrtf(w2) + 1e-3f * ex;
+    const float w = sqrt_approx(w2) + 1e-3f * ex;
     dxlo = max(__float2int_rd((oi[0] - w) * inv_ex), -R);
     dxhi = min(__float2int_rd((oi[0] + w) * inv_ex), R);
     return dxlo <= dxhi;
@@ -689,7 +752,6 @@ __global__ void __launch_bounds__(FlatShape<DIM>::T) k_density32_flat(
 {
     using TD = TileDims<DIM>;
     constexpr int T = FlatShape<DIM>::T, NR = FlatShape<DIM>::NR, R = TD::R, H0 = TD::H0, H1 = TD::H1, NHC = TD::NHC;
-    constexpr int Rz = DIM == 3 ? R : 0;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_warp[T / 32 + 1];
     __shared__ int s_home[TD::NHOME + 1];
@@ -1095,7 +1157,7 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
         const float rho_i = K.rho0 + me.w;
         const float p_i = K.c2 * me.w;
         const float inv_rho_i = rcp_approx(rho_i);
-        Acc acc_a[DIM], acc_R[DIM];
+        PairSums<DIM, Acc> sums;
         // W'/r = coef t^3, coef = -5 a_D h^-(D+2) (uniform h: one constant)
         const float norm = kernel_norm<DIM, float>();
         auto pair = [&](int j, const float4& pj, const float4& oj, const float* rv, float r2) {
@@ -1111,7 +1173,7 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
             }
             const float coef = UNIFORM ? K.dwr_coef_u : -5.f * norm * pow_dim<DIM, float>(inv_h) * inv_h * inv_h;
             const float dwr = dwr_of<DIM>(r, inv_h, coef);
-            pair_force32<DIM, Acc>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, oj, m_j, acc_a, acc_R);
+            pair_force32<DIM, Acc>(K, rv, inv_r, dwr, vi, rho_i, inv_rho_i, p_i, oj, m_j, sums);
         };
         const int cnt = nbc[i];
         if (cnt <= cap) {
@@ -1172,12 +1234,12 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             // at uniform resolution the sums were taken without the factor C of W'/r
-            const float pair_a = acc_a[d].value();
+            const float pair_a = sums.a_value(d);
             // the fluid's momentum rate from its pair terms: minus the force on the walls
             if (K.body_force) part[9 + d] = m_i * (double)pair_a;
             a[d] = K.g[d] + pair_a;
             if (K.fr_on) a[d] = fmaf(lam, K.fr_u[d] - vi[d], a[d]);
-            R[d] = acc_R[d].value();
+            R[d] = sums.R_value(d);
             R2 += R[d] * R[d];
         }
         const float htv = K.tv_h_particle ? hi : K.h_min;

@@ -119,7 +119,7 @@ __device__ __forceinline__ void for_candidates_rows(const float* oi, float reach
             ry = fmaxf(ry - 1e-3f * ey, 0.f);
             const float w2 = wz2 - ry * ry;
             if (w2 <= 0.f) continue;
-            const float w = sqrtf(w2) + 1e-3f * ex;
+            const float w = sqrt_approx(w2) + 1e-3f * ex;
             const int slo = max(__float2int_rd((oi[0] - w) * inv_exs), -(R << sh));
             const int shi = min(__float2int_rd((oi[0] + w) * inv_exs), ((R + 1) << sh) - 1);
             if (slo > shi) continue;
