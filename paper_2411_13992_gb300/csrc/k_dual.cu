@@ -118,7 +118,9 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
         uint32_t e_nxt = cnt > 1 ? lp[(size_t)n] : 0u;
         float4 pj_n = A.pos4[e_cur >> kCodeBits];
         float4 oj_n = A.vr[e_cur >> kCodeBits];
-        for (int k = 0; k < cnt; ++k) {
+        // the entry two ahead through a pointer that advances by one list row
+        const uint32_t* lq = lp + 2 * (size_t)n;
+        for (int k = 0; k < cnt; ++k, lq += n) {
             const uint32_t ec = e_cur;
             const float4 pj = pj_n;
             const float4 oj = oj_n;
@@ -127,7 +129,7 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
                 oj_n = A.vr[e_nxt >> kCodeBits];
             }
             e_cur = e_nxt;
-            e_nxt = (k + 2 < cnt) ? lp[(size_t)(k + 2) * n] : 0u;
+            e_nxt = (k + 2 < cnt) ? *lq : 0u;
             const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
             float rv[3] = {0.f, 0.f, 0.f};
             rv[0] = (oi[0] - pj.x) + sh.x;

@@ -1196,20 +1196,23 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
             };
             // two pairs per iteration in ping-pong registers: the neighbour
             // data one pair ahead and the list entries two ahead in flight
-            // (the entries read once, as streaming loads)
+            // (the entries read once, as streaming loads, through a pointer
+            // that advances by two list rows per iteration)
             uint32_t eA = cnt > 0 ? __ldcs(lp) : 0u;
             uint32_t eB = cnt > 1 ? __ldcs(lp + (size_t)n) : 0u;
             float4 pA = pos4[eA >> kCodeBits], oA = vr[eA >> kCodeBits];
             int k = 0;
-            for (; k + 1 < cnt; k += 2) {
+            const uint32_t* lq = lp + 2 * (size_t)n;
+            const size_t n2 = 2 * (size_t)n;
+            for (; k + 1 < cnt; k += 2, lq += n2) {
                 const float4 pB = pos4[eB >> kCodeBits], oB = vr[eB >> kCodeBits];
-                const uint32_t eC = k + 2 < cnt ? __ldcs(lp + (size_t)(k + 2) * n) : 0u;
+                const uint32_t eC = k + 2 < cnt ? __ldcs(lq) : 0u;
                 one(eA, pA, oA);
                 if (k + 2 < cnt) {
                     pA = pos4[eC >> kCodeBits];
                     oA = vr[eC >> kCodeBits];
                 }
-                const uint32_t eD = k + 3 < cnt ? __ldcs(lp + (size_t)(k + 3) * n) : 0u;
+                const uint32_t eD = k + 3 < cnt ? __ldcs(lq + n) : 0u;
                 one(eB, pB, oB);
                 eA = eC;
                 eB = eD;
