@@ -245,10 +245,15 @@ __device__ __forceinline__ void density_rows(const float* oi, const int* c, cons
         const bool zok = cz >= 0 && wz2 > 0.f;
         if (!__any_sync(mask, zok)) continue;
         const float shz = -(float)dz * ez;
-        for (int dy = -R; dy <= R; ++dy) {
+        // per row: dyf = dy, shy = -dy ey (exact steps of ey) and the code of
+        // the row's dx = -R cell advance with dy; the nearest y distance of the
+        // row is the larger of dy ey - o_y (dy > 0) and o_y + (-dy - 1) ey
+        // (dy < 0), the other being negative, and 0 for dy = 0
+        float dyf = (float)(-R), shy = (float)R * ey;
+        uint32_t code0 = (uint32_t)(R + kSide * kSide * (dz + R));
+        for (int dy = -R; dy <= R; ++dy, dyf += 1.f, shy -= ey, code0 += kSide) {
             const int cy = cell_step(G, c[1], dy, 1);
-            float ry = dy > 0 ? dy * ey - oi[1] : (dy < 0 ? oi[1] + (-dy - 1) * ey : 0.f);
-            ry = fmaxf(ry - 1e-3f * ey, 0.f);
+            const float ry = fmaxf(fmaxf(fmaf(dyf, ey, -oi[1]), fmaf(-dyf - 1.f, ey, oi[1])) - 1e-3f * ey, 0.f);
             const float w2 = wz2 - ry * ry;
             const float w = sqrt_approx(fmaxf(w2, 0.f)) + 1e-3f * ex;
             const int slo = max(__float2int_rd((oi[0] - w) * inv_exs), -(R << sh));
@@ -257,8 +262,6 @@ __device__ __forceinline__ void density_rows(const float* oi, const int* c, cons
             if (!__any_sync(mask, ok)) continue;
             const int row = ncx * (cy + G.nc[1] * cz);
             const int rb = row << sh;                            // first sort bin of the row
-            const float shy = -(float)dy * ey;
-            const uint32_t code0 = (uint32_t)(R + kSide * (dy + R) + kSide * kSide * (dz + R));
             // sub-cells a .. b along the row (may leave [0, nsx) on a periodic axis)
             const int a = (c[0] << sh) + slo, b = (c[0] << sh) + shi;
             if (INNER) {
