@@ -1127,8 +1127,16 @@ __global__ void __launch_bounds__(TileThreads<DIM>::COOP, 4) k_density32_coop(
 
 // ------------------------------------------------------------------ forces
 
+// Register budget at uniform resolution: six blocks of 128 threads per SM
+// (at most 85 registers; 80 used, no spills), for the three pairs of neighbour
+// data in flight ahead of the three being computed.  The pass waits on these
+// gathers (L1/L2 hits): with eight blocks and one pair of data ahead it ran
+// 12 % longer early in a 128^3 run and 11 % longer after step 400; with three
+// pairs per iteration at seven or eight blocks the registers spill (+35-75 %).
+// Variable resolution keeps eight blocks (64 registers) and one pair ahead:
+// at six blocks its pass ran 10 % longer.
 template <int DIM, typename Acc, bool UNIFORM>
-__global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __restrict__ pos4,
+__global__ void __launch_bounds__(kTPB32, UNIFORM ? 6 : 8) k_forces32(int n, const float4* __restrict__ pos4,
                                                      const int32_t* __restrict__ cell_of,
                                                      const int32_t* __restrict__ start, Grid G, Consts<float> K,
                                                      StateSet<float> S, const float* __restrict__ mf,
@@ -1181,8 +1189,8 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
         const int cnt = nbc[i];
         if (cnt <= cap) {
             // the neighbour list of the density pass: no candidate tests.
-            // Software pipeline: the list entry two ahead and the neighbour
-            // data one ahead are in flight while this pair is computed.
+            // Software pipeline: the list entries six ahead and the
+            // neighbour data three ahead are in flight while a pair is computed.
             const uint32_t* lp = nbl + i;
             auto one = [&](uint32_t ec, const float4& pj, const float4& oj) {
                 const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
@@ -1197,30 +1205,71 @@ __global__ void __launch_bounds__(kTPB32, 8) k_forces32(int n, const float4* __r
                 }
                 pair((int)(ec >> kCodeBits), pj, oj, rv, r2);
             };
-            // two pairs per iteration in ping-pong registers: the neighbour
-            // data one pair ahead and the list entries two ahead in flight
-            // (the entries read once, as streaming loads, through a pointer
-            // that advances by two list rows per iteration)
-            uint32_t eA = cnt > 0 ? __ldcs(lp) : 0u;
-            uint32_t eB = cnt > 1 ? __ldcs(lp + (size_t)n) : 0u;
-            float4 pA = pos4[eA >> kCodeBits], oA = vr[eA >> kCodeBits];
-            int k = 0;
-            const uint32_t* lq = lp + 2 * (size_t)n;
-            const size_t n2 = 2 * (size_t)n;
-            for (; k + 1 < cnt; k += 2, lq += n2) {
-                const float4 pB = pos4[eB >> kCodeBits], oB = vr[eB >> kCodeBits];
-                const uint32_t eC = k + 2 < cnt ? __ldcs(lq) : 0u;
-                one(eA, pA, oA);
-                if (k + 2 < cnt) {
-                    pA = pos4[eC >> kCodeBits];
-                    oA = vr[eC >> kCodeBits];
+            // uniform resolution: three pairs per iteration, the next
+            // iteration's three pairs of neighbour data and the entries of the
+            // one after in flight (the entries read once, as streaming loads,
+            // through a pointer that advances by three list rows per
+            // iteration); the pairs in list order, so the sums are those of a
+            // pair-by-pair walk
+            if constexpr (UNIFORM) {
+                uint32_t e[6];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) e[t] = cnt > t ? __ldcs(lp + (size_t)t * n) : 0u;
+                float4 pc[3], oc[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    pc[t] = pos4[e[t] >> kCodeBits];
+                    oc[t] = vr[e[t] >> kCodeBits];
                 }
-                const uint32_t eD = k + 3 < cnt ? __ldcs(lq + n) : 0u;
-                one(eB, pB, oB);
-                eA = eC;
-                eB = eD;
+                int k = 0;
+                const uint32_t* lq = lp + 6 * (size_t)n;
+                const size_t n3 = 3 * (size_t)n;
+                for (; k + 2 < cnt; k += 3, lq += n3) {
+                    float4 pn[3], on[3];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        pn[t] = pos4[e[3 + t] >> kCodeBits];
+                        on[t] = vr[e[3 + t] >> kCodeBits];
+                    }
+                    uint32_t en[3];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) en[t] = k + 6 + t < cnt ? __ldcs(lq + (size_t)t * n) : 0u;
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) one(e[t], pc[t], oc[t]);
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        pc[t] = pn[t];
+                        oc[t] = on[t];
+                        e[t] = e[3 + t];
+                        e[3 + t] = en[t];
+                    }
+                }
+                if (k < cnt) one(e[0], pc[0], oc[0]);
+                if (k + 1 < cnt) one(e[1], pc[1], oc[1]);
+            } else {
+                // variable resolution (the pair's h per pair: more registers):
+                // two pairs per iteration, the neighbour data one pair ahead
+                uint32_t eA = cnt > 0 ? __ldcs(lp) : 0u;
+                uint32_t eB = cnt > 1 ? __ldcs(lp + (size_t)n) : 0u;
+                float4 pA = pos4[eA >> kCodeBits], oA = vr[eA >> kCodeBits];
+                int k = 0;
+                const uint32_t* lq = lp + 2 * (size_t)n;
+                const size_t n2 = 2 * (size_t)n;
+                for (; k + 1 < cnt; k += 2, lq += n2) {
+                    const float4 pB = pos4[eB >> kCodeBits], oB = vr[eB >> kCodeBits];
+                    const uint32_t eC = k + 2 < cnt ? __ldcs(lq) : 0u;
+                    one(eA, pA, oA);
+                    if (k + 2 < cnt) {
+                        pA = pos4[eC >> kCodeBits];
+                        oA = vr[eC >> kCodeBits];
+                    }
+                    const uint32_t eD = k + 3 < cnt ? __ldcs(lq + n) : 0u;
+                    one(eB, pB, oB);
+                    eA = eC;
+                    eB = eD;
+                }
+                if (k < cnt) one(eA, pA, oA);
             }
-            if (k < cnt) one(eA, pA, oA);
         } else {
             // more neighbours than the list holds: scan the cells
             auto visit = [&](int j, uint32_t, const float4& pj, float r2, float rx, float ry, float rz) {
