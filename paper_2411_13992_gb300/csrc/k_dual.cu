@@ -89,8 +89,8 @@ __device__ __forceinline__ void fill_shift_table(const Grid& G, float4* tab)
 
 // Visit the frozen neighbour list of particle i: f(j, rv, r2, wj, oj) with
 // rv the pair vector x_i - x_j at the current positions, wj = pos4[j].w (FP32
-// form: m or h) and oj = vr[j].  The FP32 walk keeps the list entry two ahead
-// and the neighbour's data one ahead in flight.
+// form: m or h) and oj = vr[j].  The FP32 walk keeps the list entries four
+// ahead and the neighbour data two ahead in flight.
 template <typename Real, int DIM, typename F>
 __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, const float4* tab, int i, int cnt, F& f)
 {
@@ -114,22 +114,7 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
         const float4 pi = A.pos4[i];
         const float oi[3] = {pi.x, pi.y, pi.z};
         const uint32_t* lp = A.nbl + i;
-        uint32_t e_cur = cnt > 0 ? lp[0] : 0u;
-        uint32_t e_nxt = cnt > 1 ? lp[(size_t)n] : 0u;
-        float4 pj_n = A.pos4[e_cur >> kCodeBits];
-        float4 oj_n = A.vr[e_cur >> kCodeBits];
-        // the entry two ahead through a pointer that advances by one list row
-        const uint32_t* lq = lp + 2 * (size_t)n;
-        for (int k = 0; k < cnt; ++k, lq += n) {
-            const uint32_t ec = e_cur;
-            const float4 pj = pj_n;
-            const float4 oj = oj_n;
-            if (k + 1 < cnt) {
-                pj_n = A.pos4[e_nxt >> kCodeBits];
-                oj_n = A.vr[e_nxt >> kCodeBits];
-            }
-            e_cur = e_nxt;
-            e_nxt = (k + 2 < cnt) ? *lq : 0u;
+        auto one = [&](uint32_t ec, const float4& pj, const float4& oj) {
             const float4 sh = tab[ec & ((1u << kCodeBits) - 1u)];
             float rv[3] = {0.f, 0.f, 0.f};
             rv[0] = (oi[0] - pj.x) + sh.x;
@@ -140,7 +125,30 @@ __device__ __forceinline__ void for_list(const DualK<Real>& A, const Grid& G, co
                 r2 += rv[2] * rv[2];
             }
             f((int)(ec >> kCodeBits), rv, r2, pj.w, oj);
+        };
+        // two pairs per iteration, in list order: the next iteration's two
+        // pairs of neighbour data and the entries of the one after in flight,
+        // the entries through a pointer that advances by two rows
+        uint32_t e0 = cnt > 0 ? lp[0] : 0u;
+        uint32_t e1 = cnt > 1 ? lp[(size_t)n] : 0u;
+        uint32_t e2 = cnt > 2 ? lp[2 * (size_t)n] : 0u;
+        uint32_t e3 = cnt > 3 ? lp[3 * (size_t)n] : 0u;
+        float4 p0 = A.pos4[e0 >> kCodeBits], o0 = A.vr[e0 >> kCodeBits];
+        float4 p1 = A.pos4[e1 >> kCodeBits], o1 = A.vr[e1 >> kCodeBits];
+        int k = 0;
+        const uint32_t* lq = lp + 4 * (size_t)n;
+        const size_t n2 = 2 * (size_t)n;
+        for (; k + 1 < cnt; k += 2, lq += n2) {
+            const float4 p2 = A.pos4[e2 >> kCodeBits], o2 = A.vr[e2 >> kCodeBits];
+            const float4 p3 = A.pos4[e3 >> kCodeBits], o3 = A.vr[e3 >> kCodeBits];
+            const uint32_t e4 = k + 4 < cnt ? lq[0] : 0u;
+            const uint32_t e5 = k + 5 < cnt ? lq[n] : 0u;
+            one(e0, p0, o0);
+            one(e1, p1, o1);
+            p0 = p2; o0 = o2; p1 = p3; o1 = o3;
+            e0 = e2; e1 = e3; e2 = e4; e3 = e5;
         }
+        if (k < cnt) one(e0, p0, o0);
     }
 }
 
