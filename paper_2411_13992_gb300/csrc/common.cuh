@@ -328,6 +328,10 @@ constexpr int kCodes = kSide * kSide * kSide;            // 125 for R = 2
 constexpr int kCodeBits = 7;
 static_assert(kCodes <= (1 << kCodeBits), "stencil code does not fit");
 
+// Entries per particle of the force-neighbour list (a particle with more
+// neighbours is walked over its cells instead).
+__host__ __device__ constexpr int list_capacity(int dim) { return dim == 3 ? 128 : 96; }
+
 // FP32 shift of a neighbour cell from its stencil code: the pair vector is
 // (o_i - o_j) + shift for cell-relative offsets o.
 __device__ __forceinline__ void code_shift(const Grid& G, uint32_t code, float* sh)

@@ -45,6 +45,8 @@ struct Tape {
     const float4* pos4;    // FP32 form: cell-relative positions
     const int32_t* cell;   // FP32 form: cell of each particle
     const double* dt;      // step size of the step
+    const uint32_t* nbl;   // FP32 form: the step's force-neighbour list (transposed), or null
+    const int32_t* nbc;    // and its counts
 };
 
 // Visit the neighbours j != k of particle k with 0 < r < 2 h_kj, decided
@@ -56,11 +58,42 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
                                           F& f)
 {
     if constexpr (sizeof(Real) == 4) {
-        // FP32 form: the clipped row walk of the forward density pass, with
-        // its arithmetic for r^2, so the pairs are exactly the forward's
-        // (same order as the cell scan below)
         const float4 pk = T.pos4[k];
         const float ok[3] = {pk.x, pk.y, pk.z};
+        const int cnt = T.nbl ? T.nbc[k] : 0;
+        if (T.nbl && cnt <= list_capacity(DIM)) {
+            // FP32 form: the forward density pass's list of the step, which
+            // holds exactly the pairs its walk accepted, in the walk's order;
+            // the pair vector and r^2 with the walk's arithmetic
+            const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+            const uint32_t* lp = T.nbl + k;
+            for (int q = 0; q < cnt; ++q, lp += n) {
+                const uint32_t e = *lp;
+                const int j = (int)(e >> kCodeBits);
+                const uint32_t code = e & ((1u << kCodeBits) - 1u);
+                const int dx = (int)(code % kSide) - kStencilR, dy = (int)((code / kSide) % kSide) - kStencilR,
+                          dz = (int)(code / (kSide * kSide)) - kStencilR;
+                const float4 pj = T.pos4[j];
+                const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
+                                                         make_float2(ok[0], ok[1])),
+                                              make_float2(-(float)dx * ex, -(float)dy * ey));
+                const float2 qq = __fmul2_rn(rxy, rxy);
+                float r2 = qq.x + qq.y;
+                float rz = 0.f;
+                if (DIM == 3) {
+                    rz = (ok[2] - pj.z) + -(float)dz * ez;
+                    r2 = fmaf(rz, rz, r2);
+                }
+                const Real rv[3] = {rxy.x, rxy.y, rz};
+                const float inv_r = rsqrtf(r2);
+                f(j, rv, r2 * inv_r, inv_r);
+            }
+            return;
+        }
+        // more neighbours than the list holds (or no list): the clipped row
+        // walk of the forward density pass, with its arithmetic for r^2, so
+        // the pairs are exactly the forward's (same order as the cell scan
+        // below)
         const float hk = (float)T.h[k];
         const float reach = K.uniform_h ? 2.f * K.h_u : 2.f * pair_h(K, hk, K.h_u);
         auto g = [&](int j, uint32_t, const float4&, float r2, float rx, float ry, float rz) {
@@ -398,6 +431,7 @@ static Tape<Real> make_tape(const TapeView& V)
     T.vr = (const typename Vec4<Real>::T*)V.vr;
     T.R = (const Real*)V.R;
     T.start = V.start; T.pos4 = V.pos4; T.cell = V.cell; T.dt = V.dt;
+    T.nbl = V.nbl; T.nbc = V.nbc;
     return T;
 }
 

@@ -1353,7 +1353,7 @@ __global__ void __launch_bounds__(kTPB32, UNIFORM ? 6 : 8) k_forces32(int n, con
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-int nbl_capacity(int dim) { return dim == 3 ? 128 : 96; }
+int nbl_capacity(int dim) { return list_capacity(dim); }
 
 template <int DIM, typename Acc, bool U>
 static void density_t(int n, const float4* pos4, const int32_t* cell_of, const int32_t* start, const Grid& G,

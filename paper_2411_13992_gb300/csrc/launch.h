@@ -24,6 +24,8 @@ struct TapeView {
     const float4* pos4;
     const int32_t* cell;
     const double* dt;
+    const uint32_t* nbl;   // FP32 form: the step's force-neighbour list (transposed, nbl_capacity rows)
+    const int32_t* nbc;    // and its counts
 };
 
 // Adjoint buffers: cotangents in the caller's order ([3][n] FP64) and

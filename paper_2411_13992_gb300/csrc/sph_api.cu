@@ -39,6 +39,8 @@ struct TapeSlot {
     float4* pos4;
     int32_t* cell;
     double* dt;
+    uint32_t* nbl;      // FP32 form: the step's force-neighbour list (the density pass's, transposed)
+    int32_t* nbc;       // and its counts
 };
 
 struct sph_ctx {
@@ -359,6 +361,8 @@ size_t carve(sph_ctx* c, char* base)
             sl.pos4 = c->prec == 32 ? W.take<float4>(n) : nullptr;
             sl.cell = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
             sl.dt = W.take<double>(1);
+            sl.nbl = c->prec == 32 ? W.take<uint32_t>((size_t)nbl_capacity(D) * n) : nullptr;
+            sl.nbc = c->prec == 32 ? W.take<int32_t>(n) : nullptr;
             if (base && c->tape) c->tape[t] = sl;
         }
         AdjView& A = c->adj;
@@ -697,8 +701,11 @@ sph_status reload_state(sph_ctx* c, const double* x, const double* v, const doub
 }
 
 // Copy the current step's forward values into tape slot t (dt is copied by
-// the caller before the step runs).
-sph_status save_tape(sph_ctx* c, int t)
+// the caller before the step runs).  list_in_slot: the step's density pass
+// wrote its neighbour list into the slot's own list buffers (the FP32
+// form's adjoint walks that list); otherwise the list is copied from the
+// context's buffers.
+sph_status save_tape(sph_ctx* c, int t, bool list_in_slot = false)
 {
     const size_t n = (size_t)c->n;
     const size_t rs = c->prec == 64 ? 8 : 4;
@@ -717,13 +724,18 @@ sph_status save_tape(sph_ctx* c, int t)
     if (c->prec == 32) {
         SPH_CU(cudaMemcpyAsync(T.pos4, c->pos4, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->st));
         SPH_CU(cudaMemcpyAsync(T.cell, c->cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+        if (!list_in_slot) {
+            SPH_CU(cudaMemcpyAsync(T.nbl, c->nbl, (size_t)nbl_capacity(c->dim) * n * sizeof(uint32_t),
+                                   cudaMemcpyDeviceToDevice, c->st));
+            SPH_CU(cudaMemcpyAsync(T.nbc, c->nbc, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+        }
     }
     return SPH_OK;
 }
 
 TapeView tape_view(const TapeSlot& T)
 {
-    return TapeView{T.id, T.kind, T.x, T.h, T.m, T.s0, T.vr, T.R, T.start, T.pos4, T.cell, T.dt};
+    return TapeView{T.id, T.kind, T.x, T.h, T.m, T.s0, T.vr, T.R, T.start, T.pos4, T.cell, T.dt, T.nbl, T.nbc};
 }
 
 // Caller [n][3] cotangents -> [3][n] FP64 (z row zeroed in 2-D), and back.
@@ -755,8 +767,20 @@ sph_status adjoint_segment(sph_ctx* c, int nsteps)
     for (int t = 0; t < nsteps; ++t) {
         SPH_CU(cudaMemcpyAsync(c->tape[t].dt, c->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         SPH_TRY(run_sort(c, 1, 0));
-        SPH_TRY(run_forces(c, 1, 1, 1));
-        SPH_TRY(save_tape(c, t));
+        // FP32 form: the step's density pass writes its neighbour list
+        // straight into the tape slot (no copy), the force pass reads it there
+        uint32_t* const nbl = c->nbl;
+        int32_t* const nbc = c->nbc;
+        const bool in_slot = c->prec == 32;
+        if (in_slot) {
+            c->nbl = c->tape[t].nbl;
+            c->nbc = c->tape[t].nbc;
+        }
+        const sph_status s = run_forces(c, 1, 1, 1);
+        c->nbl = nbl;
+        c->nbc = nbc;
+        SPH_TRY(s);
+        SPH_TRY(save_tape(c, t, in_slot));
     }
     AdjView& A = c->adj;
     SPH_CU(cudaMemsetAsync(A.eta, 0, sizeof(double), c->st));
