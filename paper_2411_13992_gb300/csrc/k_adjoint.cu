@@ -30,6 +30,33 @@ namespace sphtv {
 template <typename Real>
 using AccOf = typename std::conditional<sizeof(Real) == 4, KSum, PlainD>::type;
 
+// The cotangents Abar_k and Rbar_k of a particle as one record of
+// kAbStride<DIM> values ({Abar, Rbar}, padded to a whole number of 16-byte
+// vectors in the FP32 form), so that the pair kernel gathers a neighbour's
+// with one or two vector loads.
+template <int DIM> constexpr int kAbStride = DIM == 3 ? 8 : 4;
+
+template <typename Real, int DIM>
+__device__ __forceinline__ void load_ab(const Real* __restrict__ AR, int k, Real* Ab, Real* Rb)
+{
+    const Real* p = AR + (size_t)k * kAbStride<DIM>;
+    if constexpr (sizeof(Real) == 4) {
+        const float4 a = *(const float4*)p;
+        if (DIM == 2) {
+            Ab[0] = a.x; Ab[1] = a.y; Rb[0] = a.z; Rb[1] = a.w;
+        } else {
+            const float4 b = *(const float4*)(p + 4);
+            Ab[0] = a.x; Ab[1] = a.y; Ab[2] = a.z; Rb[0] = a.w; Rb[1] = b.x; Rb[2] = b.y;
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            Ab[d] = p[d];
+            Rb[d] = p[DIM + d];
+        }
+    }
+}
+
 // Forward values of one step.
 template <typename Real>
 struct Tape {
@@ -66,14 +93,22 @@ __device__ __forceinline__ void adj_visit(int n, int k, const Grid& G, const Con
             // holds exactly the pairs its walk accepted, in the walk's order;
             // the pair vector and r^2 with the walk's arithmetic
             const float ex = G.edgef[0], ey = G.edgef[1], ez = G.edgef[2];
+            // the entry two ahead and the neighbour's position one ahead in flight
             const uint32_t* lp = T.nbl + k;
+            uint32_t e_n = cnt > 0 ? lp[0] : 0u;
+            uint32_t e_nn = cnt > 1 ? lp[n] : 0u;
+            float4 p_n = T.pos4[e_n >> kCodeBits];
+            lp += 2 * (size_t)n;
             for (int q = 0; q < cnt; ++q, lp += n) {
-                const uint32_t e = *lp;
+                const uint32_t e = e_n;
+                const float4 pj = p_n;
+                e_n = e_nn;
+                if (q + 1 < cnt) p_n = T.pos4[e_n >> kCodeBits];
+                e_nn = q + 2 < cnt ? *lp : 0u;
                 const int j = (int)(e >> kCodeBits);
                 const uint32_t code = e & ((1u << kCodeBits) - 1u);
                 const int dx = (int)(code % kSide) - kStencilR, dy = (int)((code / kSide) % kSide) - kStencilR,
                           dz = (int)(code / (kSide * kSide)) - kStencilR;
-                const float4 pj = T.pos4[j];
                 const float2 rxy = __fadd2_rn(__ffma2_rn(make_float2(pj.x, pj.y), make_float2(-1.f, -1.f),
                                                          make_float2(ok[0], ok[1])),
                                               make_float2(-(float)dx * ex, -(float)dy * ey));
@@ -222,14 +257,14 @@ __device__ __forceinline__ Real inv_pair_h(const Consts<Real>& K, const Tape<Rea
 template <typename Real, int DIM>
 __global__ void __launch_bounds__(256) k_adj_prep(int n, Tape<Real> T, Consts<Real> K, int step_mode,
                                                   const double* __restrict__ vc, const double* __restrict__ ac,
-                                                  const double* __restrict__ drc, Real* __restrict__ Ab,
-                                                  Real* __restrict__ Rb)
+                                                  const double* __restrict__ drc, Real* __restrict__ AR)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = T.id[k];
+    Real* const ar = AR + (size_t)k * kAbStride<DIM>;
     if (T.kind[k]) {
-        for (int d = 0; d < DIM; ++d) Ab[(size_t)d * n + k] = Rb[(size_t)d * n + k] = Real(0);
+        for (int q = 0; q < kAbStride<DIM>; ++q) ar[q] = Real(0);
         return;
     }
     const double hdt = step_mode ? 0.5 * *T.dt : 0.0;
@@ -247,16 +282,17 @@ __global__ void __launch_bounds__(256) k_adj_prep(int n, Tape<Real> T, Consts<Re
     const Real chi = tv_limiter(K, s);
     const Real dchi = (K.tv_mode == SPH_TV_LIMITED && s > K.tv_thresh && K.tv_C * s < Real(1)) ? K.tv_C : Real(0);
     for (int d = 0; d < DIM; ++d) {
-        Ab[(size_t)d * n + k] = (Real)(ac[(size_t)d * n + i] + hdt * vc[(size_t)d * n + i]);
-        Rb[(size_t)d * n + k] = K.tv_xi * H2 * (chi * D[d] + dchi * DR * Real(2) * H2 * R[d]);
+        ar[d] = (Real)(ac[(size_t)d * n + i] + hdt * vc[(size_t)d * n + i]);
+        ar[DIM + d] = K.tv_xi * H2 * (chi * D[d] + dchi * DR * Real(2) * H2 * R[d]);
     }
+    for (int q = 2 * DIM; q < kAbStride<DIM>; ++q) ar[q] = Real(0);
 }
 
 // ------------------------------------------------------------------ pairs
 
 template <typename Real, int DIM>
 __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, Consts<Real> K,
-                                                   const Real* __restrict__ Ab, const Real* __restrict__ Rb,
+                                                   const Real* __restrict__ AR,
                                                    Real* __restrict__ xbp, Real* __restrict__ vbp,
                                                    Real* __restrict__ sigb, double* __restrict__ partials)
 {
@@ -273,10 +309,7 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
         const Real inv_rho_k = Real(1) / rho_k;
         const Real m_k = (Real)T.m[k];
         Real Ak[3] = {0, 0, 0}, Rk[3] = {0, 0, 0};
-        for (int d = 0; d < DIM; ++d) {
-            Ak[d] = Ab[(size_t)d * n + k];
-            Rk[d] = Rb[(size_t)d * n + k];
-        }
+        load_ab<Real, DIM>(AR, k, Ak, Rk);
         Acc ax[DIM], av[DIM], arho;
         double eta_acc = 0.0;
         auto pair = [&](int j, const Real* rv, Real r, Real inv_r) {
@@ -302,11 +335,8 @@ __global__ void __launch_bounds__(128) k_adj_pairs(int n, Tape<Real> T, Grid G, 
             if (wall) return;
             // the fluid neighbour's sums (j as i, k as j): r_jk = -r_kj
             Real Aj[3] = {0, 0, 0}, Rj[3] = {0, 0, 0}, mrv[3] = {0, 0, 0};
-            for (int d = 0; d < DIM; ++d) {
-                Aj[d] = Ab[(size_t)d * n + j];
-                Rj[d] = Rb[(size_t)d * n + j];
-                mrv[d] = -rv[d];
-            }
+            load_ab<Real, DIM>(AR, j, Aj, Rj);
+            for (int d = 0; d < DIM; ++d) mrv[d] = -rv[d];
             pair_adjoint<Real, DIM>(K, mrv, r, inv_r, w, w2, vj, rho_j, inv_rho_j, p_j, vk, rho_k, inv_rho_k, p_k,
                                     m_k, Aj, Rj, rb, dvb, rib, rjb, eb);
             for (int d = 0; d < DIM; ++d) {
@@ -440,9 +470,8 @@ static void adjoint_step_t(int n, const TapeView& V, const Grid& G, const Consts
                            int step_mode, cudaStream_t st)
 {
     Tape<Real> T = make_tape<Real>(V);
-    k_adj_prep<Real, DIM><<<nblk(n, 256), 256, 0, st>>>(n, T, K, step_mode, A.vc, A.ac, A.drc, (Real*)A.Ab,
-                                                        (Real*)A.Rb);
-    k_adj_pairs<Real, DIM><<<nblk(n, 128), 128, 0, st>>>(n, T, G, K, (const Real*)A.Ab, (const Real*)A.Rb,
+    k_adj_prep<Real, DIM><<<nblk(n, 256), 256, 0, st>>>(n, T, K, step_mode, A.vc, A.ac, A.drc, (Real*)A.AR);
+    k_adj_pairs<Real, DIM><<<nblk(n, 128), 128, 0, st>>>(n, T, G, K, (const Real*)A.AR,
                                                          (Real*)A.xbp, (Real*)A.vbp, (Real*)A.sigb, A.partials);
     k_adj_density<Real, DIM><<<nblk(n, 128), 128, 0, st>>>(n, T, G, K, (const Real*)A.sigb, (const Real*)A.xbp,
                                                            (const Real*)A.vbp, step_mode, A.xc, A.vc, A.ac, A.drc);

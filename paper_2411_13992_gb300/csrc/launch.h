@@ -32,7 +32,7 @@ struct TapeView {
 // per-step scratch in the sorted order.
 struct AdjView {
     double *xc, *vc, *ac, *drc;
-    void *Ab, *Rb, *xbp, *vbp, *sigb;
+    void *AR, *xbp, *vbp, *sigb;   // AR: per particle {Abar, Rbar} (k_adjoint.cu's record layout)
     double* partials;
     double* eta;
 };

@@ -370,8 +370,7 @@ size_t carve(sph_ctx* c, char* base)
         A.vc = W.take<double>(3 * n);
         A.ac = W.take<double>(3 * n);
         A.drc = W.take<double>(3 * n);
-        A.Ab = W.take<char>(D * n * rs);
-        A.Rb = W.take<char>(D * n * rs);
+        A.AR = W.take<char>((size_t)(D == 3 ? 8 : 4) * n * rs);   // {Abar, Rbar} records (k_adjoint.cu)
         A.xbp = W.take<char>(D * n * rs);
         A.vbp = W.take<char>(D * n * rs);
         A.sigb = W.take<char>(n * rs);
