@@ -307,15 +307,18 @@ __global__ void k_order_cells(int nbin, const int32_t* __restrict__ prefix, cons
 // {offset, m}, since h is then a constant), mf = m in FP32, cell_out = key;
 // pos4c (when given: the FP32 form at uniform resolution) = {offset, bits of
 // the cell index}, which the FP32 density walk reads instead of pos4 and
-// cell_out.
+// cell_out.  When *varies is 0 every particle has particle 0's h, m and
+// sigma0 and is a fluid particle, and both state sets hold these arrays
+// (set by sph_set_state): they are left where they are.
 template <typename Real, int DIM, bool CARRY_AD, bool F32POS>
 __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real> src, StateSet<Real> dst,
                           const int32_t* __restrict__ key, Grid G, float4* __restrict__ pos4,
                           int32_t* __restrict__ cell_out, float* __restrict__ mf, int uniform_h,
-                          float4* __restrict__ pos4c)
+                          float4* __restrict__ pos4c, const uint32_t* __restrict__ varies)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const bool moves = *varies != 0;
     int i = perm[k];
     double xs[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -330,13 +333,15 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, StateSet<Real
         }
     }
     if (src.drho) dst.drho[k] = src.drho[i];
-    double h = src.h[i];
-    double m = src.m[i];
-    dst.h[k] = h;
-    dst.m[k] = m;
-    dst.s0[k] = src.s0[i];
+    const double h = moves ? src.h[i] : src.h[0];
+    const double m = moves ? src.m[i] : src.m[0];
+    if (moves) {
+        dst.h[k] = h;
+        dst.m[k] = m;
+        dst.s0[k] = src.s0[i];
+        dst.kind[k] = src.kind[i];
+    }
     dst.id[k] = src.id[i];
-    dst.kind[k] = src.kind[i];
     if (F32POS) {
         int kk = key[i] >> G.sub_shift;   // the cell of the sort key
         int c[3];
@@ -389,7 +394,7 @@ cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int3
 template <typename Real>
 static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                       const Grid& G, float4* pos4, int32_t* cell, float* mf, int uh, int carry_ad, cudaStream_t st,
-                      float4* pos4c)
+                      float4* pos4c, const uint32_t* varies)
 {
     const int T = 256;
     auto s = *(StateSet<Real>*)src;
@@ -397,25 +402,25 @@ static void permute_t(int dim, int n, const int32_t* perm, void* src, void* dst,
     constexpr bool F32 = true;   // both forms: the density passes walk the FP32 cell-relative positions
     if (dim == 2) {
         if (carry_ad)
-            k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+            k_permute<Real, 2, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c, varies);
         else
-            k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+            k_permute<Real, 2, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c, varies);
     } else {
         if (carry_ad)
-            k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+            k_permute<Real, 3, true, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c, varies);
         else
-            k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c);
+            k_permute<Real, 3, false, F32><<<nblk(n, T), T, 0, st>>>(n, perm, s, d, key, G, pos4, cell, mf, uh, pos4c, varies);
     }
 }
 
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                            const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
-                           cudaStream_t st, float4* pos4c)
+                           cudaStream_t st, const uint32_t* varies, float4* pos4c)
 {
     if (prec == 64)
-        permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c);
+        permute_t<double>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c, varies);
     else
-        permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c);
+        permute_t<float>(dim, n, perm, src, dst, key, G, pos4, cell, mf, uniform_h, carry_ad, st, pos4c, varies);
     return cudaGetLastError();
 }
 

@@ -140,6 +140,18 @@ __global__ void k_check_input(int n, const double* __restrict__ h, const double*
     if (!ok) atomicOr(err, ERRB_INPUT);
 }
 
+// Sets *varies (cleared by the caller) when a particle's h, m or sigma0
+// differs from particle 0's or a particle is a wall particle.
+__global__ void k_check_constants(int n, const double* __restrict__ h, const double* __restrict__ m,
+                                  const double* __restrict__ s0, const int8_t* __restrict__ kind, uint32_t* varies)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool v = kind[i] != 0 || h[i] != h[0] || m[i] != m[0] || s0[i] != s0[0];
+    const unsigned b = __ballot_sync(__activemask(), v);
+    if (b && (threadIdx.x & 31) == __ffs(b) - 1) atomicOr(varies, 1u);
+}
+
 template <typename Real>
 __global__ void k_scalar_out(int n, const Real* __restrict__ src, const int32_t* __restrict__ id,
                              double* __restrict__ dst)
@@ -261,6 +273,13 @@ cudaError_t launch_check_input(int n, const double* h, const double* m, double h
                                cudaStream_t st)
 {
     k_check_input<<<nblk(n, 256), 256, 0, st>>>(n, h, m, h_min, h_max, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_constants(int n, const double* h, const double* m, const double* s0, const int8_t* kind,
+                                   uint32_t* varies, cudaStream_t st)
+{
+    k_check_constants<<<nblk(n, 256), 256, 0, st>>>(n, h, m, s0, kind, varies);
     return cudaGetLastError();
 }
 

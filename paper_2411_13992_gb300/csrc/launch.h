@@ -56,7 +56,7 @@ cudaError_t launch_scatter_order(int n, int nbin, const int32_t* key, const int3
                                  int shift, int32_t* cell_start, cudaStream_t st, int64_t* launches);
 cudaError_t launch_permute(int prec, int dim, int n, const int32_t* perm, void* src, void* dst, const int32_t* key,
                            const Grid& G, float4* pos4, int32_t* cell, float* mf, int uniform_h, int carry_ad,
-                           cudaStream_t st, float4* pos4c = nullptr);
+                           cudaStream_t st, const uint32_t* varies, float4* pos4c = nullptr);
 
 // k_pair.cu (FP64 form; FP32 calls are forwarded to k_pair32.cu)
 int pair_threads(int prec, int n, int sms);
@@ -111,6 +111,8 @@ cudaError_t launch_rho_out(int prec, int n, const void* vr, const int8_t* kind, 
 cudaError_t launch_check_input(int n, const double* h, const double* m, double h_min, double h_max, uint32_t* err,
                                cudaStream_t st);
 cudaError_t launch_scalar_out(int prec, int n, const void* src, const int32_t* id, double* dst, cudaStream_t st);
+cudaError_t launch_check_constants(int n, const double* h, const double* m, const double* s0, const int8_t* kind,
+                                   uint32_t* varies, cudaStream_t st);
 cudaError_t launch_scalar_in(int prec, int n, const double* src, const int8_t* kind, void* dst, cudaStream_t st);
 
 // k_dual.cu (dual-criteria time stepping).  Device pointers of one context;

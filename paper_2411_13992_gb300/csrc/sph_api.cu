@@ -89,7 +89,8 @@ struct sph_ctx {
     double* rows;        // first-level reduction of the partials
     double* diag;
     double* dt;
-    uint32_t* err;
+    uint32_t* err;          // [0] the sticky device error word; [1] nonzero when the particles' h, m,
+                            // sigma0 or kind vary (else the sort leaves these arrays where they are)
     double* stage;
     int have_state, have_cells, ad_given;
     // kick-drift-kick, built with a and dr given: the state is still in the
@@ -434,7 +435,7 @@ sph_status run_sort(sph_ctx* c, int drift, int carry_ad)
     SPH_MARK(SPH_K_ORDER, 1);
     SPH_MARK(SPH_K_PERMUTE, 0);
     SPH_CU(launch_permute(c->prec, c->dim, n, c->perm, cur_set(c), other_set(c), c->key, c->G, c->pos4, c->cell,
-                          c->mf, c->K32.uniform_h, carry_ad, c->st, c->pos4c));
+                          c->mf, c->K32.uniform_h, carry_ad, c->st, c->err + 1, c->pos4c));
     ++c->launches;
     SPH_MARK(SPH_K_PERMUTE, 1);
     c->cur = 1 - c->cur;
@@ -668,6 +669,21 @@ sph_status vec_in(sph_ctx* c, int prec, const double* src, void* dst)
     return SPH_OK;
 }
 
+// h, m, sigma0 and kind of state set 0 into state set 1: the sort leaves these
+// arrays where they are when they do not vary over the particles, so both
+// sets must hold them.
+sph_status copy_constants(sph_ctx* c)
+{
+    const size_t n = (size_t)c->n;
+    const StateSet<double>& A = c->set[0].d;
+    const StateSet<double>& B = c->set[1].d;
+    SPH_CU(cudaMemcpyAsync(B.h, A.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(B.m, A.m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(B.s0, A.s0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    SPH_CU(cudaMemcpyAsync(B.kind, A.kind, n, cudaMemcpyDeviceToDevice, c->st));
+    return SPH_OK;
+}
+
 sph_status reload_state(sph_ctx* c, const double* x, const double* v, const double* a, const double* dr)
 {
     const size_t n = (size_t)c->n;
@@ -690,6 +706,7 @@ sph_status reload_state(sph_ctx* c, const double* x, const double* v, const doub
     SPH_CU(cudaMemcpyAsync(Sd.m, c->orig_m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     SPH_CU(cudaMemcpyAsync(Sd.s0, c->orig_s0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     SPH_CU(cudaMemcpyAsync(Sd.kind, c->orig_kind, n, cudaMemcpyDeviceToDevice, c->st));
+    SPH_TRY(copy_constants(c));
     SPH_CU(launch_walls_velocity(c->prec, c->dim, (int)n, Sd.kind, c->orig_vw, sv, c->st));
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     c->launches += 2;
@@ -896,6 +913,7 @@ sph_status sph_create(const sph_params* p, int64_t n, void* workspace, size_t by
     }
     carve(c, (char*)workspace);
     if (cudaMemsetAsync(c->err, 0, 4 * sizeof(uint32_t), c->st) != cudaSuccess ||
+        cudaMemsetAsync(c->err + 1, 1, 1, c->st) != cudaSuccess ||
         cudaMemsetAsync(c->diag, 0, DG_COUNT * sizeof(double), c->st) != cudaSuccess) {
         delete c;
         return SPH_ERR_CUDA;
@@ -950,6 +968,10 @@ sph_status sph_set_state(sph_ctx* c, const double* x, const double* v, const dou
     }
     SPH_CU(launch_init_ids((int)n, Sd.id, c->st));
     SPH_CU(launch_check_input((int)n, Sd.h, Sd.m, c->P.h_min, c->P.h_max, c->err, c->st));
+    SPH_CU(cudaMemsetAsync(c->err + 1, 0, sizeof(uint32_t), c->st));
+    SPH_CU(launch_check_constants((int)n, Sd.h, Sd.m, Sd.s0, Sd.kind, c->err + 1, c->st));
+    SPH_TRY(copy_constants(c));
+    ++c->launches;
     if (Sd.drho) SPH_CU(cudaMemsetAsync(Sd.drho, 0, n * rs, c->st));
     c->launches += 3;
     if (c->P.adjoint_steps > 0) {
@@ -1435,6 +1457,7 @@ extern "C" sph_status sph_density_noalloc(const sph_params* p, int64_t n, const 
     SPH_CU(cudaMemsetAsync(c.count, 0, nc1 * sizeof(int32_t), c.st));
     SPH_CU(cudaMemsetAsync(c.prefix, 0, nc1 * sizeof(int32_t), c.st));
     SPH_CU(cudaMemsetAsync(c.err, 0, 4 * sizeof(uint32_t), c.st));
+    SPH_CU(cudaMemsetAsync(c.err + 1, 1, 1, c.st));   // the sort moves h, m, sigma0 and kind
     SPH_CU(cudaMemsetAsync(S0.v, 0, (size_t)c.dim * n * sizeof(double), c.st));
     SPH_CU(launch_vec_in(64, c.dim, ni, x, S0.x, c.st));
     SPH_CU(cudaMemcpyAsync(S0.h, h, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
