@@ -95,31 +95,42 @@ __global__ void k_kick_drift_key(int n, StateSet<Real> S, const double* __restri
                 S.x[(size_t)d * n + i] = xs[d];
             }
         }
-    } else if (drift == 1 && S.kind[i] == 0) {
-        const double dt = *dt_ptr;
-        const double hdt = 0.5 * dt;
-        // FP32 form: the displacement dt v + dr in FP32 (one rounding, from
-        // FP32 inputs), accumulated into the FP64 position
-        const float dt_f = d2f_rn(dt);
+    } else if (drift == 1) {
+        // every load issued before the kind test and the arithmetic
+        Real vv[3] = {0, 0, 0}, aa[3] = {0, 0, 0}, rr[3] = {0, 0, 0};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            size_t o = (size_t)d * n + i;
-            Real vh = kick<Real>(S.v[o], hdt, S.a[o]);
-            S.v[o] = vh;
-            double xn;
-            if (sizeof(Real) == 4)
-                xn = __dadd_rn(xs[d], to_double(__fmaf_rn(dt_f, (float)vh, (float)S.dr[o])));
-            else
-                xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(S.dr[o]));
-            if (G.periodic[d]) {
-                // the wrap only in warps where a particle left the box (the
-                // FP64 operation would otherwise be issued for every warp)
-                const int w = wrap_side(G, xn, d);
-                if (__any_sync(__activemask(), w != 0) && w != 0)
-                    xn = w < 0 ? __dadd_rn(xn, G.L[d]) : __dsub_rn(xn, G.L[d]);
+            const size_t o = (size_t)d * n + i;
+            vv[d] = S.v[o];
+            aa[d] = S.a[o];
+            rr[d] = S.dr[o];
+        }
+        const double dt = *dt_ptr;
+        if (S.kind[i] == 0) {
+            const double hdt = 0.5 * dt;
+            // FP32 form: the displacement dt v + dr in FP32 (one rounding, from
+            // FP32 inputs), accumulated into the FP64 position
+            const float dt_f = d2f_rn(dt);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                size_t o = (size_t)d * n + i;
+                Real vh = kick<Real>(vv[d], hdt, aa[d]);
+                S.v[o] = vh;
+                double xn;
+                if (sizeof(Real) == 4)
+                    xn = __dadd_rn(xs[d], to_double(__fmaf_rn(dt_f, (float)vh, (float)rr[d])));
+                else
+                    xn = __dadd_rn(__dadd_rn(xs[d], __dmul_rn(dt, to_double(vh))), to_double(rr[d]));
+                if (G.periodic[d]) {
+                    // the wrap only in warps where a particle left the box (the
+                    // FP64 operation would otherwise be issued for every warp)
+                    const int w = wrap_side(G, xn, d);
+                    if (__any_sync(__activemask(), w != 0) && w != 0)
+                        xn = w < 0 ? __dadd_rn(xn, G.L[d]) : __dsub_rn(xn, G.L[d]);
+                }
+                xs[d] = xn;
+                S.x[o] = xn;
             }
-            xs[d] = xn;
-            S.x[o] = xn;
         }
     }
 #pragma unroll
