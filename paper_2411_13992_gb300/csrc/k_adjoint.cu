@@ -13,8 +13,8 @@
 //                   neighbour's sums (k as j), so no atomics are needed;
 //                   also the density cotangent and d/d(eta) partials
 //   k_adj_density : the density sum rho_k = rho0 sum_j W_kj / sigma0_k, then
-//                   the reverse of the drift and the opening kick
-//   k_adj_sum     : d/d(eta) of the step (fixed-order reduction)
+//                   the reverse of the drift and the opening kick; its first
+//                   block adds the step's d/d(eta) (fixed-order reduction)
 //
 // Subgradients: d beta/d dU = eta_R / c inside 0 < eta_R dU / c < 1, else 0
 // (Eq. 6); d chi/d s = C inside thresh < s < 1/C, else 0 (Eq. 15).
@@ -366,9 +366,28 @@ __global__ void __launch_bounds__(128) k_adj_density(int n, Tape<Real> T, Grid G
                                                      const Real* __restrict__ sigb, const Real* __restrict__ xbp,
                                                      const Real* __restrict__ vbp, int step_mode,
                                                      double* __restrict__ xc, double* __restrict__ vc,
-                                                     double* __restrict__ ac, double* __restrict__ drc)
+                                                     double* __restrict__ ac, double* __restrict__ drc,
+                                                     const double* __restrict__ partials, int nblocks,
+                                                     double* __restrict__ eta)
 {
     using Acc = AccOf<Real>;
+    if (blockIdx.x == 0) {
+        // block 0 first adds the pair kernel's per-block d/d(eta) partials to
+        // eta (a fixed order: strided per thread, then the warps, then the
+        // block's warps by thread 0)
+        __shared__ double wsum[32];
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(size_t)b * kNPart];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
+            *eta += t;
+        }
+    }
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = T.id[k];
@@ -404,19 +423,6 @@ __global__ void __launch_bounds__(128) k_adj_density(int n, Tape<Real> T, Grid G
         xc[o] = xb;
         vc[o] = vh;
     }
-}
-
-__global__ void __launch_bounds__(256) k_adj_sum(int nblocks, const double* __restrict__ partials,
-                                                 double* __restrict__ acc)
-{
-    double v[kNPart];
-#pragma unroll
-    for (int q = 0; q < kNPart; ++q) v[q] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += partials[(size_t)b * kNPart];
-    __shared__ double out[kNPart];
-    block_partials<false>(v, out);
-    __syncthreads();
-    if (threadIdx.x == 0) *acc += out[0];
 }
 
 // ----------------------------------------------------- cotangent layouts
@@ -474,8 +480,8 @@ static void adjoint_step_t(int n, const TapeView& V, const Grid& G, const Consts
     k_adj_pairs<Real, DIM><<<nblk(n, 128), 128, 0, st>>>(n, T, G, K, (const Real*)A.AR,
                                                          (Real*)A.xbp, (Real*)A.vbp, (Real*)A.sigb, A.partials);
     k_adj_density<Real, DIM><<<nblk(n, 128), 128, 0, st>>>(n, T, G, K, (const Real*)A.sigb, (const Real*)A.xbp,
-                                                           (const Real*)A.vbp, step_mode, A.xc, A.vc, A.ac, A.drc);
-    k_adj_sum<<<1, 256, 0, st>>>(nblk(n, 128), A.partials, A.eta);
+                                                           (const Real*)A.vbp, step_mode, A.xc, A.vc, A.ac, A.drc,
+                                                           A.partials, nblk(n, 128), A.eta);
 }
 
 cudaError_t launch_adjoint_step(int prec, int dim, int n, const TapeView& V, const Grid& G, const void* K,

@@ -803,7 +803,7 @@ sph_status adjoint_segment(sph_ctx* c, int nsteps)
     for (int t = nsteps - 1; t >= 0; --t) {
         SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[t]), cells_only(c->G), consts(c), A, 1,
                                       c->st));
-        c->launches += 4;
+        c->launches += 3;
     }
     return SPH_OK;
 }
@@ -1348,7 +1348,7 @@ sph_status sph_force_pass_adjoint(sph_ctx* c, const double* x, const double* v, 
     SPH_TRY(cot_in(c, drbar, A.drc));
     SPH_CU(launch_adjoint_step(c->prec, c->dim, (int)c->n, tape_view(c->tape[0]), cells_only(c->G), consts(c), A, 0,
                               c->st));
-    c->launches += 4;
+    c->launches += 3;
     SPH_TRY(cot_out(c, A.xc, xbar));
     SPH_TRY(cot_out(c, A.vc, vbar));
     double eta = 0.0;
