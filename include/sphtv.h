@@ -130,7 +130,10 @@ typedef struct sph_params {
     int32_t kahan;          /* FP32 form: 1 = compensated pair sums (default) */
     int32_t adjoint_steps;  /* longest segment sph_step_adjoint will replay
                                (0: no adjoint buffers in the workspace; must be 0
-                               with SPH_INT_DUAL) */
+                               with SPH_INT_DUAL); each step of it takes a tape
+                               slot in the workspace, which in the FP32 form also
+                               holds that step's neighbour list (128 entries per
+                               particle in 3-D, 96 in 2-D, 4 bytes each) */
     int32_t integrator;     /* SPH_INT_*: kick-drift-kick (default) or dual-criteria;
                                SPH_INT_DUAL requires fixed_dt = 0 */
     int32_t graphs;         /* 1 (default): sph_step replays kick-drift-kick steps two at a
