@@ -2,7 +2,7 @@
 2-D Taylor-Green vortex at dp = 1/200, Re = 100, to t = 5 (40,000 particles,
 about 4,700 advection steps per run, FP32).
 
-What the paper states and this build reproduces:
+What the paper states and these GPU runs reproduce:
 * the unlimited correction (Eq. 14) overcorrects: late in the decay its
   transport speed max|v + dr/Dt| exceeds the fluid speed max|v| and the
   kinetic energy decays more slowly than the analytic exp(-16 pi^2 t / Re);
