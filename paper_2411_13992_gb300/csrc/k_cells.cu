@@ -261,10 +261,12 @@ __device__ __forceinline__ int bin_start_of(const int32_t* __restrict__ prefix, 
 
 // ------------------------------------------------ scatter and cell order
 
-// Slots by warp-aggregated atomics on the bins' counts, counting down: a bin
-// of c particles hands out c - 1 .. 0, so every count is back at zero after
-// the scatter (the next sort needs no clearing).  The order inside a bin is
-// fixed afterwards by k_order_cells.
+// Slots by atomics on the bins' counts, counting down: a bin of c particles
+// hands out c - 1 .. 0, so every count is back at zero after the scatter
+// (the next sort needs no clearing).  The order inside a bin is fixed
+// afterwards by k_order_cells.  One atomic per particle: the sub-cell bins
+// are seldom shared within a warp, and aggregating the lanes by
+// __match_any_sync cost more than it saved.
 __global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t* __restrict__ prefix,
                           const int32_t* __restrict__ tile_off, int32_t* __restrict__ count,
                           int32_t* __restrict__ perm)
@@ -272,15 +274,7 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ key, const int32_t*
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = key[i];
-    const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, k);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int np = __popc(peers);
-    int base = 0;
-    if (lane == leader) base = atomicSub(&count[k], np) - np;
-    base = __shfl_sync(act, base, leader);
-    const int pos = bin_start_of(prefix, tile_off, k) + base + __popc(peers & ((1u << lane) - 1u));
+    const int pos = bin_start_of(prefix, tile_off, k) + atomicSub(&count[k], 1) - 1;
     perm[pos] = i;
 }
 
