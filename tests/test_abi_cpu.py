@@ -95,6 +95,23 @@ def test_workspace_query_and_argument_checks(lib):
         sph.sph_query_workspace(p, 0)
 
 
+def test_adjoint_tape_holds_each_steps_neighbour_list(lib):
+    """Each adjoint tape slot of the FP32 form keeps its step's neighbour list
+    (list capacity x n entries of 4 bytes, and n counts); the FP64 form's
+    reverse kernels scan the cells and keep no list."""
+    for c, cap in ((cases.tgv2d(20), 96), (cases.tgv3d(10), 128)):
+        n = c["n"]
+        grow = {}
+        for prec in (32, 64):
+            q0 = sph.params_from_case(c, prec)
+            q2 = sph.params_from_case(c, prec)
+            q2.adjoint_steps = 2
+            grow[prec] = sph.sph_query_workspace(q2, n) - sph.sph_query_workspace(q0, n)
+        lists = 2 * (cap * n * 4 + n * 4)
+        assert grow[32] >= lists, (grow, lists)
+        assert grow[32] - lists < grow[64], (grow, lists)
+
+
 def test_sub_cells_of_the_sort(lib):
     """x_subcells 0/1 (no refinement), 2 and 4 are accepted (default 4); the
     sort's count, cursor and sub-cell start arrays grow with the bins; where
